@@ -1,0 +1,118 @@
+"""Pins of the oracle's forces, energy and integrator.
+
+References: central finite differences of the shadow free energy, Newton's
+third law, Table I's moment conditions, time reversibility of the undamped
+integrator, and energy conservation of the damped one.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+M = O.Model()
+
+
+def omega_at(R, L, Z, n, model):
+    ev = O.evaluate(R, L, Z, n, model, None, with_kernel=False, with_forces=False)
+    return ev.Omega
+
+
+@pytest.fixture(scope="module")
+def small():
+    s = synth.make_system(8, 42, L=7.0)
+    rng = np.random.default_rng(4)
+    n = rng.normal(scale=0.05, size=8)
+    n -= n.mean()
+    return s, n
+
+
+def test_forces_match_finite_differences_of_free_energy(small):
+    # With 20 squarings the occupations equal Fermi-Dirac to ~1e-13, so the
+    # Hellmann-Feynman forces are the exact gradient of Omega at fixed n.
+    s, n = small
+    m20 = O.Model(n_sq=20)
+    ev = O.evaluate(s.R, s.L, s.Z, n, m20, None, with_kernel=False)
+    h = 1e-5
+    for I in (0, 3, 7):
+        for c in range(3):
+            Rp, Rm = s.R.copy(), s.R.copy()
+            Rp[I, c] += h
+            Rm[I, c] -= h
+            fd = -(omega_at(Rp, s.L, s.Z, n, m20) - omega_at(Rm, s.L, s.Z, n, m20)) / (2 * h)
+            assert ev.F[I, c] == pytest.approx(fd, abs=2e-7)
+
+
+def test_forces_with_ten_squarings_are_close_to_gradient(small):
+    s, n = small
+    ev = O.evaluate(s.R, s.L, s.Z, n, M, None, with_kernel=False)
+    h = 1e-5
+    I = 2
+    for c in range(3):
+        Rp, Rm = s.R.copy(), s.R.copy()
+        Rp[I, c] += h
+        Rm[I, c] -= h
+        fd = -(omega_at(Rp, s.L, s.Z, n, M) - omega_at(Rm, s.L, s.Z, n, M)) / (2 * h)
+        assert ev.F[I, c] == pytest.approx(fd, abs=1e-4)
+
+
+def test_forces_sum_to_zero(small):
+    s, n = small
+    ev = O.evaluate(s.R, s.L, s.Z, n, M, None, with_kernel=False)
+    assert np.allclose(ev.F.sum(axis=0), 0.0, atol=1e-11)
+
+
+@pytest.mark.parametrize("kmax", [5, 6, 7])
+def test_table_I_coefficients_annihilate_constant_and_linear_histories(kmax):
+    kappa, alpha, c = O.TABLE_I[kmax]
+    c = np.asarray(c, dtype=float)
+    k = np.arange(len(c))
+    assert c.sum() == 0.0
+    assert (k * c).sum() == 0.0
+    assert kappa < 2.0
+
+
+def test_dissipation_vanishes_on_linear_trajectory():
+    xl = O.XLParams()
+    a, b = np.array([0.1, -0.1]), np.array([0.01, 0.02])
+    hist = np.array([a - k * b for k in range(xl.kmax + 1)])   # n(t - k dt) = a - k b
+    n_new = O.n_update(hist, np.zeros(2), xl)
+    assert np.allclose(n_new, a + b, atol=1e-15)
+
+
+def test_undamped_integrator_is_time_reversible():
+    s = synth.make_system(8, 42, L=7.0)
+    xl = O.XLParams(alpha=0.0, rank_m=2, kernel_c=-15.0, mix_alpha=0.06, scf_tol=1e-12,
+                    scf_max_iter=3000)
+    st0, _ = O.md_init(s.R, s.V, s.L, s.Z, s.mass, M, xl)
+    st = st0
+    for _ in range(6):
+        st, _ = O.md_step(st, s.L, s.Z, s.mass, M, xl)
+    # reverse at t6: flip the velocities; the "previous" n of the backward run
+    # is n(t7) = 2 n6 - n5 - kappa K r6, the undamped Eq. VRL_Damp.
+    n7 = O.n_update(st.nhist, st.Kr, xl)
+    hist = st.nhist.copy()
+    hist[1] = n7
+    rev = O.MDState(R=st.R.copy(), V=-st.V, nhist=hist, F=st.F, Kr=st.Kr)
+    st_back = rev
+    for _ in range(6):
+        st_back, _ = O.md_step(st_back, s.L, s.Z, s.mass, M, xl)
+    d = O.min_image(st_back.R - st0.R, s.L)
+    assert np.max(np.abs(d)) < 1e-11
+    assert np.allclose(st_back.nhist[0], st0.nhist[0], atol=1e-11)
+    assert np.allclose(-st_back.V, st0.V, atol=1e-11)
+
+
+def test_energy_is_conserved_over_a_short_run():
+    s = synth.make_system(24, 1705, L=7.0)
+    xl = O.XLParams(rank_m=2, kernel_c=1 - 1 / 0.06, mix_alpha=0.06)
+    st, ev = O.md_init(s.R, s.V, s.L, s.Z, s.mass, M, xl)
+    E = [O.kinetic_energy(st.V, s.mass) + ev.Omega]
+    for _ in range(60):
+        st, ev = O.md_step(st, s.L, s.Z, s.mass, M, xl)
+        E.append(O.kinetic_energy(st.V, s.mass) + ev.Omega)
+    E = np.array(E)
+    assert np.max(np.abs(E - E[0])) < 1e-4
+    # no systematic drift: slope of a linear fit over the run is tiny
+    slope = np.polyfit(np.arange(len(E)), E, 1)[0]
+    assert abs(slope) < 1e-6
