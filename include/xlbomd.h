@@ -1,0 +1,174 @@
+/*
+ * xlbomd.h - C ABI of the GB300 XL-BOMD hot path.
+ *
+ * Finite-temperature extended-Lagrangian Born-Oppenheimer molecular dynamics
+ * (A. M. N. Niklasson, arXiv:1705.10845) on an orthogonal self-consistent-
+ * charge tight-binding (SCC-TB) model.  One MD step (Section II.E, Eqs.
+ * Integration and VRL_Damp) builds H[n] from the dynamical charges n, forms
+ * the density matrix D = f(H[n]) by the recursive Fermi-operator expansion
+ * with the chemical potential fixed by Tr D = N_occ (Section IV.B), computes
+ * the charge response along m probe directions by canonical density-matrix
+ * perturbation theory (Section V.B), applies the rank-m kernel
+ * K ~ (dq/dn - I)^-1 (Section V.D-V.E, Eqs. KCI, JCI, K_up, v_1), takes the
+ * Mulliken charges and Hellmann-Feynman forces (Eq. EqMotFT) and advances R
+ * and n (Eq. VRL_Damp with Table I).
+ *
+ * Conventions (every entry point):
+ *  - All device state is owned by the context; the library allocates it in
+ *    xlbomd_init and frees it in xlbomd_free.  Host arrays passed in are
+ *    copied before the call returns; the caller keeps ownership.
+ *  - Work is enqueued on the CUDA stream given to xlbomd_init (NULL = the
+ *    legacy default stream).  Calls that must read device results to decide
+ *    the next launch (the chemical-potential Newton loop, the probe loop of
+ *    the kernel update, xlbomd_get) synchronise that stream.
+ *  - Errors never abort the process and no kernel traps.  A failing call
+ *    returns a negative status; the status is also stored in the context
+ *    (sticky: later calls return it without doing work until
+ *    xlbomd_clear_error) and xlbomd_last_error() gives a message.
+ *  - Units: Angstrom, eV, fs, amu, Kelvin; charges in electrons.
+ *  - Layouts: positions, velocities, forces are natoms x 3 row-major double;
+ *    charge vectors are natoms doubles; matrices are N x N row-major double
+ *    with N = 4 natoms (orbital order s, px, py, pz per atom).
+ */
+#ifndef XLBOMD_API_H_
+#define XLBOMD_API_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct xlbomd_ctx xlbomd_ctx;
+
+typedef enum {
+  XLBOMD_OK = 0,
+  XLBOMD_ERR_ARG = -1,           /* invalid argument or size */
+  XLBOMD_ERR_OOM = -2,           /* device allocation failed */
+  XLBOMD_ERR_CUDA = -3,          /* a CUDA call failed */
+  XLBOMD_ERR_NOT_CONVERGED = -4, /* SCF or chemical-potential iteration budget spent */
+  XLBOMD_ERR_SPECTRUM = -5,      /* |beta (e - mu)| / 2^(n+1) >= 1 for a Gershgorin bound */
+  XLBOMD_ERR_DIVERGED = -6,      /* residual |q - n| above the divergence threshold */
+  XLBOMD_ERR_TIMEOUT = -7,       /* a bounded device wait gave up */
+  XLBOMD_ERR_UNSUPPORTED = -8    /* requested precision not built for this device */
+} xlbomd_status;
+
+/* Arithmetic of the expansion and response matrix products. */
+typedef enum {
+  XLBOMD_FP64 = 0,   /* plain FP64 products */
+  XLBOMD_FP16x3 = 1, /* split FP16 hi/lo operands, 3 products, FP32 accumulation */
+  XLBOMD_BF16x3 = 2  /* split BF16 hi/lo operands, 3 products, FP32 accumulation */
+} xlbomd_prec;
+
+/* Model and integrator constants.  xlbomd_default_params() fills the values
+ * of the 24-atom reference system (Te = 1000 K, 10 squarings, rank 2). */
+typedef struct {
+  /* Slater-Koster model (Section VI stand-in) */
+  double eps_s, eps_p;     /* on-site energies (eV) */
+  double t0[4];            /* ss-sigma, sp-sigma, pp-sigma, pp-pi prefactors (eV) */
+  double r_decay;          /* hopping decay length (A) */
+  double r_cut, r_taper;   /* quintic taper on [r_taper, r_cut] (A) */
+  double hubbard_U;        /* on-site Coulomb (eV) */
+  double coulomb_k;        /* e^2 / (4 pi eps0) = 14.399645 eV A */
+  /* electrons */
+  double Te;               /* electronic temperature (K) */
+  int n_sq;                /* squarings of the recursive Fermi-operator expansion */
+  /* XL-BOMD (Table I row kmax) */
+  double dt;               /* fs */
+  double kappa, alpha;
+  double c[8];
+  int kmax;                /* 5, 6 or 7 */
+  int rank_m;              /* probes per kernel update, 0..8 */
+  double kernel_c;         /* J_0 = c I, c != 1 (Eq. JCI) */
+  double mix_alpha;        /* linear mixing of the t0 SCF */
+  double scf_tol;          /* max |q - n| of the t0 SCF */
+  int scf_max_iter;
+  double mu_tol;           /* |beta dmu| below which the Newton loop on mu stops */
+  int mu_max_iter;
+  double diverge_tol;      /* max |q - n| above which a step reports ERR_DIVERGED */
+  int prec;                /* xlbomd_prec */
+  int energy_every;        /* energy monitor every k steps inside xlbomd_step (0 = never) */
+} xlbomd_params;
+
+/* One trajectory.  R and V are natoms x 3 row-major (A, A/fs), Z natoms
+ * valence charges (4 for the carbon-like model), mass in amu. */
+typedef struct {
+  int natoms;
+  double box_L;
+  const double* R;
+  const double* V;
+  const double* Z;
+  double mass;
+} xlbomd_system;
+
+/* Quantities for xlbomd_get / xlbomd_set. */
+typedef enum {
+  XLBOMD_Q = 0,        /* get: Mulliken charges q[n] (natoms) */
+  XLBOMD_N = 1,        /* get/set: n(t) (natoms); set fills the whole history with it */
+  XLBOMD_NHIST = 2,    /* get/set: n(t - k dt), k = 0..kmax ((kmax+1) x natoms) */
+  XLBOMD_F = 3,        /* get: forces (natoms x 3, eV/A) */
+  XLBOMD_R = 4,        /* get/set: positions (natoms x 3) */
+  XLBOMD_V = 5,        /* get/set: velocities (natoms x 3) */
+  XLBOMD_KR = 6,       /* get: K (q - n) (natoms) */
+  XLBOMD_RES = 7,      /* get: residual q - n (natoms) */
+  XLBOMD_ENERGY = 8,   /* get: [Omega, band, coulomb, entropy, kinetic, total] (6) */
+  XLBOMD_MU = 9,       /* get/set: chemical potential (1); set is the Newton start */
+  XLBOMD_D = 10,       /* get: density matrix (N x N) */
+  XLBOMD_H = 11,       /* get: H[n] (N x N) */
+  XLBOMD_GAMMA = 12,   /* get: Coulomb matrix gamma (natoms x natoms) */
+  XLBOMD_STATS = 13,   /* get: [mu passes, NS products, probes used, GEMMs, steps] (5) */
+  XLBOMD_PROBES = 14   /* get: probes V then responses W (2 x rank_m x natoms) */
+} xlbomd_quantity;
+
+/* Defaults of the 24-atom reference workload. */
+void xlbomd_default_params(xlbomd_params* p);
+
+/* Allocate device state for nsys trajectories and upload R, V, Z (Eq. IBC
+ * nuclear initial conditions).  Builds H0 and gamma; n = 0.  Does not run
+ * the t0 SCF (xlbomd_scf).  cuda_stream is a cudaStream_t or NULL.
+ * Errors: ERR_ARG (natoms < 1, box_L <= r_cut, rank_m > 8, kmax not 5..7,
+ * n_sq < 1, kernel_c == 1, nsys < 1), ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED. */
+xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* systems, int nsys,
+                          void* cuda_stream, xlbomd_ctx** out);
+
+/* t0 ground state of system sys (Eq. IBC): linear-mixing SCF
+ * n <- n + mix_alpha (q[n] - n) (Eq. SCF_K with K_0) to max|q - n| < scf_tol,
+ * then n-history = n(t0), forces and K r at t0.  sys = -1: every system. */
+xlbomd_status xlbomd_scf(xlbomd_ctx* ctx, int sys);
+
+/* a1-a2: H0 and gamma at the current R, H[n] = H0 + diag(gamma n). */
+xlbomd_status xlbomd_build_H(xlbomd_ctx* ctx, int sys);
+
+/* a3-a6: recursive expansion D = f(H[n]) with mu from Tr D = N_occ
+ * (Section IV.B), Mulliken q, residual r = q - n, forces (Eq. EqMotFT). */
+xlbomd_status xlbomd_density(xlbomd_ctx* ctx, int sys);
+
+/* a7 for one probe: w = d q[n + lambda v] / d lambda (Section V.B, canonical
+ * perturbation theory, mu re-solved to hold N_occ).  v_dev, w_dev are device
+ * arrays of natoms doubles; requires xlbomd_density on the same state. */
+xlbomd_status xlbomd_response(xlbomd_ctx* ctx, int sys, const double* v_dev, double* w_dev);
+
+/* a7-a8: rank-m kernel on r (Eqs. K_up, v_1; Woodbury form), result in KR. */
+xlbomd_status xlbomd_kernel_update(xlbomd_ctx* ctx, int sys);
+
+/* a10: energy monitor (shadow free energy Omega and kinetic energy). */
+xlbomd_status xlbomd_energy(xlbomd_ctx* ctx, int sys);
+
+/* a1-a10 for every system, nsteps times (Eqs. Integration, VRL_Damp). */
+xlbomd_status xlbomd_step(xlbomd_ctx* ctx, int nsteps);
+
+/* Copy a quantity to host memory (synchronises the stream). */
+xlbomd_status xlbomd_get(xlbomd_ctx* ctx, int sys, int what, double* host_out);
+
+/* Overwrite a quantity from host memory (R, V, N, NHIST, MU). */
+xlbomd_status xlbomd_set(xlbomd_ctx* ctx, int sys, int what, const double* host_in);
+
+/* Sizes: natoms and padded orbital count of system sys. */
+xlbomd_status xlbomd_sizes(xlbomd_ctx* ctx, int sys, int* natoms, int* n_orb, int* n_pad);
+
+xlbomd_status xlbomd_clear_error(xlbomd_ctx* ctx);
+const char* xlbomd_last_error(xlbomd_ctx* ctx);
+xlbomd_status xlbomd_free(xlbomd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XLBOMD_API_H_ */

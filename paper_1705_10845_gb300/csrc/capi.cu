@@ -1,0 +1,673 @@
+// C ABI of the XL-BOMD hot path and its host-side orchestration.
+//
+// Per system the library keeps: positions, velocities, forces, the n history
+// n(t - k dt) (Eq. VRL_Damp), H0 and H[n], gamma, the expansion matrices
+// T_0..T_n and Y_0..Y_{n-1} of the recursive Fermi-operator expansion (kept
+// for the response chains), the response work matrices and the rank-m probes.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/xlbomd.h"
+#include "internal.h"
+#include "precision.h"
+
+using namespace xl;
+
+namespace {
+
+constexpr double kKB = 8.617333262e-5;
+constexpr double kAcc = 9.648533e-3;   // 1 eV/(amu A) in A/fs^2
+
+struct Sys {
+  int nat = 0, N = 0, np = 0, natp = 0, ng = 0, kp = 0;
+  double L = 0, mass = 0, nocc = 0, eta = 0;
+  // device, FP64
+  double *R = nullptr, *V = nullptr, *F = nullptr, *Z = nullptr, *nh = nullptr, *q = nullptr, *r = nullptr;
+  double *Kr = nullptr, *pot = nullptr, *potv = nullptr, *gam = nullptr, *SF = nullptr, *G4 = nullptr;
+  double *H0 = nullptr, *H = nullptr, *Dm = nullptr;
+  double *ddiag = nullptr, *dmu_diag = nullptr, *d1 = nullptr, *dvec = nullptr, *dvec_mu = nullptr;
+  double *pV = nullptr, *pW = nullptr, *scal = nullptr, *work = nullptr, *energy = nullptr;
+  MatSet mats;   // expansion matrices in the working precision
+  // host
+  double mu = 0.0;
+  bool mu_valid = false;
+  double mu_hist[3] = {0, 0, 0};
+  int n_mu_hist = 0;
+  double dmu_last = 0.0;
+  bool have_density = false;
+  int probes_used = 0;
+  double stats[5] = {0, 0, 0, 0, 0};
+  double eh[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  std::vector<double> G4h;
+};
+
+}  // namespace
+
+struct xlbomd_ctx {
+  xlbomd_params p{};
+  cudaStream_t stream = nullptr;
+  std::vector<Sys> sys;
+  double* pinned = nullptr;
+  double* cdev = nullptr;
+  int status = XLBOMD_OK;
+  std::string msg;
+  xl::Engine* eng = nullptr;
+};
+
+namespace {
+
+xlbomd_status fail(xlbomd_ctx* c, xlbomd_status st, const std::string& m) {
+  if (c) {
+    if (c->status == XLBOMD_OK) {
+      c->status = st;
+      c->msg = m;
+    }
+  }
+  return st;
+}
+
+#define CK(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(ctx, XLBOMD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CKS(call)                          \
+  do {                                     \
+    xlbomd_status s_ = (call);             \
+    if (s_ != XLBOMD_OK) return s_;        \
+  } while (0)
+
+xlbomd_status dalloc(xlbomd_ctx* ctx, double** p, size_t count) {
+  cudaError_t e = cudaMalloc((void**)p, sizeof(double) * std::max<size_t>(count, 1));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(ctx, XLBOMD_ERR_OOM, "cudaMalloc failed");
+  }
+  e = cudaMemsetAsync(*p, 0, sizeof(double) * std::max<size_t>(count, 1), ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, XLBOMD_ERR_CUDA, cudaGetErrorString(e));
+  return XLBOMD_OK;
+}
+
+ModelConst model_of(const xlbomd_params& p) {
+  ModelConst m;
+  m.eps_s = p.eps_s;
+  m.eps_p = p.eps_p;
+  for (int k = 0; k < 4; ++k) m.t0[k] = p.t0[k];
+  m.r_decay = p.r_decay;
+  m.r_cut = p.r_cut;
+  m.r_taper = p.r_taper;
+  m.U = p.hubbard_U;
+  m.k = p.coulomb_k;
+  return m;
+}
+
+double beta_of(const xlbomd_params& p) { return 1.0 / (kKB * p.Te); }
+
+// Reciprocal vectors of the Ewald sum: eta = 4/L, G = 2 pi h / L with h in a
+// half space, 0 < |G| <= 2 eta 6.07; weight w = 2 * 4 pi / V exp(-G^2/4eta^2)/G^2.
+void ewald_vectors(double L, double& eta, std::vector<double>& G4) {
+  eta = 4.0 / L;
+  const double gmax = 2.0 * eta * 6.07;
+  const int hmax = (int)std::ceil(gmax * L / (2.0 * kPi));
+  G4.clear();
+  for (int hx = -hmax; hx <= hmax; ++hx)
+    for (int hy = -hmax; hy <= hmax; ++hy)
+      for (int hz = -hmax; hz <= hmax; ++hz) {
+        const bool pos = hx > 0 || (hx == 0 && (hy > 0 || (hy == 0 && hz > 0)));
+        if (!pos) continue;
+        const double gx = 2 * kPi * hx / L, gy = 2 * kPi * hy / L, gz = 2 * kPi * hz / L;
+        const double g2 = gx * gx + gy * gy + gz * gz;
+        if (g2 > gmax * gmax) continue;
+        const double w = 2.0 * 4.0 * kPi / (L * L * L) * std::exp(-g2 / (4.0 * eta * eta)) / g2;
+        G4.push_back(gx);
+        G4.push_back(gy);
+        G4.push_back(gz);
+        G4.push_back(w);
+      }
+}
+
+xlbomd_status check(xlbomd_ctx* ctx, int sys) {
+  if (!ctx) return XLBOMD_ERR_ARG;
+  if (ctx->status != XLBOMD_OK) return (xlbomd_status)ctx->status;
+  if (sys < 0 || sys >= (int)ctx->sys.size()) return fail(ctx, XLBOMD_ERR_ARG, "system index out of range");
+  return XLBOMD_OK;
+}
+
+xlbomd_status sync_read(xlbomd_ctx* ctx, const double* dev, int count) {
+  CK(cudaMemcpyAsync(ctx->pinned, dev, sizeof(double) * count, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return XLBOMD_OK;
+}
+
+// a1-a2
+xlbomd_status build_H(xlbomd_ctx* ctx, Sys& S) {
+  cudaStream_t st = ctx->stream;
+  const ModelConst m = model_of(ctx->p);
+  CK(launch_build_H0(st, m, S.nat, S.L, S.R, S.H0, S.np));
+  if (ctx->p.coulomb_k != 0.0) {
+    CK(launch_gamma_real(st, m, S.nat, S.L, S.eta, S.R, S.gam, S.natp));
+    CK(launch_structure_factors(st, S.nat, S.ng, S.G4, S.R, S.SF, S.kp));
+    EpiF64 e;
+    e.alpha = ctx->p.coulomb_k;
+    e.E = S.gam;
+    e.lde = S.natp;
+    e.beta = 1.0;
+    CK(gemm_f64_nt(st, S.natp, S.natp, S.kp, S.SF, S.kp, S.SF, S.kp, S.gam, S.natp, e, false));
+  }
+  CK(launch_gemv(st, S.nat, S.gam, S.natp, S.nh, S.pot));
+  CK(launch_apply_potential(st, S.nat, S.np, S.H0, S.pot, S.H));
+  S.have_density = false;
+  return XLBOMD_OK;
+}
+
+// Newton-Schulz plan per level from the scalar map over t in [0, t_max(k)]:
+// level 0 starts from Y = I - S (error t^4), level k > 0 from c_k Y_{k-1}
+// with c_k minimising max |1 - c b_k / b_{k-1}|, b = 1 + t^2.
+void ns_plan(double t0max, int n, double tol, std::vector<int>& s, std::vector<double>& c) {
+  const int G = 2001;
+  std::vector<double> t(G), prev(G);
+  for (int i = 0; i < G; ++i) t[i] = t0max * i / (G - 1);
+  s.assign(n, 0);
+  c.assign(n, 1.0);
+  for (int k = 0; k < n; ++k) {
+    double e;
+    if (k == 0) {
+      e = 0.0;
+      for (int i = 0; i < G; ++i) e = std::max(e, std::fabs(1.0 - (1.0 + t[i] * t[i]) * (1.0 - t[i] * t[i])));
+    } else {
+      double rmin = 1e300, rmax = -1e300;
+      for (int i = 0; i < G; ++i) {
+        const double rho = (1.0 + t[i] * t[i]) / (1.0 + prev[i] * prev[i]);
+        rmin = std::min(rmin, rho);
+        rmax = std::max(rmax, rho);
+      }
+      c[k] = 2.0 / (rmin + rmax);
+      e = (rmax - rmin) / (rmax + rmin);
+    }
+    int it = 0;
+    double err = e;
+    while (err > tol && it < 10) {
+      err = err * err;
+      ++it;
+    }
+    s[k] = it;
+    prev = t;
+    for (int i = 0; i < G; ++i) t[i] = 2.0 * t[i] / (1.0 + t[i] * t[i]);
+  }
+}
+
+// a3-a6
+xlbomd_status density(xlbomd_ctx* ctx, Sys& S, bool with_forces) {
+  cudaStream_t st = ctx->stream;
+  const xlbomd_params& p = ctx->p;
+  const double beta = beta_of(p);
+  const int n = p.n_sq;
+  const double sc = beta / std::ldexp(1.0, n + 1);
+  Engine& E = *ctx->eng;
+
+  CK(launch_gershgorin(st, S.N, S.np, S.H, S.work));
+  CKS(sync_read(ctx, S.work, 2));
+  const double glo = ctx->pinned[0], ghi = ctx->pinned[1];
+
+  double mu;
+  if (S.mu_valid) {
+    mu = S.mu;
+    if (S.n_mu_hist >= 3)
+      mu = 3.0 * S.mu_hist[0] - 3.0 * S.mu_hist[1] + S.mu_hist[2];
+    else if (S.n_mu_hist == 2)
+      mu = 2.0 * S.mu_hist[0] - S.mu_hist[1];
+  } else {
+    mu = 0.5 * (glo + ghi);
+  }
+  double blo = glo - 1.0, bhi = ghi + 1.0;   // bracket of the root of Tr D(mu) = N_occ
+  const double tol_ns = (p.prec == XLBOMD_FP64) ? 1e-16 : 1e-8;
+  std::vector<int> plan_s;
+  std::vector<double> plan_c;
+  double dmu = 0.0;
+  int pass = 0;
+  for (;; ++pass) {
+    if (pass >= p.mu_max_iter) return fail(ctx, XLBOMD_ERR_NOT_CONVERGED, "chemical potential did not converge");
+    const double t0max = sc * std::max(std::fabs(ghi - mu), std::fabs(mu - glo));
+    if (!(t0max < 1.0)) return fail(ctx, XLBOMD_ERR_SPECTRUM, "|beta (e - mu)| / 2^(n+1) >= 1");
+    ns_plan(t0max, n, tol_ns, plan_s, plan_c);
+    CK(E.foe(st, S.mats, S.H, S.N, mu, sc, plan_s, plan_c, S.stats));
+    // mu chain: T1_0 = +sc I, full last level
+    CK(E.chain(st, S.mats, S.dvec_mu, S.N, true, S.dmu_diag, S.stats));
+    CK(E.trace_tn(st, S.mats, S.N, S.scal));          // scal[0] = sum_i T_n,ii
+    CK(launch_sum(st, S.N, S.dmu_diag, S.scal + 1));    // scal[1] = sum_i dT_n,ii/dmu
+    CKS(sync_read(ctx, S.scal, 2));
+    const double trD = 0.5 * (S.N + ctx->pinned[0]);
+    const double trDmu = 0.5 * ctx->pinned[1];
+    if (!std::isfinite(trD) || !std::isfinite(trDmu))
+      return fail(ctx, XLBOMD_ERR_NOT_CONVERGED, "non-finite trace in the expansion");
+    if (trD < S.nocc)
+      blo = std::max(blo, mu);
+    else
+      bhi = std::min(bhi, mu);
+    dmu = (trDmu > 0.0) ? (S.nocc - trD) / trDmu : 0.0;
+    S.stats[0] += 1;
+    if (std::fabs(dmu) * beta < p.mu_tol) break;
+    double next = mu + dmu;
+    if (!(trDmu > 0.0) || !(next > blo && next < bhi)) next = 0.5 * (blo + bhi);
+    mu = next;
+  }
+  // first-order correction D(mu + dmu) = D(mu) + dmu dD/dmu
+  S.dmu_last = dmu;
+  S.mu = mu + dmu;
+  S.mu_valid = true;
+  S.mu_hist[2] = S.mu_hist[1];
+  S.mu_hist[1] = S.mu_hist[0];
+  S.mu_hist[0] = S.mu;
+  S.n_mu_hist = std::min(S.n_mu_hist + 1, 3);
+  CK(E.density_out(st, S.mats, S.N, dmu, S.dmu_diag, S.ddiag, S.Dm));
+  CK(launch_charges(st, S.nat, S.ddiag, S.Z, S.nh, S.q, S.r));
+  if (with_forces) {
+    CK(launch_forces(st, model_of(p), S.nat, S.L, S.eta, S.ng, S.G4, S.R, S.Dm, S.np, S.q, S.nh, S.F, S.work));
+  }
+  S.have_density = true;
+  return XLBOMD_OK;
+}
+
+// a7: one probe.  H1 = diag(gamma v) on orbitals, T1_0 = -sc H1.
+xlbomd_status response(xlbomd_ctx* ctx, Sys& S, const double* v, double* w) {
+  cudaStream_t st = ctx->stream;
+  const double sc = beta_of(ctx->p) / std::ldexp(1.0, ctx->p.n_sq + 1);
+  CK(launch_gemv(st, S.nat, S.gam, S.natp, v, S.potv));
+  CK(launch_expand_potential(st, S.nat, S.np, -sc, S.potv, S.dvec));
+  CK(ctx->eng->chain(st, S.mats, S.dvec, S.N, false, S.d1, S.stats));
+  CK(launch_response_finish(st, S.nat, S.N, S.d1, S.dmu_diag, S.scal + 4, w));
+  return XLBOMD_OK;
+}
+
+// a7-a8
+xlbomd_status kernel_update(xlbomd_ctx* ctx, Sys& S) {
+  cudaStream_t st = ctx->stream;
+  const xlbomd_params& p = ctx->p;
+  int m = 0;
+  for (int i = 0; i < p.rank_m; ++i) {
+    CK(launch_kernel_vec(st, 0, S.nat, i, p.kernel_c, S.r, S.pV, S.pW, nullptr, S.scal + 8));
+    CKS(sync_read(ctx, S.scal + 8, 1));
+    if (ctx->pinned[0] != 1.0) break;
+    CKS(response(ctx, S, S.pV + (size_t)i * S.nat, S.pW + (size_t)i * S.nat));
+    m = i + 1;
+  }
+  CK(launch_kernel_vec(st, 1, S.nat, m, p.kernel_c, S.r, S.pV, S.pW, S.Kr, S.scal + 8));
+  S.probes_used = m;
+  S.stats[2] = m;
+  return XLBOMD_OK;
+}
+
+// a10
+xlbomd_status energy(xlbomd_ctx* ctx, Sys& S) {
+  cudaStream_t st = ctx->stream;
+  CK(launch_frob_dot(st, S.N, S.np, S.Dm, S.H0, S.work, S.energy + 0));
+  CK(launch_energy_vec(st, S.nat, S.q, S.nh, S.pot, S.V, S.mass, S.energy + 1));
+  CK(ctx->eng->entropy(st, S.mats, S.N, beta_of(ctx->p), ctx->p.n_sq, S.mu, S.dmu_last, S.Dm, S.H, S.work,
+                       S.energy + 3));
+  CKS(sync_read(ctx, S.energy, 4));
+  const double band = 2.0 * ctx->pinned[0], coul = ctx->pinned[1], ke = ctx->pinned[2];
+  const double ent = -2.0 * kKB * ctx->p.Te * ctx->pinned[3];
+  const double om = band + coul + ent;
+  const double out[6] = {om, band, coul, ent, ke, om + ke};
+  std::memcpy(S.eh, out, sizeof(out));
+  return XLBOMD_OK;
+}
+
+xlbomd_status scf(xlbomd_ctx* ctx, Sys& S) {
+  cudaStream_t st = ctx->stream;
+  const xlbomd_params& p = ctx->p;
+  for (int it = 0; it < p.scf_max_iter; ++it) {
+    CK(launch_gemv(st, S.nat, S.gam, S.natp, S.nh, S.pot));
+    CK(launch_apply_potential(st, S.nat, S.np, S.H0, S.pot, S.H));
+    CKS(density(ctx, S, false));
+    CK(launch_absmax(st, S.nat, S.r, S.scal + 9));
+    CKS(sync_read(ctx, S.scal + 9, 1));
+    const double res = ctx->pinned[0];
+    if (!std::isfinite(res) || res > 1e3) return fail(ctx, XLBOMD_ERR_DIVERGED, "t0 SCF diverged");
+    if (res < p.scf_tol) {
+      CK(launch_fill_history(st, S.nat, p.kmax, S.nh));
+      CK(launch_forces(st, model_of(p), S.nat, S.L, S.eta, S.ng, S.G4, S.R, S.Dm, S.np, S.q, S.nh, S.F, S.work));
+      return kernel_update(ctx, S);
+    }
+    CK(launch_axpy(st, S.nat, p.mix_alpha, S.r, S.nh));
+  }
+  return fail(ctx, XLBOMD_ERR_NOT_CONVERGED, "t0 SCF did not converge");
+}
+
+xlbomd_status md_step(xlbomd_ctx* ctx, Sys& S, bool do_energy) {
+  cudaStream_t st = ctx->stream;
+  const xlbomd_params& p = ctx->p;
+  const double minv = kAcc / S.mass;
+  CK(launch_verlet_first(st, S.nat, S.L, p.dt, minv, S.R, S.V, S.F, S.nh, p.kmax, S.Kr, p.kappa, p.alpha,
+                         ctx->cdev));
+  CKS(build_H(ctx, S));
+  CKS(density(ctx, S, true));
+  CKS(kernel_update(ctx, S));
+  CK(launch_verlet_second(st, S.nat, p.dt, minv, S.V, S.F));
+  CK(launch_absmax(st, S.nat, S.r, S.scal + 9));
+  if (do_energy) CKS(energy(ctx, S));
+  CKS(sync_read(ctx, S.scal + 9, 1));
+  if (!(ctx->pinned[0] <= p.diverge_tol)) return fail(ctx, XLBOMD_ERR_DIVERGED, "residual |q - n| too large");
+  S.stats[4] += 1;
+  return XLBOMD_OK;
+}
+
+void free_sys(Sys& S) {
+  double** ptrs[] = {&S.R,  &S.V,        &S.F,    &S.Z,  &S.nh,  &S.q,    &S.r,     &S.Kr,    &S.pot,
+                     &S.potv, &S.gam,    &S.SF,   &S.G4, &S.H0,  &S.H,    &S.Dm,    &S.ddiag, &S.dmu_diag,
+                     &S.d1, &S.dvec,     &S.dvec_mu, &S.pV, &S.pW, &S.scal, &S.work, &S.energy};
+  for (double** p : ptrs) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  free_matset(S.mats);
+}
+
+}  // namespace
+
+extern "C" {
+
+void xlbomd_default_params(xlbomd_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->eps_s = -8.0;
+  p->eps_p = -3.0;
+  p->t0[0] = -2.5;
+  p->t0[1] = -1.8;
+  p->t0[2] = 1.2;
+  p->t0[3] = -0.6;
+  p->r_decay = 1.2;
+  p->r_cut = 5.0;
+  p->r_taper = 4.5;
+  p->hubbard_U = 6.0;
+  p->coulomb_k = 14.399645;
+  p->Te = 1000.0;
+  p->n_sq = 10;
+  p->dt = 0.25;
+  p->kappa = 1.82;
+  p->alpha = 0.018;
+  const double c5[6] = {-6, 14, -8, -3, 4, -1};
+  for (int k = 0; k < 6; ++k) p->c[k] = c5[k];
+  p->kmax = 5;
+  p->rank_m = 2;
+  p->mix_alpha = 0.06;
+  p->kernel_c = 1.0 - 1.0 / 0.06;
+  p->scf_tol = 1e-10;
+  p->scf_max_iter = 2000;
+  p->mu_tol = 1e-9;
+  p->mu_max_iter = 60;
+  p->diverge_tol = 1.0;
+  p->prec = XLBOMD_FP64;
+  p->energy_every = 0;
+}
+
+xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* systems, int nsys, void* cuda_stream,
+                          xlbomd_ctx** out) {
+  if (!params || !systems || !out || nsys < 1) return XLBOMD_ERR_ARG;
+  *out = nullptr;
+  const xlbomd_params& p = *params;
+  if (p.n_sq < 1 || p.n_sq > 40 || p.kmax < 1 || p.kmax > 7 || p.rank_m < 0 || p.rank_m > kMaxRank ||
+      p.kernel_c == 1.0 || !(p.Te > 0) || !(p.dt > 0) || p.mu_max_iter < 1)
+    return XLBOMD_ERR_ARG;
+  if (p.prec != XLBOMD_FP64 && p.prec != XLBOMD_FP16x3 && p.prec != XLBOMD_BF16x3) return XLBOMD_ERR_ARG;
+  for (int i = 0; i < nsys; ++i) {
+    const xlbomd_system& s = systems[i];
+    if (s.natoms < 1 || !(s.box_L > p.r_cut) || !s.R || !s.V || !s.Z || !(s.mass > 0)) return XLBOMD_ERR_ARG;
+  }
+  xlbomd_ctx* ctx = new xlbomd_ctx();
+  ctx->p = p;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  ctx->eng = make_engine(p.prec);
+  if (!ctx->eng) {
+    delete ctx;
+    return XLBOMD_ERR_UNSUPPORTED;
+  }
+  auto bail = [&](xlbomd_status st) {
+    xlbomd_free(ctx);
+    return st;
+  };
+  if (cudaMallocHost((void**)&ctx->pinned, 64 * sizeof(double)) != cudaSuccess) return bail(XLBOMD_ERR_OOM);
+  if (dalloc(ctx, &ctx->cdev, 8) != XLBOMD_OK) return bail(XLBOMD_ERR_OOM);
+  if (cudaMemcpy(ctx->cdev, p.c, sizeof(double) * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(XLBOMD_ERR_CUDA);
+  ctx->sys.resize(nsys);
+  const double sc = beta_of(p) / std::ldexp(1.0, p.n_sq + 1);
+  for (int i = 0; i < nsys; ++i) {
+    const xlbomd_system& s = systems[i];
+    Sys& S = ctx->sys[i];
+    S.nat = s.natoms;
+    S.N = 4 * s.natoms;
+    S.np = (S.N + 127) / 128 * 128;
+    S.natp = (S.nat + 63) / 64 * 64;
+    S.L = s.box_L;
+    S.mass = s.mass;
+    double zs = 0;
+    for (int a = 0; a < S.nat; ++a) zs += s.Z[a];
+    S.nocc = 0.5 * zs;
+    ewald_vectors(S.L, S.eta, S.G4h);
+    S.ng = (int)(S.G4h.size() / 4);
+    S.kp = (2 * S.ng + 15) / 16 * 16;
+    const size_t nat = S.nat, np2 = (size_t)S.np * S.np;
+    xlbomd_status st = XLBOMD_OK;
+    auto A = [&](double** ptr, size_t cnt) {
+      if (st == XLBOMD_OK) st = dalloc(ctx, ptr, cnt);
+    };
+    A(&S.R, 3 * nat);
+    A(&S.V, 3 * nat);
+    A(&S.F, 3 * nat);
+    A(&S.Z, nat);
+    A(&S.nh, (size_t)(p.kmax + 1) * nat);
+    A(&S.q, nat);
+    A(&S.r, nat);
+    A(&S.Kr, nat);
+    A(&S.pot, nat);
+    A(&S.potv, nat);
+    A(&S.gam, (size_t)S.natp * S.natp);
+    A(&S.SF, (size_t)S.natp * S.kp);
+    A(&S.G4, std::max<size_t>(S.G4h.size(), 4));
+    A(&S.H0, np2);
+    A(&S.H, np2);
+    A(&S.Dm, np2);
+    A(&S.ddiag, S.np);
+    A(&S.dmu_diag, S.np);
+    A(&S.d1, S.np);
+    A(&S.dvec, S.np);
+    A(&S.dvec_mu, S.np);
+    A(&S.pV, (size_t)(kMaxRank + 1) * nat);
+    A(&S.pW, (size_t)(kMaxRank + 1) * nat);
+    A(&S.scal, 64);
+    A(&S.work, std::max<size_t>({(size_t)4 * S.ng + 16, (size_t)2 * S.N + 16, (size_t)4096}));
+    A(&S.energy, 8);
+    if (st != XLBOMD_OK) return bail(st);
+    if (alloc_matset(S.mats, p.prec, S.np, p.n_sq) != cudaSuccess) return bail(XLBOMD_ERR_OOM);
+    // R wrapped into [0, L)
+    std::vector<double> Rw(3 * nat);
+    for (size_t a = 0; a < 3 * nat; ++a) Rw[a] = s.R[a] - S.L * std::floor(s.R[a] / S.L);
+    if (cudaMemcpy(S.R, Rw.data(), sizeof(double) * 3 * nat, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(S.V, s.V, sizeof(double) * 3 * nat, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(S.Z, s.Z, sizeof(double) * nat, cudaMemcpyHostToDevice) != cudaSuccess ||
+        (S.ng && cudaMemcpy(S.G4, S.G4h.data(), sizeof(double) * S.G4h.size(), cudaMemcpyHostToDevice) != cudaSuccess))
+      return bail(XLBOMD_ERR_CUDA);
+    std::vector<double> dmu(S.np, 0.0);
+    for (int a = 0; a < S.N; ++a) dmu[a] = sc;
+    if (cudaMemcpy(S.dvec_mu, dmu.data(), sizeof(double) * S.np, cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(XLBOMD_ERR_CUDA);
+    if (build_H(ctx, S) != XLBOMD_OK) return bail((xlbomd_status)ctx->status);
+  }
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return bail(XLBOMD_ERR_CUDA);
+  *out = ctx;
+  return XLBOMD_OK;
+}
+
+xlbomd_status xlbomd_scf(xlbomd_ctx* ctx, int sys) {
+  if (!ctx) return XLBOMD_ERR_ARG;
+  const int lo = sys < 0 ? 0 : sys, hi = sys < 0 ? (int)ctx->sys.size() : sys + 1;
+  for (int i = lo; i < hi; ++i) {
+    CKS(check(ctx, i));
+    CKS(scf(ctx, ctx->sys[i]));
+  }
+  return XLBOMD_OK;
+}
+
+xlbomd_status xlbomd_build_H(xlbomd_ctx* ctx, int sys) {
+  CKS(check(ctx, sys));
+  return build_H(ctx, ctx->sys[sys]);
+}
+
+xlbomd_status xlbomd_density(xlbomd_ctx* ctx, int sys) {
+  CKS(check(ctx, sys));
+  return density(ctx, ctx->sys[sys], true);
+}
+
+xlbomd_status xlbomd_response(xlbomd_ctx* ctx, int sys, const double* v_dev, double* w_dev) {
+  CKS(check(ctx, sys));
+  if (!v_dev || !w_dev) return fail(ctx, XLBOMD_ERR_ARG, "null probe pointer");
+  if (!ctx->sys[sys].have_density) return fail(ctx, XLBOMD_ERR_ARG, "xlbomd_density must run first");
+  return response(ctx, ctx->sys[sys], v_dev, w_dev);
+}
+
+xlbomd_status xlbomd_kernel_update(xlbomd_ctx* ctx, int sys) {
+  CKS(check(ctx, sys));
+  if (!ctx->sys[sys].have_density) return fail(ctx, XLBOMD_ERR_ARG, "xlbomd_density must run first");
+  return kernel_update(ctx, ctx->sys[sys]);
+}
+
+xlbomd_status xlbomd_energy(xlbomd_ctx* ctx, int sys) {
+  CKS(check(ctx, sys));
+  if (!ctx->sys[sys].have_density) return fail(ctx, XLBOMD_ERR_ARG, "xlbomd_density must run first");
+  return energy(ctx, ctx->sys[sys]);
+}
+
+xlbomd_status xlbomd_step(xlbomd_ctx* ctx, int nsteps) {
+  if (!ctx || nsteps < 0) return XLBOMD_ERR_ARG;
+  for (int t = 0; t < nsteps; ++t)
+    for (int i = 0; i < (int)ctx->sys.size(); ++i) {
+      CKS(check(ctx, i));
+      Sys& S = ctx->sys[i];
+      const bool e = ctx->p.energy_every > 0 && ((int)S.stats[4] + 1) % ctx->p.energy_every == 0;
+      CKS(md_step(ctx, S, e));
+    }
+  return XLBOMD_OK;
+}
+
+xlbomd_status xlbomd_get(xlbomd_ctx* ctx, int sys, int what, double* host_out) {
+  CKS(check(ctx, sys));
+  if (!host_out) return fail(ctx, XLBOMD_ERR_ARG, "null output");
+  Sys& S = ctx->sys[sys];
+  const size_t nat = S.nat;
+  auto cp = [&](const double* d, size_t cnt) -> xlbomd_status {
+    CK(cudaMemcpyAsync(host_out, d, sizeof(double) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return XLBOMD_OK;
+  };
+  auto cp2d = [&](const double* d, int rows, int ld) -> xlbomd_status {
+    CK(cudaMemcpy2DAsync(host_out, sizeof(double) * rows, d, sizeof(double) * ld, sizeof(double) * rows, rows,
+                         cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return XLBOMD_OK;
+  };
+  switch (what) {
+    case XLBOMD_Q: return cp(S.q, nat);
+    case XLBOMD_N: return cp(S.nh, nat);
+    case XLBOMD_NHIST: return cp(S.nh, (size_t)(ctx->p.kmax + 1) * nat);
+    case XLBOMD_F: return cp(S.F, 3 * nat);
+    case XLBOMD_R: return cp(S.R, 3 * nat);
+    case XLBOMD_V: return cp(S.V, 3 * nat);
+    case XLBOMD_KR: return cp(S.Kr, nat);
+    case XLBOMD_RES: return cp(S.r, nat);
+    case XLBOMD_ENERGY: std::memcpy(host_out, S.eh, 6 * sizeof(double)); return XLBOMD_OK;
+    case XLBOMD_MU: host_out[0] = S.mu; return XLBOMD_OK;
+    case XLBOMD_D: return cp2d(S.Dm, S.N, S.np);
+    case XLBOMD_H: return cp2d(S.H, S.N, S.np);
+    case XLBOMD_GAMMA: return cp2d(S.gam, S.nat, S.natp);
+    case XLBOMD_STATS: std::memcpy(host_out, S.stats, 5 * sizeof(double)); return XLBOMD_OK;
+    case XLBOMD_PROBES: {
+      CK(cudaMemcpyAsync(host_out, S.pV, sizeof(double) * ctx->p.rank_m * nat, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(host_out + ctx->p.rank_m * nat, S.pW, sizeof(double) * ctx->p.rank_m * nat,
+                         cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      return XLBOMD_OK;
+    }
+    default: return fail(ctx, XLBOMD_ERR_ARG, "unknown quantity");
+  }
+}
+
+xlbomd_status xlbomd_set(xlbomd_ctx* ctx, int sys, int what, const double* host_in) {
+  CKS(check(ctx, sys));
+  if (!host_in) return fail(ctx, XLBOMD_ERR_ARG, "null input");
+  Sys& S = ctx->sys[sys];
+  const size_t nat = S.nat;
+  switch (what) {
+    case XLBOMD_R: {
+      std::vector<double> Rw(3 * nat);
+      for (size_t a = 0; a < 3 * nat; ++a) Rw[a] = host_in[a] - S.L * std::floor(host_in[a] / S.L);
+      CK(cudaMemcpyAsync(S.R, Rw.data(), sizeof(double) * 3 * nat, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      S.have_density = false;
+      return XLBOMD_OK;
+    }
+    case XLBOMD_V:
+      CK(cudaMemcpyAsync(S.V, host_in, sizeof(double) * 3 * nat, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      return XLBOMD_OK;
+    case XLBOMD_N:
+      for (int k = 0; k <= ctx->p.kmax; ++k)
+        CK(cudaMemcpyAsync(S.nh + k * nat, host_in, sizeof(double) * nat, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      S.have_density = false;
+      return XLBOMD_OK;
+    case XLBOMD_NHIST:
+      CK(cudaMemcpyAsync(S.nh, host_in, sizeof(double) * (ctx->p.kmax + 1) * nat, cudaMemcpyHostToDevice,
+                         ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      S.have_density = false;
+      return XLBOMD_OK;
+    case XLBOMD_MU:
+      S.mu = host_in[0];
+      S.mu_valid = true;
+      S.n_mu_hist = 0;
+      return XLBOMD_OK;
+    default: return fail(ctx, XLBOMD_ERR_ARG, "quantity cannot be set");
+  }
+}
+
+xlbomd_status xlbomd_sizes(xlbomd_ctx* ctx, int sys, int* natoms, int* n_orb, int* n_pad) {
+  if (!ctx || sys < 0 || sys >= (int)ctx->sys.size()) return XLBOMD_ERR_ARG;
+  if (natoms) *natoms = ctx->sys[sys].nat;
+  if (n_orb) *n_orb = ctx->sys[sys].N;
+  if (n_pad) *n_pad = ctx->sys[sys].np;
+  return XLBOMD_OK;
+}
+
+xlbomd_status xlbomd_clear_error(xlbomd_ctx* ctx) {
+  if (!ctx) return XLBOMD_ERR_ARG;
+  ctx->status = XLBOMD_OK;
+  ctx->msg.clear();
+  cudaGetLastError();
+  return XLBOMD_OK;
+}
+
+const char* xlbomd_last_error(xlbomd_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->msg.c_str();
+}
+
+xlbomd_status xlbomd_free(xlbomd_ctx* ctx) {
+  if (!ctx) return XLBOMD_ERR_ARG;
+  if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  for (Sys& S : ctx->sys) free_sys(S);
+  if (ctx->cdev) cudaFree(ctx->cdev);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  delete ctx->eng;
+  delete ctx;
+  return XLBOMD_OK;
+}
+
+}  // extern "C"

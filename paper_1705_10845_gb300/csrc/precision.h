@@ -1,0 +1,82 @@
+// Precision engines of the expansion and response chains.
+//
+// The orchestration (capi.cu) is written once; an Engine runs the matrix
+// recursions in one arithmetic: plain FP64 products, or split-precision
+// tensor-core products (hi/lo 16-bit operands, FP32 accumulation).
+#pragma once
+#include <vector>
+
+#include "internal.h"
+
+namespace xl {
+
+// Matrices of one system in the working precision.  In the FP64 engine each
+// logical matrix is a double array; the split engines keep an FP32 value
+// array plus hi/lo 16-bit operand arrays with a power-of-two scale.
+struct SplitMat {
+  float* f = nullptr;        // value (np x np)
+  uint16_t* hi = nullptr;    // operand hi part of value * scale
+  uint16_t* lo = nullptr;    // operand lo part
+  float* scale = nullptr;    // device scalar
+  unsigned* amax = nullptr;  // device scalar: float bits of max |value|
+};
+
+struct MatSet {
+  int prec = 0, np = 0, n = 0;
+  // FP64 engine
+  std::vector<double*> T, Y;
+  double *S = nullptr, *Q = nullptr, *Yw = nullptr, *G = nullptr, *A1 = nullptr, *Mt = nullptr;
+  double *T1a = nullptr, *T1b = nullptr, *Tmu = nullptr;
+  // split engines
+  std::vector<SplitMat> sT, sY;
+  SplitMat sS, sQ, sYw, sG, sA1, sMt, sT1a, sT1b, sTmu;
+  void* tc_plan = nullptr;   // tensor-map cache of the tensor-core engine
+};
+
+cudaError_t alloc_matset(MatSet& m, int prec, int np, int n);
+void free_matset(MatSet& m);
+
+class Engine {
+ public:
+  virtual ~Engine() {}
+  // T_0 = -sc (H - mu I); n levels T_{k+1} = 2 T_k Y_k, Y_k = (I + T_k^2)^-1 by
+  // plan.s[k] Newton-Schulz steps (2I - Y B) Y from Y = I - S (k = 0) or c_k Y_{k-1}.
+  virtual cudaError_t foe(cudaStream_t s, MatSet& m, const double* H, int N, double mu, double sc,
+                          const std::vector<int>& ns, const std::vector<double>& nc, double* stats) = 0;
+  // Response chain with diagonal T1_0 = diag(dvec): T1_{k+1} = Y_k (2 T1_k - A1 T_{k+1}),
+  // A1 = T_k T1_k + T1_k T_k.  out_diag = diag(T1_n); full_last keeps T1_n in Tmu.
+  virtual cudaError_t chain(cudaStream_t s, MatSet& m, const double* dvec, int N, bool full_last,
+                            double* out_diag, double* stats) = 0;
+  // out[0] = sum_{i<N} (T_n)_ii
+  virtual cudaError_t trace_tn(cudaStream_t s, MatSet& m, int N, double* out) = 0;
+  // ddiag = 1 + diag(T_n) + dmu dmu_diag (= 2 D_aa);  D = (I + T_n)/2 + dmu Tmu / 2 (FP64)
+  virtual cudaError_t density_out(cudaStream_t s, MatSet& m, int N, double dmu, const double* dmu_diag,
+                                  double* ddiag, double* D) = 0;
+  // out[0] = sum_i s(f_i) (electronic entropy / kB of the occupations of D)
+  virtual cudaError_t entropy(cudaStream_t s, MatSet& m, int N, double beta, int n_sq, double mu, double dmu,
+                              const double* D, const double* H, double* work, double* out) = 0;
+};
+
+Engine* make_engine(int prec);
+
+// split-precision engines (engine_split.cu)
+Engine* make_split_engine(int prec);
+cudaError_t alloc_matset_split(MatSet& m);
+void free_matset_split(MatSet& m);
+
+// FP64 eigenvalue-free entropy (entropy.cu)
+cudaError_t launch_entropy_f64(cudaStream_t s, MatSet& m, int N, double beta, int n_sq, double mu, double dmu,
+                               const double* D, const double* H, double* work, double* out);
+
+// misc FP64 launchers (foe_kernels.cu)
+cudaError_t launch_expand_potential(cudaStream_t s, int nat, int np, double scale, const double* pot, double* dvec);
+cudaError_t launch_response_finish(cudaStream_t s, int nat, int N, const double* d1, const double* dmu_diag,
+                                   double* scal, double* w);
+cudaError_t launch_absmax(cudaStream_t s, int n, const double* x, double* out);
+cudaError_t launch_fill_history(cudaStream_t s, int nat, int kmax, double* nh);
+cudaError_t launch_axpy(cudaStream_t s, int n, double a, const double* x, double* y);
+cudaError_t launch_diag_sum(cudaStream_t s, int n, int np, const double* X, double* out);
+cudaError_t launch_density_out_f64(cudaStream_t s, int N, int np, const double* Tn, const double* Tmu, double dmu,
+                                   double* ddiag, double* D);
+
+}  // namespace xl

@@ -1,0 +1,194 @@
+"""GPU parity of the plain-FP64 path against the oracle (through the C ABI).
+
+Tolerances (FP64 path): charges 1e-9 e, energies 1e-8 relative, forces
+1e-8 eV/A, Hamiltonian and density elements 1e-10.  Inputs are seeded
+synthetic systems; the 37-atom case has a padded orbital count (148 -> 256).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+ALPHA_MIX = 0.06
+
+
+@pytest.fixture(scope="module")
+def X():
+    import paper_1705_10845_gb300 as X
+    X.build.build()
+    X.load()
+    return X
+
+
+def sysdict(s):
+    return dict(natoms=s.natoms, L=s.L, R=s.R, V=s.V, Z=s.Z, mass=s.mass)
+
+
+def model_params(X, **kw):
+    p = X.default_params(mix_alpha=ALPHA_MIX, kernel_c=1.0 - 1.0 / ALPHA_MIX, **kw)
+    return p
+
+
+def oracle_model(p):
+    return O.Model(Te=p.Te, n_sq=p.n_sq)
+
+
+CASES = [
+    ("tiny24", lambda: synth.make_system(24, 1705, L=7.0)),
+    ("ragged37", lambda: synth.make_system(37, 11)),
+    ("small8", lambda: synth.make_system(8, 42, L=7.0)),
+]
+
+
+def random_n(nat, seed, scale=0.02):
+    rng = np.random.default_rng(seed)
+    n = rng.normal(scale=scale, size=nat)
+    return n - n.mean()
+
+
+@pytest.mark.parametrize("name,make", CASES)
+def test_build_H_and_gamma(X, name, make):
+    s = make()
+    p = model_params(X)
+    m = oracle_model(p)
+    n = random_n(s.natoms, 1)
+    with X.Context(p, [sysdict(s)]) as ctx:
+        ctx.set(0, X.N, n)
+        ctx.build_H(0)
+        H = ctx.get(0, X.H)
+        G = ctx.get(0, X.GAMMA)
+    Gref = O.build_gamma(s.R, s.L, m)
+    Href = O.hamiltonian(O.build_H0(s.R, s.L, m), Gref, n)
+    assert np.max(np.abs(G - Gref)) < 1e-10 * np.max(np.abs(Gref))
+    assert np.max(np.abs(H - Href)) < 1e-11
+
+
+@pytest.mark.parametrize("name,make", CASES)
+def test_density_charges_forces_energy(X, name, make):
+    s = make()
+    p = model_params(X)
+    m = oracle_model(p)
+    n = random_n(s.natoms, 2)
+    ref = O.evaluate(s.R, s.L, s.Z, n, m, None, with_kernel=False)
+    with X.Context(p, [sysdict(s)]) as ctx:
+        ctx.set(0, X.N, n)
+        ctx.set(0, X.MU, [ref.dens.mu + 0.02])
+        ctx.build_H(0)
+        ctx.density(0)
+        ctx.energy(0)
+        q, D, F, mu = ctx.get(0, X.Q), ctx.get(0, X.D), ctx.get(0, X.F), ctx.get(0, X.MU)[0]
+        E = ctx.get(0, X.ENERGY)
+    assert abs(mu - ref.dens.mu) < 1e-9
+    assert np.max(np.abs(D - ref.dens.D)) < 1e-10
+    assert np.max(np.abs(q - ref.q)) < 1e-9
+    assert np.max(np.abs(F - ref.F)) < 1e-8
+    parts = ref.parts
+    assert E[1] == pytest.approx(parts["band"], rel=1e-10, abs=1e-9)
+    assert E[2] == pytest.approx(parts["coulomb"], rel=1e-9, abs=1e-9)
+    assert E[3] == pytest.approx(parts["entropy"], rel=1e-7, abs=1e-8)
+    assert E[0] == pytest.approx(ref.Omega, rel=1e-8)
+
+
+@pytest.mark.parametrize("name,make", CASES[:2])
+def test_response_and_kernel(X, name, make):
+    import torch
+    s = make()
+    p = model_params(X, rank_m=4)
+    m = oracle_model(p)
+    n = random_n(s.natoms, 3)
+    xl = O.XLParams(rank_m=4, kernel_c=p.kernel_c)
+    ref = O.evaluate(s.R, s.L, s.Z, n, m, xl)
+    rng = np.random.default_rng(4)
+    v = rng.normal(size=s.natoms)
+    v -= v.mean()
+    v /= np.linalg.norm(v)
+    wref = O.response(ref.dens, ref.gamma, v)
+    with X.Context(p, [sysdict(s)]) as ctx:
+        ctx.set(0, X.N, n)
+        ctx.set(0, X.MU, [ref.dens.mu])
+        ctx.build_H(0)
+        ctx.density(0)
+        vd = torch.tensor(v, dtype=torch.float64, device="cuda")
+        wd = torch.zeros_like(vd)
+        ctx.response(0, vd.data_ptr(), wd.data_ptr())
+        torch.cuda.synchronize()
+        w = wd.cpu().numpy()
+        ctx.kernel_update(0)
+        Kr = ctx.get(0, X.KR)
+        probes = ctx.get(0, X.PROBES)
+    assert np.max(np.abs(w - wref)) < 1e-8 * max(1.0, np.max(np.abs(wref)))
+    assert np.max(np.abs(Kr - ref.Kr)) < 1e-9
+    Vref = np.array(ref.V)
+    assert np.max(np.abs(probes[0][:len(Vref)] - Vref)) < 1e-8
+
+
+def test_scf_ground_state(X):
+    s = synth.make_system(24, 1705, L=7.0)
+    p = model_params(X)
+    m = oracle_model(p)
+    n_ref, _ = O.scf(s.R, s.L, s.Z, m, ALPHA_MIX, tol=p.scf_tol)
+    with X.Context(p, [sysdict(s)]) as ctx:
+        ctx.scf(0)
+        n = ctx.get(0, X.N)
+        hist = ctx.get(0, X.NHIST)
+    assert np.max(np.abs(n - n_ref)) < 1e-9
+    assert np.allclose(hist, hist[0][None, :])
+
+
+def test_trajectory_matches_oracle(X):
+    s = synth.make_system(24, 1705, L=7.0)
+    p = model_params(X)
+    m = oracle_model(p)
+    xl = O.XLParams(rank_m=p.rank_m, kernel_c=p.kernel_c, mix_alpha=ALPHA_MIX)
+    st, ev = O.md_init(s.R, s.V, s.L, s.Z, s.mass, m, xl)
+    with X.Context(p, [sysdict(s)]) as ctx:
+        ctx.set(0, X.N, st.nhist[0])
+        ctx.set(0, X.MU, [ev.dens.mu])
+        ctx.build_H(0)
+        ctx.density(0)
+        ctx.kernel_update(0)
+        assert np.max(np.abs(ctx.get(0, X.KR) - st.Kr)) < 1e-9
+        for k in range(20):
+            st, ev = O.md_step(st, s.L, s.Z, s.mass, m, xl)
+            ctx.step(1)
+            ctx.energy(0)
+            R = ctx.get(0, X.R)
+            dR = O.min_image(R - st.R, s.L)
+            assert np.max(np.abs(dR)) < 1e-9, k
+            assert np.max(np.abs(ctx.get(0, X.Q) - ev.q)) < 1e-9, k
+            assert np.max(np.abs(ctx.get(0, X.N) - st.nhist[0])) < 1e-9, k
+            E = ctx.get(0, X.ENERGY)
+            assert E[0] == pytest.approx(ev.Omega, rel=1e-8), k
+
+
+def test_single_atom_edge_case(X):
+    p = model_params(X)
+    s = dict(natoms=1, L=7.0, R=np.array([[1.0, 2.0, 3.0]]), V=np.zeros((1, 3)), Z=np.array([4.0]), mass=12.0)
+    with X.Context(p, [s]) as ctx:
+        ctx.build_H(0)
+        ctx.density(0)
+        q = ctx.get(0, X.Q)
+        F = ctx.get(0, X.F)
+    assert abs(q[0]) < 1e-12
+    assert np.max(np.abs(F)) < 1e-12
+
+
+def test_argument_errors_are_reported(X):
+    p = model_params(X)
+    s = synth.make_system(8, 42, L=7.0)
+    bad = sysdict(s)
+    bad["L"] = 4.0           # box not larger than the hopping cutoff
+    with pytest.raises(X.XlbomdError) as e:
+        X.Context(p, [bad])
+    assert e.value.status == -1
+    with X.Context(p, [sysdict(s)]) as ctx:
+        with pytest.raises(X.XlbomdError) as e:
+            ctx.kernel_update(0)     # no density yet
+        assert e.value.status == -1
+        with pytest.raises(X.XlbomdError):
+            ctx.build_H(0)           # sticky until cleared
+        ctx._lib.xlbomd_clear_error(ctx.h)
+        ctx.build_H(0)
