@@ -164,6 +164,14 @@ xlbomd_status xlbomd_set(xlbomd_ctx* ctx, int sys, int what, const double* host_
 /* Sizes: natoms and padded orbital count of system sys. */
 xlbomd_status xlbomd_sizes(xlbomd_ctx* ctx, int sys, int* natoms, int* n_orb, int* n_pad);
 
+/* Diagnostics: one split-precision tensor-core product C = A B^T (n x n, n a
+ * multiple of 128, prec FP16x3 or BF16x3, sym = symmetric-output mode) of
+ * seeded uniform [-1, 1) matrices, compared on the device with the FP64
+ * product of the same FP64 inputs.  result[0] = max |C_tc - C_fp64|,
+ * result[2] = device wait-timeout flag, result[3] = ms per product.
+ * This is a check of the matrix-product engine; the paper has no counterpart. */
+xlbomd_status xlbomd_selftest_gemm(int n, int prec, int sym, double* result);
+
 xlbomd_status xlbomd_clear_error(xlbomd_ctx* ctx);
 const char* xlbomd_last_error(xlbomd_ctx* ctx);
 xlbomd_status xlbomd_free(xlbomd_ctx* ctx);

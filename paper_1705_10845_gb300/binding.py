@@ -76,6 +76,8 @@ def load(path: str | None = None):
     lib.xlbomd_last_error.argtypes = [P]
     lib.xlbomd_last_error.restype = C.c_char_p
     lib.xlbomd_free.argtypes = [P]
+    lib.xlbomd_selftest_gemm.argtypes = [I, I, I, DP]
+    lib.xlbomd_selftest_gemm.restype = C.c_int
     for name in ("xlbomd_init", "xlbomd_scf", "xlbomd_build_H", "xlbomd_density", "xlbomd_kernel_update",
                  "xlbomd_energy", "xlbomd_step", "xlbomd_response", "xlbomd_get", "xlbomd_set",
                  "xlbomd_sizes", "xlbomd_clear_error", "xlbomd_free"):
@@ -103,6 +105,16 @@ def default_params(**overrides) -> Params:
 
 def _dptr(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def selftest_gemm(n: int, prec: str = "fp16x3", sym: bool = False):
+    """One tensor-core split product of seeded matrices checked on the device
+    against the FP64 product: returns (max abs error, timeout flag, ms)."""
+    out = np.zeros(4)
+    st = load().xlbomd_selftest_gemm(int(n), PREC[prec], int(bool(sym)), _dptr(out))
+    if st != XLBOMD_OK:
+        raise XlbomdError(st, "xlbomd_selftest_gemm")
+    return float(out[0]), int(out[2]), float(out[3])
 
 
 class Context:

@@ -659,6 +659,13 @@ const char* xlbomd_last_error(xlbomd_ctx* ctx) {
   return ctx->msg.c_str();
 }
 
+xlbomd_status xlbomd_selftest_gemm(int n, int prec, int sym, double* result) {
+  if (!result || n <= 0 || n % 128) return XLBOMD_ERR_ARG;
+  const int rc = selftest_gemm(n, prec, sym, result);
+  if (rc == -1) return XLBOMD_ERR_ARG;
+  return rc == 0 ? XLBOMD_OK : XLBOMD_ERR_CUDA;
+}
+
 xlbomd_status xlbomd_free(xlbomd_ctx* ctx) {
   if (!ctx) return XLBOMD_ERR_ARG;
   if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);

@@ -1,10 +1,498 @@
-// Split-precision engines (FP16x3 / BF16x3 tensor-core products).
+// Split-precision engine: the expansion and response chains with tensor-core
+// products on hi/lo 16-bit operands (FP16x3 or BF16x3) and FP32 values.
+//
+// Every matrix keeps an FP32 value array and a split operand pair
+// hi = rn16(x s), lo = rn16(x s - hi) with a power-of-two scale s chosen from
+// max |x| so that max |x s| lies in [2^10, 2^11) (FP16 keeps full precision
+// in both parts); producers raise max |x| atomically and a conversion pass
+// writes hi/lo.  Traces, charges and the density matrix handed to the forces
+// are accumulated in FP64.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <unordered_map>
+
 #include "precision.h"
+#include "tc.h"
 
 namespace xl {
+namespace {
 
-Engine* make_split_engine(int) { return nullptr; }
-cudaError_t alloc_matset_split(MatSet&) { return cudaErrorNotSupported; }
-void free_matset_split(MatSet&) {}
+#define RET(x)                        \
+  do {                                \
+    cudaError_t e_ = (x);             \
+    if (e_ != cudaSuccess) return e_; \
+  } while (0)
+
+inline unsigned nblk(size_t count, int tpb = 256) { return (unsigned)((count + tpb - 1) / tpb); }
+
+__device__ __forceinline__ void raise_amax(unsigned* amax, float v) {
+  v = fabsf(v);
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(amax, __float_as_uint(v));
+}
+
+// Conversion to the split operand pair.  All threads derive the same scale
+// from amax; thread 0 of block 0 publishes it.
+template <bool BF16>
+__global__ void convert_split_kernel(size_t count, const float* __restrict__ f, const unsigned* __restrict__ amax,
+                                     uint16_t* __restrict__ hi, uint16_t* __restrict__ lo, float* __restrict__ scale) {
+  const float m = __uint_as_float(*amax);
+  float s = 1.0f;
+  if (m > 0.0f && isfinite(m)) s = ldexpf(1.0f, 10 - ilogbf(m));
+  if (blockIdx.x == 0 && threadIdx.x == 0) *scale = s;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const float x = f[i] * s;
+    if (BF16) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(x);
+      const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+      hi[i] = __bfloat16_as_ushort(h);
+      lo[i] = __bfloat16_as_ushort(l);
+    } else {
+      const __half h = __float2half_rn(x);
+      const __half l = __float2half_rn(x - __half2float(h));
+      hi[i] = __half_as_ushort(h);
+      lo[i] = __half_as_ushort(l);
+    }
+  }
+}
+
+__global__ void t0_init_f32_kernel(int n, int np, const double* __restrict__ H, double mu, double sc,
+                                   float* __restrict__ T0, unsigned* amax) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float v = 0.0f;
+  if (idx < (size_t)np * np) {
+    const int i = (int)(idx / np), j = (int)(idx % np);
+    if (i < n && j < n) v = (float)(-sc * (H[idx] - (i == j ? mu : 0.0)));
+    T0[idx] = v;
+  }
+  raise_amax(amax, v);
+}
+
+// Y = a I + b X
+__global__ void axpi_f32_kernel(int np, float a, float b, const float* __restrict__ X, float* __restrict__ Y,
+                                unsigned* amax) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float v = 0.0f;
+  if (idx < (size_t)np * np) {
+    const int i = (int)(idx / np), j = (int)(idx % np);
+    v = b * X[idx] + (i == j ? a : 0.0f);
+    Y[idx] = v;
+  }
+  raise_amax(amax, v);
+}
+
+__global__ void level0_A1_f32_kernel(int np, const float* __restrict__ T0, const double* __restrict__ d,
+                                     float* __restrict__ A1, unsigned* amax) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float v = 0.0f;
+  if (idx < (size_t)np * np) {
+    const int i = (int)(idx / np), j = (int)(idx % np);
+    v = (float)((double)T0[idx] * (d[i] + d[j]));
+    A1[idx] = v;
+  }
+  raise_amax(amax, v);
+}
+
+__global__ void transpose_add_f32_kernel(int np, const float* __restrict__ G, float* __restrict__ A1,
+                                         unsigned* amax) {
+  __shared__ float tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < 32; r += 8) tile[r][tx] = G[(size_t)(bx + r) * np + by + tx];
+  __syncthreads();
+  float m = 0.0f;
+  for (int r = ty; r < 32; r += 8) {
+    const size_t o = (size_t)(by + r) * np + bx + tx;
+    const float v = G[o] + tile[tx][r];
+    A1[o] = v;
+    m = fmaxf(m, fabsf(v));
+  }
+  raise_amax(amax, m);
+}
+
+__global__ void row_dot_f32_kernel(int n, int np, const float* __restrict__ Y, const float* __restrict__ M,
+                                   double* __restrict__ out) {
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int j = lane; j < np; j += 32) acc += (double)Y[(size_t)i * np + j] * (double)M[(size_t)i * np + j];
+  acc = warp_sum(acc);
+  if (lane == 0) out[i] = acc;
+}
+
+__global__ void get_diag_f32_kernel(int n, int np, const float* __restrict__ X, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)X[(size_t)i * np + i];
+}
+
+__global__ void diag_sum_f32_kernel(int n, int np, const float* __restrict__ X, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += (double)X[(size_t)i * np + i];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) *out = acc;
+}
+
+__global__ void density_out_f32_kernel(int N, int np, const float* __restrict__ Tn, const float* __restrict__ Tmu,
+                                       double dmu, double* __restrict__ ddiag, double* __restrict__ D) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)np * np) return;
+  const int i = (int)(idx / np), j = (int)(idx % np);
+  double v = 0.0;
+  if (i < N && j < N) {
+    v = 0.5 * ((double)Tn[idx] + dmu * (double)Tmu[idx] + (i == j ? 1.0 : 0.0));
+    if (i == j) ddiag[i] = 2.0 * v;
+  }
+  D[idx] = v;
+}
+
+__global__ void fill_nan_kernel(double* out) { *out = nan(""); }
+
+class EngineSplit : public Engine {
+ public:
+  explicit EngineSplit(int prec) : bf16_(prec == XLBOMD_BF16x3_ID ? 1 : 0) {}
+  ~EngineSplit() override {
+    for (auto& kv : tiles_) cudaFree(kv.second.first);
+    if (err_) cudaFree(err_);
+  }
+
+  cudaError_t convert(cudaStream_t s, SplitMat& m, int np) {
+    const size_t count = (size_t)np * np;
+    const unsigned g = std::min<size_t>(nblk(count), 152 * 16);
+    if (bf16_)
+      convert_split_kernel<true><<<g, 256, 0, s>>>(count, m.f, m.amax, m.hi, m.lo, m.scale);
+    else
+      convert_split_kernel<false><<<g, 256, 0, s>>>(count, m.f, m.amax, m.hi, m.lo, m.scale);
+    return cudaGetLastError();
+  }
+
+  cudaError_t prep_tiles(int np) {
+    if (tiles_.count(np)) return cudaSuccess;
+    std::vector<int> t128 = tc_sym_tiles(np, 128), t256 = (np % 256 == 0) ? tc_sym_tiles(np, 256) : std::vector<int>();
+    std::vector<int> all(t128);
+    all.insert(all.end(), t256.begin(), t256.end());
+    int* d = nullptr;
+    RET(cudaMalloc((void**)&d, sizeof(int) * std::max<size_t>(all.size(), 2)));
+    RET(cudaMemcpy(d, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice));
+    tiles_[np] = {d, {(int)t128.size() / 2, (int)t256.size() / 2}};
+    if (!err_) {
+      RET(cudaMalloc((void**)&err_, sizeof(int)));
+      RET(cudaMemset(err_, 0, sizeof(int)));
+    }
+    return cudaSuccess;
+  }
+
+  // C = alpha A B^T + beta E + diag I + dvec_scale diag(dvec), then split conversion of C
+  cudaError_t gemm(cudaStream_t s, int np, const SplitMat& A, const SplitMat& B, SplitMat& C, float alpha,
+                   const SplitMat* E, float beta, float diag, const double* dvec, float dvec_scale, bool sym,
+                   double* stats) {
+    RET(prep_tiles(np));
+    auto& tl = tiles_[np];
+    RET(cudaMemsetAsync(C.amax, 0, sizeof(unsigned), s));
+    TcArgs a;
+    a.nseg = 3;
+    a.sym = sym ? 1 : 0;
+    a.bf16 = bf16_;
+    a.alpha = alpha;
+    a.E = E ? E->f : nullptr;
+    a.beta = beta;
+    a.diag = diag;
+    a.dvec = dvec;
+    a.ndvec = dvec ? np : 0;
+    a.dvec_scale = dvec_scale;
+    a.C = C.f;
+    a.ldc = np;
+    a.amax = C.amax;
+    a.sa = A.scale;
+    a.sb = B.scale;
+    a.err = err_;
+    const int n128 = tl.second.first, n256 = tl.second.second;
+    RET(gemm_tc(s, np, A.hi, A.lo, B.hi, B.lo, a, tl.first, tl.first + 2 * n128, n128, n256));
+    if (stats) stats[3] += sym ? 0.5 : 1.0;
+    return convert(s, C, np);
+  }
+
+  cudaError_t foe(cudaStream_t s, MatSet& m, const double* H, int N, double mu, double sc,
+                  const std::vector<int>& ns, const std::vector<double>& nc, double* stats) override {
+    const int np = m.np, n = m.n;
+    const size_t cnt = (size_t)np * np;
+    RET(cudaMemsetAsync(m.sT[0].amax, 0, sizeof(unsigned), s));
+    t0_init_f32_kernel<<<nblk(cnt), 256, 0, s>>>(N, np, H, mu, sc, m.sT[0].f, m.sT[0].amax);
+    RET(cudaGetLastError());
+    RET(convert(s, m.sT[0], np));
+    for (int k = 0; k < n; ++k) {
+      RET(gemm(s, np, m.sT[k], m.sT[k], m.sS, 1.f, nullptr, 0.f, 0.f, nullptr, 1.f, true, stats));
+      SplitMat& Y = m.sY[k];
+      RET(cudaMemsetAsync(Y.amax, 0, sizeof(unsigned), s));
+      if (k == 0)
+        axpi_f32_kernel<<<nblk(cnt), 256, 0, s>>>(np, 1.f, -1.f, m.sS.f, Y.f, Y.amax);
+      else
+        axpi_f32_kernel<<<nblk(cnt), 256, 0, s>>>(np, 0.f, (float)nc[k], m.sY[k - 1].f, Y.f, Y.amax);
+      RET(cudaGetLastError());
+      RET(convert(s, Y, np));
+      for (int it = 0; it < ns[k]; ++it) {
+        RET(gemm(s, np, m.sY[k], m.sS, m.sQ, -1.f, &m.sY[k], -1.f, 2.f, nullptr, 1.f, false, stats));
+        RET(gemm(s, np, m.sQ, m.sY[k], m.sYw, 1.f, nullptr, 0.f, 0.f, nullptr, 1.f, true, stats));
+        std::swap(m.sY[k], m.sYw);
+        if (stats) stats[1] += 1;
+      }
+      RET(gemm(s, np, m.sT[k], m.sY[k], m.sT[k + 1], 2.f, nullptr, 0.f, 0.f, nullptr, 1.f, true, stats));
+    }
+    return cudaSuccess;
+  }
+
+  cudaError_t chain(cudaStream_t s, MatSet& m, const double* dvec, int N, bool full_last, double* out_diag,
+                    double* stats) override {
+    const int np = m.np, n = m.n;
+    const size_t cnt = (size_t)np * np;
+    SplitMat* T1 = &m.sT1a;
+    SplitMat* T1n = &m.sT1b;
+    for (int k = 0; k < n; ++k) {
+      const bool last = (k == n - 1);
+      RET(cudaMemsetAsync(m.sA1.amax, 0, sizeof(unsigned), s));
+      if (k == 0) {
+        level0_A1_f32_kernel<<<nblk(cnt), 256, 0, s>>>(np, m.sT[0].f, dvec, m.sA1.f, m.sA1.amax);
+        RET(cudaGetLastError());
+        RET(convert(s, m.sA1, np));
+        RET(gemm(s, np, m.sT[1], m.sA1, m.sMt, -1.f, nullptr, 0.f, 0.f, dvec, 2.f, false, stats));
+      } else {
+        RET(gemm(s, np, m.sT[k], *T1, m.sG, 1.f, nullptr, 0.f, 0.f, nullptr, 1.f, false, stats));
+        dim3 grid(np / 32, np / 32), block(32, 8);
+        transpose_add_f32_kernel<<<grid, block, 0, s>>>(np, m.sG.f, m.sA1.f, m.sA1.amax);
+        RET(cudaGetLastError());
+        RET(convert(s, m.sA1, np));
+        RET(gemm(s, np, m.sT[k + 1], m.sA1, m.sMt, -1.f, T1, 2.f, 0.f, nullptr, 1.f, false, stats));
+      }
+      if (last && !full_last) {
+        row_dot_f32_kernel<<<(N + 7) / 8, 256, 0, s>>>(N, np, m.sY[k].f, m.sMt.f, out_diag);
+        return cudaGetLastError();
+      }
+      SplitMat* dst = (last && full_last) ? &m.sTmu : T1n;
+      RET(gemm(s, np, m.sY[k], m.sMt, *dst, 1.f, nullptr, 0.f, 0.f, nullptr, 1.f, true, stats));
+      if (last) {
+        get_diag_f32_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, np, dst->f, out_diag);
+        return cudaGetLastError();
+      }
+      T1n = T1;
+      T1 = dst;
+    }
+    return cudaSuccess;
+  }
+
+  cudaError_t trace_tn(cudaStream_t s, MatSet& m, int N, double* out) override {
+    diag_sum_f32_kernel<<<1, 1024, 0, s>>>(N, m.np, m.sT[m.n].f, out);
+    return cudaGetLastError();
+  }
+
+  cudaError_t density_out(cudaStream_t s, MatSet& m, int N, double dmu, const double*, double* ddiag,
+                          double* D) override {
+    density_out_f32_kernel<<<nblk((size_t)m.np * m.np), 256, 0, s>>>(N, m.np, m.sT[m.n].f, m.sTmu.f, dmu, ddiag, D);
+    return cudaGetLastError();
+  }
+
+  cudaError_t entropy(cudaStream_t s, MatSet&, int, double, int, double, double, const double*, const double*,
+                      double*, double* out) override {
+    fill_nan_kernel<<<1, 1, 0, s>>>(out);
+    return cudaGetLastError();
+  }
+
+  int* err_ = nullptr;
+
+ private:
+  int bf16_;
+  std::unordered_map<int, std::pair<int*, std::pair<int, int>>> tiles_;
+};
+
+cudaError_t alloc_split(SplitMat& m, int np, float* scal_f, unsigned* scal_u) {
+  const size_t cnt = (size_t)np * np;
+  RET(cudaMalloc((void**)&m.f, cnt * sizeof(float)));
+  RET(cudaMalloc((void**)&m.hi, cnt * sizeof(uint16_t)));
+  RET(cudaMalloc((void**)&m.lo, cnt * sizeof(uint16_t)));
+  RET(cudaMemset(m.f, 0, cnt * sizeof(float)));
+  RET(cudaMemset(m.hi, 0, cnt * sizeof(uint16_t)));
+  RET(cudaMemset(m.lo, 0, cnt * sizeof(uint16_t)));
+  m.scale = scal_f;
+  m.amax = scal_u;
+  return cudaSuccess;
+}
+
+void free_split(SplitMat& m) {
+  if (m.f) cudaFree(m.f);
+  if (m.hi) {
+    tc_forget_maps(m.hi);
+    cudaFree(m.hi);
+  }
+  if (m.lo) {
+    tc_forget_maps(m.lo);
+    cudaFree(m.lo);
+  }
+  m.f = nullptr;
+  m.hi = m.lo = nullptr;
+}
+
+}  // namespace
+
+Engine* make_split_engine(int prec) {
+  if (prec != XLBOMD_FP16x3_ID && prec != XLBOMD_BF16x3_ID) return nullptr;
+  return new EngineSplit(prec);
+}
+
+cudaError_t alloc_matset_split(MatSet& m) {
+  const int np = m.np, n = m.n;
+  const int nmat = (n + 1) + n + 9;
+  // one block of device scalars: scales (float) then amax (unsigned)
+  float* scal = nullptr;
+  RET(cudaMalloc((void**)&scal, sizeof(float) * 2 * nmat));
+  RET(cudaMemset(scal, 0, sizeof(float) * 2 * nmat));
+  m.tc_plan = scal;
+  float* sf = scal;
+  unsigned* su = reinterpret_cast<unsigned*>(scal + nmat);
+  int idx = 0;
+  m.sT.assign(n + 1, SplitMat());
+  m.sY.assign(n, SplitMat());
+  for (auto& x : m.sT) {
+    RET(alloc_split(x, np, sf + idx, su + idx));
+    ++idx;
+  }
+  for (auto& x : m.sY) {
+    RET(alloc_split(x, np, sf + idx, su + idx));
+    ++idx;
+  }
+  SplitMat* w[] = {&m.sS, &m.sQ, &m.sYw, &m.sG, &m.sA1, &m.sMt, &m.sT1a, &m.sT1b, &m.sTmu};
+  for (SplitMat* x : w) {
+    RET(alloc_split(*x, np, sf + idx, su + idx));
+    ++idx;
+  }
+  return cudaSuccess;
+}
+
+void free_matset_split(MatSet& m) {
+  for (auto& x : m.sT) free_split(x);
+  for (auto& x : m.sY) free_split(x);
+  m.sT.clear();
+  m.sY.clear();
+  SplitMat* w[] = {&m.sS, &m.sQ, &m.sYw, &m.sG, &m.sA1, &m.sMt, &m.sT1a, &m.sT1b, &m.sTmu};
+  for (SplitMat* x : w) free_split(*x);
+  if (m.tc_plan) cudaFree(m.tc_plan);
+  m.tc_plan = nullptr;
+}
+
+// ---- self-test of the tensor-core product against the FP64 product ----
+
+namespace {
+
+__global__ void fill_random_kernel(size_t count, int np, uint64_t seed, int sym, double* out) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= count) return;
+  size_t i = idx / np, j = idx % np;
+  if (sym && j < i) {
+    const size_t t = i;
+    i = j;
+    j = t;
+  }
+  uint64_t z = seed + 0x9E3779B97F4A7C15ull * (i * (uint64_t)np + j + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  out[idx] = ((double)(z >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
+}
+
+__global__ void to_f32_kernel(size_t count, const double* __restrict__ x, float* __restrict__ f, unsigned* amax) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float v = 0.0f;
+  if (idx < count) {
+    v = (float)x[idx];
+    f[idx] = v;
+  }
+  raise_amax(amax, v);
+}
+
+__global__ void max_abs_diff_kernel(size_t count, const float* __restrict__ a, const double* __restrict__ b,
+                                    double* __restrict__ out) {
+  __shared__ double sh[32];
+  double m = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs((double)a[i] - b[i]));
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, sh[w]);
+    unsigned long long* o = reinterpret_cast<unsigned long long*>(out);
+    atomicMax(o, (unsigned long long)__double_as_longlong(t));
+  }
+}
+
+}  // namespace
+
+// Returns 0 on success and writes [max |C_tc - C_ref|, max |C_ref|, error flag, ms per product].
+int selftest_gemm(int n, int prec, int sym, double* result) {
+  if (n % 128 || n <= 0 || (prec != XLBOMD_FP16x3_ID && prec != XLBOMD_BF16x3_ID)) return -1;
+  EngineSplit eng(prec);
+  const size_t cnt = (size_t)n * n;
+  double *A = nullptr, *B = nullptr, *Cref = nullptr, *out = nullptr;
+  float* scal = nullptr;
+  SplitMat sa, sb, sc;
+  cudaStream_t s = nullptr;
+  int rc = -2;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = 0.f;
+  if (cudaMalloc((void**)&A, cnt * 8) || cudaMalloc((void**)&B, cnt * 8) || cudaMalloc((void**)&Cref, cnt * 8) ||
+      cudaMalloc((void**)&out, 8) || cudaMalloc((void**)&scal, 6 * sizeof(float)))
+    goto done;
+  cudaMemset(scal, 0, 6 * sizeof(float));
+  if (alloc_split(sa, n, scal, (unsigned*)scal + 3) || alloc_split(sb, n, scal + 1, (unsigned*)scal + 4) ||
+      alloc_split(sc, n, scal + 2, (unsigned*)scal + 5))
+    goto done;
+  fill_random_kernel<<<nblk(cnt), 256>>>(cnt, n, 11, 0, A);
+  fill_random_kernel<<<nblk(cnt), 256>>>(cnt, n, 23, sym, B);
+  to_f32_kernel<<<nblk(cnt), 256>>>(cnt, A, sa.f, sa.amax);
+  to_f32_kernel<<<nblk(cnt), 256>>>(cnt, B, sb.f, sb.amax);
+  if (eng.convert(s, sa, n) || eng.convert(s, sb, n)) goto done;
+  {
+    EpiF64 e;
+    if (gemm_f64_nt(s, n, n, n, A, n, B, n, Cref, n, e, sym != 0)) goto done;
+  }
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  if (eng.gemm(s, n, sa, sb, sc, 1.f, nullptr, 0.f, 0.f, nullptr, 1.f, sym != 0, nullptr)) goto done;
+  cudaEventRecord(e0, s);
+  for (int r = 0; r < 5; ++r)
+    if (eng.gemm(s, n, sa, sb, sc, 1.f, nullptr, 0.f, 0.f, nullptr, 1.f, sym != 0, nullptr)) goto done;
+  cudaEventRecord(e1, s);
+  if (cudaDeviceSynchronize() != cudaSuccess) goto done;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaMemset(out, 0, 8);
+  max_abs_diff_kernel<<<304, 256>>>(cnt, sc.f, Cref, out);
+  if (cudaDeviceSynchronize() != cudaSuccess) goto done;
+  {
+    double h[1];
+    int herr = 0;
+    cudaMemcpy(h, out, 8, cudaMemcpyDeviceToHost);
+    cudaMemcpy(&herr, eng.err_, sizeof(int), cudaMemcpyDeviceToHost);
+    result[0] = h[0];
+    result[1] = 0.0;
+    result[2] = herr;
+    result[3] = ms / 5.0;
+    rc = 0;
+  }
+done:
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  free_split(sa);
+  free_split(sb);
+  free_split(sc);
+  if (A) cudaFree(A);
+  if (B) cudaFree(B);
+  if (Cref) cudaFree(Cref);
+  if (out) cudaFree(out);
+  if (scal) cudaFree(scal);
+  return rc;
+}
 
 }  // namespace xl

@@ -1,0 +1,399 @@
+// Split-precision tensor-core products for sm_103a (tcgen05 + TMEM + TMA).
+//
+// C = epi( sum_seg A_seg B_seg^T ) with 16-bit operands (FP16 or BF16) and an
+// FP32 accumulator in tensor memory.  A split product uses three K segments,
+// A_hi B_hi + A_hi B_lo + A_lo B_hi, accumulated into one TMEM tile; the
+// operands carry power-of-two scales that the epilogue removes.
+//
+// Per CTA: one 128 x BN output tile.  Warp 0 issues TMA loads (128-byte
+// swizzle, K-major) into a STAGES-deep ring guarded by mbarriers; warp 1
+// allocates TMEM and one elected thread issues tcgen05.mma (M = 128,
+// N = BN, K = 16) per 32-byte K step; warps 2-5 wait for the accumulator,
+// read it with tcgen05.ld (32 lanes x 32 columns per load), apply the
+// epilogue and store FP32 rows (and the mirrored columns of a symmetric
+// product).  Every mbarrier wait is bounded: on timeout the kernel records an
+// error code and leaves its loops, and TMEM is always released.
+#include <cuda.h>
+
+#include <cstdio>
+#include <mutex>
+#include <unordered_map>
+
+#include "precision.h"
+#include "tc.h"
+
+namespace xl {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;           // 64 x 16-bit = 128 bytes: one swizzle row
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int kWaitLimit = 1 << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for the completion of the phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (int it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+  const uint32_t a = smem_u32(p);
+  uint64_t d = 0;
+  d |= (uint64_t)((a >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;              // version
+  d |= (uint64_t)2 << 61;              // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: D = F32, A/B = F16 (0) or BF16 (1), both K-major.
+__host__ __device__ constexpr uint32_t instr_desc(int bn, int ab_fmt) {
+  return (1u << 4) | ((uint32_t)ab_fmt << 7) | ((uint32_t)ab_fmt << 10) | ((uint32_t)(bn >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                   const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, TcArgs a) {
+  constexpr int B_BYTES = BN * BK * 2;
+  constexpr uint32_t TMEM_COLS = BN;   // 128 or 256 (power of two >= 32)
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int tm, tn;
+  if (a.tile_list) {
+    tm = a.tile_list[2 * blockIdx.x];
+    tn = a.tile_list[2 * blockIdx.x + 1];
+  } else {
+    tm = blockIdx.x / a.tiles_n;
+    tn = blockIdx.x % a.tiles_n;
+  }
+
+  if (warp == 0 && lane == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  const int nk = a.K / BK;
+  const int total = a.nseg * nk;
+  bool ok = true;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int kb = 0; kb < total; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (kb >= STAGES && !mbar_wait(&empty[s], ph ^ 1)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+        const int seg = kb / nk, kk = (kb % nk) * BK;
+        const CUtensorMap* ma = (seg == 2) ? &mAlo : &mAhi;
+        const CUtensorMap* mb = (seg == 1) ? &mBlo : &mBhi;
+        tma_load_2d(sA + s * A_BYTES, ma, kk, tm * BM, &full[s]);
+        tma_load_2d(sB + s * B_BYTES, mb, kk, tn * BN, &full[s]);
+      }
+      if (!ok) atomicExch(a.err, 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc_f16 = instr_desc(BN, 0);
+      constexpr uint32_t idesc_bf16 = instr_desc(BN, 1);
+      const uint32_t idesc = a.bf16 ? idesc_bf16 : idesc_f16;
+      for (int kb = 0; kb < total; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!mbar_wait(&full[s], ph)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < BK / 16; ++j) {
+          const uint64_t ad = smem_desc(sA + s * A_BYTES + j * 32);
+          const uint64_t bd = smem_desc(sB + s * B_BYTES + j * 32);
+          mma_f16(tmem, ad, bd, idesc, (kb > 0 || j > 0) ? 1u : 0u);
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(accf);
+      if (!ok) atomicExch(a.err, 2);
+    }
+  } else {
+    // epilogue warps 2..5: TMEM lanes 32 * (warp % 4) ..
+    const int q = warp & 3;
+    if (!mbar_wait(accf, 0)) {
+      if (lane == 0) atomicExch(a.err, 3);
+    } else {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int row = tm * BM + q * 32 + lane;
+      const float inv = a.alpha / (__ldg(a.sa) * __ldg(a.sb));
+      float vmax = 0.0f;
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 32), v);
+        const int col0 = tn * BN + ch * 32;
+        const float* er = a.E ? a.E + (size_t)row * a.ldc + col0 : nullptr;
+        float* cr = a.C + (size_t)row * a.ldc + col0;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int col = col0 + i;
+          float x = inv * v[i];
+          if (er) x += a.beta * er[i];
+          if (col == row) {
+            x += a.diag;
+            if (a.dvec && row < a.ndvec) x += a.dvec_scale * (float)a.dvec[row];
+          }
+          v[i] = x;
+        }
+        if (!a.sym) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 4) {
+            *reinterpret_cast<float4*>(cr + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            vmax = fmaxf(vmax, fmaxf(fmaxf(fabsf(v[i]), fabsf(v[i + 1])), fmaxf(fabsf(v[i + 2]), fabsf(v[i + 3]))));
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int col = col0 + i;
+            if (col >= row) {
+              cr[i] = v[i];
+              if (col > row) a.C[(size_t)col * a.ldc + row] = v[i];
+              vmax = fmaxf(vmax, fabsf(v[i]));
+            }
+          }
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+      if (lane == 0 && a.amax) atomicMax(a.amax, __float_as_uint(vmax));
+    }
+  }
+
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ---- host side: tensor maps ----
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+struct MapKey {
+  const void* p;
+  int rows, box, bf16;
+  bool operator==(const MapKey& o) const { return p == o.p && rows == o.rows && box == o.box && bf16 == o.bf16; }
+};
+struct MapHash {
+  size_t operator()(const MapKey& k) const {
+    return std::hash<const void*>()(k.p) ^ (size_t)k.rows * 1315423911u ^ (size_t)k.box * 2654435761u ^ k.bf16;
+  }
+};
+
+std::mutex g_map_mu;
+std::unordered_map<MapKey, CUtensorMap, MapHash> g_maps;
+
+bool make_map(CUtensorMap* out, const void* base, int n, int box_rows, int bf16) {
+  std::lock_guard<std::mutex> lk(g_map_mu);
+  MapKey k{base, n, box_rows, bf16};
+  auto it = g_maps.find(k);
+  if (it != g_maps.end()) {
+    *out = it->second;
+    return true;
+  }
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)n * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUtensorMap m;
+  CUresult r = enc(&m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return false;
+  g_maps[k] = m;
+  *out = m;
+  return true;
+}
+
+template <int BN>
+int smem_bytes() {
+  return STAGES * (A_BYTES + BN * BK * 2) + (2 * STAGES + 1) * 8 + 16 + 1024;
+}
+
+}  // namespace
+
+void tc_forget_maps(const void* base) {
+  std::lock_guard<std::mutex> lk(g_map_mu);
+  for (auto it = g_maps.begin(); it != g_maps.end();) {
+    if (it->first.p == base)
+      it = g_maps.erase(it);
+    else
+      ++it;
+  }
+}
+
+cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* Alo, const uint16_t* Bhi,
+                    const uint16_t* Blo, TcArgs args, const int* sym_tiles_128, const int* sym_tiles_256,
+                    int n_sym_128, int n_sym_256) {
+  if (n % 128 != 0 || n <= 0) return cudaErrorInvalidValue;
+  const bool wide = (n % 256 == 0);
+  const int bn = wide ? 256 : 128;
+  CUtensorMap mAhi, mAlo, mBhi, mBlo;
+  if (!make_map(&mAhi, Ahi, n, BM, args.bf16) || !make_map(&mAlo, Alo ? Alo : Ahi, n, BM, args.bf16) ||
+      !make_map(&mBhi, Bhi, n, bn, args.bf16) || !make_map(&mBlo, Blo ? Blo : Bhi, n, bn, args.bf16))
+    return cudaErrorInvalidValue;
+  args.K = n;
+  args.tiles_n = n / bn;
+  int nblocks;
+  if (args.sym) {
+    args.tile_list = wide ? sym_tiles_256 : sym_tiles_128;
+    nblocks = wide ? n_sym_256 : n_sym_128;
+  } else {
+    args.tile_list = nullptr;
+    nblocks = (n / BM) * (n / bn);
+  }
+  if (wide) {
+    static bool attr = false;
+    const int sb = smem_bytes<256>();
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    gemm_tc_kernel<256><<<nblocks, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, args);
+  } else {
+    static bool attr = false;
+    const int sb = smem_bytes<128>();
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    gemm_tc_kernel<128><<<nblocks, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, args);
+  }
+  return cudaGetLastError();
+}
+
+// Tile lists of symmetric products: tiles (tm, tn) of BM x bn that reach the
+// upper triangle (bn tn + bn > BM tm), row-major order.
+std::vector<int> tc_sym_tiles(int n, int bn) {
+  std::vector<int> t;
+  for (int tm = 0; tm < n / BM; ++tm)
+    for (int tn = 0; tn < n / bn; ++tn)
+      if (bn * tn + bn > BM * tm) {
+        t.push_back(tm);
+        t.push_back(tn);
+      }
+  return t;
+}
+
+}  // namespace xl

@@ -10,6 +10,9 @@
 
 namespace xl {
 
+constexpr int XLBOMD_FP16x3_ID = 1;
+constexpr int XLBOMD_BF16x3_ID = 2;
+
 // Matrices of one system in the working precision.  In the FP64 engine each
 // logical matrix is a double array; the split engines keep an FP32 value
 // array plus hi/lo 16-bit operand arrays with a power-of-two scale.
@@ -63,6 +66,9 @@ Engine* make_engine(int prec);
 Engine* make_split_engine(int prec);
 cudaError_t alloc_matset_split(MatSet& m);
 void free_matset_split(MatSet& m);
+
+// tensor-core product self-test (engine_split.cu)
+int selftest_gemm(int n, int prec, int sym, double* result);
 
 // FP64 eigenvalue-free entropy (entropy.cu)
 cudaError_t launch_entropy_f64(cudaStream_t s, MatSet& m, int N, double beta, int n_sq, double mu, double dmu,

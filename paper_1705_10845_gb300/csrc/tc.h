@@ -1,0 +1,39 @@
+// Tensor-core split-precision product (gemm_tc.cu) interface.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace xl {
+
+struct TcArgs {
+  int K = 0;                      // inner dimension (set by gemm_tc)
+  int nseg = 3;                   // 1: hi only; 3: hi*hi + hi*lo + lo*hi
+  int sym = 0;                    // symmetric output (upper tiles, mirrored)
+  int bf16 = 0;                   // operand type: 0 FP16, 1 BF16
+  int tiles_n = 0;                // set by gemm_tc
+  const int* tile_list = nullptr; // set by gemm_tc
+  float alpha = 1.0f;             // C = alpha acc / (sa sb) + beta E + diag I + dvec_scale diag(dvec)
+  const float* E = nullptr;
+  float beta = 0.0f;
+  float diag = 0.0f;
+  const double* dvec = nullptr;
+  int ndvec = 0;
+  float dvec_scale = 1.0f;
+  float* C = nullptr;
+  int ldc = 0;
+  unsigned* amax = nullptr;       // max |C| (float bits), atomically raised
+  const float* sa = nullptr;      // operand scales (device scalars)
+  const float* sb = nullptr;
+  int* err = nullptr;             // set non-zero when a bounded wait gives up
+};
+
+// n x n product (n a multiple of 128); the symmetric tile lists come from tc_sym_tiles.
+cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* Alo, const uint16_t* Bhi,
+                    const uint16_t* Blo, TcArgs args, const int* sym_tiles_128, const int* sym_tiles_256,
+                    int n_sym_128, int n_sym_256);
+std::vector<int> tc_sym_tiles(int n, int bn);
+void tc_forget_maps(const void* base);
+
+}  // namespace xl

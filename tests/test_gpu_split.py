@@ -1,0 +1,67 @@
+"""GPU checks of the split-precision tensor-core path (tcgen05, FP16x3/BF16x3).
+
+The product engine is checked against the FP64 product; the density, charges,
+forces and kernel against the oracle.  Tolerances of the mixed forms: charges
+1e-5 e, forces 1e-4 eV/A.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+ALPHA_MIX = 0.06
+
+
+@pytest.fixture(scope="module")
+def X():
+    import paper_1705_10845_gb300 as X
+    X.build.build()
+    X.load()
+    return X
+
+
+def sysdict(s):
+    return dict(natoms=s.natoms, L=s.L, R=s.R, V=s.V, Z=s.Z, mass=s.mass)
+
+
+@pytest.mark.parametrize("n", [128, 256, 384, 1024])
+@pytest.mark.parametrize("sym", [False, True])
+@pytest.mark.parametrize("prec,bound", [("fp16x3", 1e-6), ("bf16x3", 2e-5)])
+def test_tensor_core_product_matches_fp64(X, n, sym, prec, bound):
+    err, flag, ms = X.binding.selftest_gemm(n, prec, sym)
+    assert flag == 0
+    # entries are sums of n products of U(-1, 1) numbers; the tensor-core FP32
+    # accumulation loses up to ~2^-23 of the running sum per step, so the
+    # error bound grows linearly with n (a wrong operand layout gives O(1)).
+    print(prec, n, sym, err, ms)
+    assert err < bound * n, (err, ms)
+
+
+@pytest.mark.parametrize("prec", ["fp16x3", "bf16x3"])
+@pytest.mark.parametrize("case", ["tiny24", "ragged37"])
+def test_split_density_against_oracle(X, prec, case):
+    s = synth.make_system(24, 1705, L=7.0) if case == "tiny24" else synth.make_system(37, 11)
+    p = X.default_params(mix_alpha=ALPHA_MIX, kernel_c=1 - 1 / ALPHA_MIX, prec=prec, mu_tol=1e-5)
+    m = O.Model(Te=p.Te, n_sq=p.n_sq)
+    rng = np.random.default_rng(2)
+    n = rng.normal(scale=0.02, size=s.natoms)
+    n -= n.mean()
+    xl = O.XLParams(rank_m=p.rank_m, kernel_c=p.kernel_c)
+    ref = O.evaluate(s.R, s.L, s.Z, n, m, xl)
+    with X.Context(p, [sysdict(s)]) as ctx:
+        ctx.set(0, X.N, n)
+        ctx.set(0, X.MU, [ref.dens.mu + 0.01])
+        ctx.build_H(0)
+        ctx.density(0)
+        ctx.kernel_update(0)
+        q, F, Kr = ctx.get(0, X.Q), ctx.get(0, X.F), ctx.get(0, X.KR)
+    tol_q = 1e-5 if prec == "fp16x3" else 1e-4
+    tol_f = 1e-4 if prec == "fp16x3" else 1e-3
+    print(prec, case, "dq", np.abs(q - ref.q).max(), "dF", np.abs(F - ref.F).max(), "dKr",
+          np.abs(Kr - ref.Kr).max())
+    assert np.max(np.abs(q - ref.q)) < tol_q
+    assert np.max(np.abs(F - ref.F)) < tol_f
+    assert np.max(np.abs(Kr - ref.Kr)) < 100 * tol_q
