@@ -286,8 +286,10 @@ def build_gamma(R, L, model: Model, eta=None):
     for T in itertools.product((-1, 0, 1), repeat=3):
         d = dmin + np.asarray(T, dtype=float) * L
         gam += _ok_real(np.sqrt(np.sum(d * d, axis=2)), a, eta)
-    for g, Ag in zip(G, A):
-        gam += Ag * np.cos(dmin @ g)
+    # reciprocal part: cos(G.(R_J - R_I)) = cos(G.R_I) cos(G.R_J) + sin(G.R_I) sin(G.R_J)
+    ph = R @ G.T
+    C, S = np.cos(ph), np.sin(ph)
+    gam += (C * A) @ C.T + (S * A) @ S.T
     return k * gam
 
 
@@ -307,8 +309,13 @@ def build_gamma_grad(R, L, model: Model):
         with np.errstate(divide="ignore", invalid="ignore"):
             fr = np.where(r > 0.0, _ok_real_dr(r, a, eta) / r, 0.0)
         out += fr[..., None] * d
-    for g, Ag in zip(G, A):
-        out += (-Ag * np.sin(dmin @ g))[..., None] * g
+    # reciprocal part: -sum_G A_G G sin(G.(R_J - R_I)),
+    # sin(G.(R_J - R_I)) = cos(G.R_I) sin(G.R_J) - sin(G.R_I) cos(G.R_J)
+    ph = R @ G.T
+    C, S = np.cos(ph), np.sin(ph)
+    for c in range(3):
+        w = A * G[:, c]
+        out[..., c] -= (C * w) @ S.T - (S * w) @ C.T
     return k * out
 
 
