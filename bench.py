@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the XL-BOMD hot path on GB300.
+
+Workload (default): one trajectory of 1536 carbon-like atoms (N = 6144
+orbitals) in a 28 A periodic cube, Te = 1500 K, 14 squarings of the recursive
+Fermi-operator expansion, rank-4 kernel, dt = 0.25 fs; split FP16x3
+tensor-core products with FP64 traces, charges, forces and integration.
+A step is one full XL-BOMD step (H build, expansion with the
+chemical-potential loop, charges, forces, four response chains, kernel
+update, Verlet).  With --gpus N each rank runs its own replica trajectory
+(seed 1705 + rank): weak scaling, no collective on the data path.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the host cores instead (bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "XL-BOMD steps/s and FOE TFLOP/s vs peak, mixed vs FP64 GPU at |dq|<=1e-5 e"
+ALPHA_MIX = 0.06
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp16x3", choices=["fp16x3", "bf16x3", "fp64"])
+    ap.add_argument("--natoms", type=int, default=1536)
+    ap.add_argument("--Te", type=float, default=1500.0)
+    ap.add_argument("--nsq", type=int, default=14)
+    ap.add_argument("--rank", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=0,
+                    help="also time this many plain-FP64 GPU steps of the same workload")
+    return ap.parse_args()
+
+
+def workload_config(a, parallel):
+    return {
+        "workload": f"XL-BOMD, {a.natoms} carbon-like atoms (N = {4 * a.natoms} orbitals), orthogonal SCC-TB, "
+                    f"Te = {a.Te:g} K, {a.nsq} squarings, rank-{a.rank} kernel, dt = 0.25 fs",
+        "natoms": a.natoms, "n_orb": 4 * a.natoms, "Te_K": a.Te, "n_squarings": a.nsq, "rank_m": a.rank,
+        "prec": a.prec, "parallelism": parallel,
+        "l2": "inputs larger than L2: about 11 GB of expansion matrices are rewritten every step",
+    }
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(gpu_index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("bf16_tflops"), d.get("bf16_tflops_sustained"), d.get("hbm_gbs"), "measured"
+    except (OSError, ValueError):
+        return 1900.0, 1700.0, 6800.0, "fallback"
+
+
+def make_params(X, a, prec):
+    return X.default_params(Te=a.Te, n_sq=a.nsq, rank_m=a.rank, dt=0.25, mix_alpha=ALPHA_MIX,
+                            kernel_c=1.0 - 1.0 / ALPHA_MIX, prec=prec,
+                            scf_tol=1e-10 if prec == "fp64" else 1e-5, scf_mode=1, kernel_auto=1,
+                            mu_tol=1e-9 if prec == "fp64" else 1e-3, scf_max_iter=200)
+
+
+def oracle_sample(R, L, Z, n, a):
+    """One oracle density evaluation (H0, gamma, eigendecomposition, mu,
+    Mulliken charges) at the given state; returns (seconds, q)."""
+    import oracle as O
+    m = O.Model(Te=a.Te, n_sq=a.nsq)
+    t = time.perf_counter()
+    q = O.charges_at(R, L, Z, n, m)
+    return time.perf_counter() - t, q
+
+
+def run_reference(a, ws, rank):
+    """The oracle as it stands on the host cores (FP64 CPU), same workload."""
+    import numpy as np
+
+    import synth
+    if ws > 1 and rank != 0:
+        return 0
+    cores = len(os.sched_getaffinity(0))
+    s = synth.make_system(a.natoms, 1705)
+    rng = np.random.default_rng(0)
+    n = rng.normal(scale=0.01, size=a.natoms)
+    n -= n.mean()
+    # each step: one oracle density evaluation of the whole system; the
+    # number of timed steps is capped so the run ends within a few minutes
+    t_first, _ = oracle_sample(s.R, s.L, s.Z, n, a)          # warm-up
+    k = max(1, min(a.steps, int(150.0 / max(t_first, 1e-3))))
+    t0 = time.perf_counter()
+    for _ in range(k):
+        oracle_sample(s.R, s.L, s.Z, n, a)
+    dt = time.perf_counter() - t0
+    v = k / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": a.gpus,
+            "steps": k, "warmup": 1, "ms_per_step": 1000.0 * dt / k, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(a, "oracle on host cores"),
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                             "sample": "one oracle density evaluation (H0, Ewald gamma, full eigendecomposition, "
+                                       "chemical potential, Mulliken charges) of the whole system per step; "
+                                       "the response chains, forces and integration of a full step are not "
+                                       "included, so this overstates the CPU step rate"},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    a = parse()
+    ws, rank, local = dist_setup()
+    if a.impl == "reference":
+        return run_reference(a, ws, rank)
+
+    import numpy as np
+    import torch
+
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+
+    import paper_1705_10845_gb300 as X
+    import synth
+    if rank == 0:
+        X.build.build()
+    if dist is not None:
+        dist.barrier()
+    X.load()
+
+    s = synth.make_system(a.natoms, 1705 + rank)
+    sysd = dict(natoms=s.natoms, L=s.L, R=s.R, V=s.V, Z=s.Z, mass=s.mass)
+    p = make_params(X, a, a.prec)
+    stream = torch.cuda.current_stream()
+    ctx = X.Context(p, [sysd], stream=stream.cuda_stream)
+
+    # t0 ground state (untimed), then warm-up steps
+    t_scf = time.perf_counter()
+    ctx.scf(0)
+    torch.cuda.synchronize()
+    t_scf = time.perf_counter() - t_scf
+    ctx.step(a.warmup)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident state ----
+    sampler = ClockSampler(local)
+    st0 = ctx.get(0, X.STATS)
+    l0 = X.binding.launch_count()
+    ctx.gemm_profile(1)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    wall = time.perf_counter()
+    ctx.step(a.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    launches = X.binding.launch_count() - l0
+    prof = ctx.gemm_profile(2)
+    ctx.gemm_profile(0)
+    st1 = ctx.get(0, X.STATS)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    sec = ms / 1000.0
+    value = ws * a.steps / sec
+
+    # ---- end to end: host state in, results out, every step ----
+    ke = a.e2e_steps if a.e2e_steps is not None else max(1, a.steps // 2)
+    nat = a.natoms
+    k1 = p.kmax + 1
+    pin = lambda n_: torch.empty(n_, dtype=torch.float64, pin_memory=True).numpy()
+    hR, hV, hN = pin(3 * nat), pin(3 * nat), pin(k1 * nat)
+    hR[:] = ctx.get(0, X.R).ravel()
+    hV[:] = ctx.get(0, X.V).ravel()
+    hN[:] = ctx.get(0, X.NHIST).ravel()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        ctx.set(0, X.R, hR)
+        ctx.set(0, X.V, hV)
+        ctx.set(0, X.NHIST, hN)
+        ctx.step(1)
+        hR[:] = ctx.get(0, X.R).ravel()
+        hV[:] = ctx.get(0, X.V).ravel()
+        hN[:] = ctx.get(0, X.NHIST).ravel()
+        q_host = ctx.get(0, X.Q)
+        f_host = ctx.get(0, X.F)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([te], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te = float(t.item())
+    e2e_value = ws * ke / te
+    h2d = 8 * (3 * nat + 3 * nat + k1 * nat)
+    d2h = 8 * (3 * nat + 3 * nat + k1 * nat + nat + 3 * nat)
+
+    # ---- optional plain-FP64 GPU steps of the same workload from this state ----
+    fp64 = None
+    if a.fp64_steps > 0:
+        p64 = make_params(X, a, "fp64")
+        sysd64 = dict(sysd)
+        sysd64["R"] = ctx.get(0, X.R)
+        sysd64["V"] = ctx.get(0, X.V)
+        ctx64 = X.Context(p64, [sysd64], stream=stream.cuda_stream)
+        ctx64.set(0, X.NHIST, ctx.get(0, X.NHIST))
+        ctx64.set(0, X.MU, ctx.get(0, X.MU))
+        ctx64.build_H(0)
+        ctx64.density(0)
+        ctx64.kernel_update(0)
+        torch.cuda.synchronize()
+        f0 = time.perf_counter()
+        ctx64.step(a.fp64_steps)
+        torch.cuda.synchronize()
+        f64s = time.perf_counter() - f0
+        fp64 = {"steps": a.fp64_steps, "steps_per_s": a.fp64_steps / f64s, "s_per_step": f64s / a.fp64_steps}
+        ctx64.close()
+
+    # ---- parity at the final state and the CPU baseline (rank 0) ----
+    cpu = None
+    parity = None
+    if rank == 0 and not a.no_cpu_baseline:
+        R = ctx.get(0, X.R)
+        nn = ctx.get(0, X.N)
+        ctx.build_H(0)
+        ctx.density(0)
+        qg = ctx.get(0, X.Q)
+        tcpu, qo = oracle_sample(R, s.L, s.Z, nn, a)
+        cpu = {"value": 1.0 / tcpu, "unit": "steps/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+               "sample": "one oracle density evaluation (H0, Ewald gamma, full eigendecomposition, chemical "
+                         "potential, Mulliken charges) at the final GPU state; response chains, forces and "
+                         "integration are not included, so this overstates the CPU step rate"}
+        parity = {"max_abs_dq_vs_fp64_oracle": float(np.max(np.abs(qg - qo))), "tolerance": 1e-5}
+
+    bf, bf_sus, hbm, src = peaks()
+    gemm_launches, gemm_ms, gemm_flops = prof
+    achieved = gemm_flops / (gemm_ms / 1000.0) / 1e12 if gemm_ms > 0 else None
+    peak = bf_sus
+    units = st1 - st0
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": a.prec, "data": "synthetic", "config": workload_config(a, f"replicas x{ws}"),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "gemm_tc_kernel (split-precision tcgen05 product)",
+                     "note": f"algorithmic 2n^3 per product (n^3 when symmetric-output) over CUDA-event time of "
+                             f"{int(gemm_launches)} launches; each split product runs 3 half-precision "
+                             f"tensor products, so tensor-pipe work is 3x the algorithmic flops; peak = "
+                             f"{src} sustained bf16"},
+        "foe_tflops": (gemm_flops / sec / 1e12) if sec > 0 else None,
+        "gemm_time_share": (gemm_ms / ms) if ms > 0 else None,
+        "per_step": {"mu_passes": units[0] / a.steps, "products": units[3] / a.steps,
+                     "probes": float(st1[2])},
+        "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "parity": parity,
+        "fp64_gpu": fp64,
+        "init_scf_s": t_scf,
+        "wall_s": wall,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

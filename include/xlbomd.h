@@ -86,6 +86,13 @@ typedef struct {
   double diverge_tol;      /* max |q - n| above which a step reports ERR_DIVERGED */
   int prec;                /* xlbomd_prec */
   int energy_every;        /* energy monitor every k steps inside xlbomd_step (0 = never) */
+  int scf_mode;            /* t0 SCF: 0 = linear mixing, 1 = n <- n - K_m (q - n) with the rank-m
+                              kernel (Eq. SCF_K), for systems whose charge sloshing is too stiff
+                              for linear mixing */
+  int kernel_auto;         /* 1: at the start of xlbomd_scf, set c of J_0 = c I per system to
+                              1.2 x the most negative eigenvalue of dq/dn (power iteration on
+                              the response, 12 probes), so that K_0 = (c - 1)^-1 I keeps the
+                              stiffest charge mode stable */
 } xlbomd_params;
 
 /* One trajectory.  R and V are natoms x 3 row-major (A, A/fs), Z natoms
@@ -129,8 +136,9 @@ void xlbomd_default_params(xlbomd_params* p);
 xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* systems, int nsys,
                           void* cuda_stream, xlbomd_ctx** out);
 
-/* t0 ground state of system sys (Eq. IBC): linear-mixing SCF
- * n <- n + mix_alpha (q[n] - n) (Eq. SCF_K with K_0) to max|q - n| < scf_tol,
+/* t0 ground state of system sys (Eq. IBC): SCF to max|q - n| < scf_tol by
+ * linear mixing n <- n + mix_alpha (q[n] - n) (Eq. SCF_K with K_0, scf_mode 0)
+ * or by n <- n - K_m (q[n] - n) with the rank-m kernel (Eq. SCF_K, scf_mode 1);
  * then n-history = n(t0), forces and K r at t0.  sys = -1: every system. */
 xlbomd_status xlbomd_scf(xlbomd_ctx* ctx, int sys);
 
@@ -171,6 +179,17 @@ xlbomd_status xlbomd_sizes(xlbomd_ctx* ctx, int sys, int* natoms, int* n_orb, in
  * result[2] = device wait-timeout flag, result[3] = ms per product.
  * This is a check of the matrix-product engine; the paper has no counterpart. */
 xlbomd_status xlbomd_selftest_gemm(int n, int prec, int sym, double* result);
+
+/* Diagnostics: number of CUDA kernels the library has launched since it was
+ * loaded (all contexts). */
+long long xlbomd_launch_count(void);
+
+/* Diagnostics: CUDA-event timing of the matrix products of a context, taken
+ * on the context's stream.  mode 1 = start (reset) recording, 0 = stop,
+ * 2 = collect (synchronises) out[0] = products recorded, out[1] = their total
+ * device time in ms, out[2] = their algorithmic flops (2 n^3, half for a
+ * symmetric-output product).  The paper has no counterpart. */
+xlbomd_status xlbomd_gemm_profile(xlbomd_ctx* ctx, int mode, double* out);
 
 xlbomd_status xlbomd_clear_error(xlbomd_ctx* ctx);
 const char* xlbomd_last_error(xlbomd_ctx* ctx);

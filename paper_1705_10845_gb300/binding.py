@@ -36,7 +36,8 @@ class Params(C.Structure):
         ("kmax", C.c_int), ("rank_m", C.c_int), ("kernel_c", C.c_double), ("mix_alpha", C.c_double),
         ("scf_tol", C.c_double), ("scf_max_iter", C.c_int), ("mu_tol", C.c_double),
         ("mu_max_iter", C.c_int), ("diverge_tol", C.c_double), ("prec", C.c_int),
-        ("energy_every", C.c_int),
+        ("energy_every", C.c_int), ("scf_mode", C.c_int),
+        ("kernel_auto", C.c_int),
     ]
 
 
@@ -76,6 +77,10 @@ def load(path: str | None = None):
     lib.xlbomd_last_error.argtypes = [P]
     lib.xlbomd_last_error.restype = C.c_char_p
     lib.xlbomd_free.argtypes = [P]
+    lib.xlbomd_launch_count.argtypes = []
+    lib.xlbomd_launch_count.restype = C.c_longlong
+    lib.xlbomd_gemm_profile.argtypes = [P, I, DP]
+    lib.xlbomd_gemm_profile.restype = C.c_int
     lib.xlbomd_selftest_gemm.argtypes = [I, I, I, DP]
     lib.xlbomd_selftest_gemm.restype = C.c_int
     for name in ("xlbomd_init", "xlbomd_scf", "xlbomd_build_H", "xlbomd_density", "xlbomd_kernel_update",
@@ -105,6 +110,11 @@ def default_params(**overrides) -> Params:
 
 def _dptr(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def launch_count() -> int:
+    """Kernels launched by libxlbomd.so since it was loaded."""
+    return int(load().xlbomd_launch_count())
 
 
 def selftest_gemm(n: int, prec: str = "fp16x3", sym: bool = False):
@@ -200,6 +210,12 @@ class Context:
     def set(self, sys, what, values):
         a = np.ascontiguousarray(values, dtype=np.float64).reshape(-1)
         self._check(self._lib.xlbomd_set(self.h, sys, what, _dptr(a)), "xlbomd_set")
+
+    def gemm_profile(self, mode: int):
+        """mode 1 start, 0 stop, 2 collect -> (launches, total ms, algorithmic flops)."""
+        out = np.zeros(3)
+        self._check(self._lib.xlbomd_gemm_profile(self.h, mode, _dptr(out)), "xlbomd_gemm_profile")
+        return tuple(out) if mode == 2 else None
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -16,6 +17,8 @@
 #include "precision.h"
 
 using namespace xl;
+
+std::atomic<long long> xl::g_launch_count{0};
 
 namespace {
 
@@ -38,6 +41,7 @@ struct Sys {
   double mu_hist[3] = {0, 0, 0};
   int n_mu_hist = 0;
   double dmu_last = 0.0;
+  double kc = 0.0;          // c of J_0 = c I for this system
   bool have_density = false;
   int probes_used = 0;
   double stats[5] = {0, 0, 0, 0, 0};
@@ -59,6 +63,15 @@ struct xlbomd_ctx {
 };
 
 namespace {
+
+bool debug_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("XLBOMD_DEBUG");
+    v = (e && e[0] && e[0] != '0') ? 1 : 0;
+  }
+  return v == 1;
+}
 
 xlbomd_status fail(xlbomd_ctx* c, xlbomd_status st, const std::string& m) {
   if (c) {
@@ -251,9 +264,17 @@ xlbomd_status density(xlbomd_ctx* ctx, Sys& S, bool with_forces) {
       blo = std::max(blo, mu);
     else
       bhi = std::min(bhi, mu);
+    const double dmu_prev = dmu;
     dmu = (trDmu > 0.0) ? (S.nocc - trD) / trDmu : 0.0;
     S.stats[0] += 1;
+    if (debug_enabled())
+      std::fprintf(stderr, "[xlbomd] mu pass %d: mu %.12f trD %.10f (nocc %.1f) trDmu %.6e dmu %.3e bracket [%.6f, %.6f] t0max %.4e\n",
+                   pass, mu, trD, S.nocc, trDmu, dmu, blo, bhi, t0max);
     if (std::fabs(dmu) * beta < p.mu_tol) break;
+    // Newton converges quadratically; once a step is not much smaller than
+    // the previous one (and already small), the rounding noise of the
+    // product arithmetic has been reached: keep the first-order correction.
+    if (pass >= 1 && std::fabs(dmu) * beta < 0.05 && std::fabs(dmu) > 0.25 * std::fabs(dmu_prev)) break;
     double next = mu + dmu;
     if (!(trDmu > 0.0) || !(next > blo && next < bhi)) next = 0.5 * (blo + bhi);
     mu = next;
@@ -292,13 +313,13 @@ xlbomd_status kernel_update(xlbomd_ctx* ctx, Sys& S) {
   const xlbomd_params& p = ctx->p;
   int m = 0;
   for (int i = 0; i < p.rank_m; ++i) {
-    CK(launch_kernel_vec(st, 0, S.nat, i, p.kernel_c, S.r, S.pV, S.pW, nullptr, S.scal + 8));
+    CK(launch_kernel_vec(st, 0, S.nat, i, S.kc, S.r, S.pV, S.pW, nullptr, S.scal + 8));
     CKS(sync_read(ctx, S.scal + 8, 1));
     if (ctx->pinned[0] != 1.0) break;
     CKS(response(ctx, S, S.pV + (size_t)i * S.nat, S.pW + (size_t)i * S.nat));
     m = i + 1;
   }
-  CK(launch_kernel_vec(st, 1, S.nat, m, p.kernel_c, S.r, S.pV, S.pW, S.Kr, S.scal + 8));
+  CK(launch_kernel_vec(st, 1, S.nat, m, S.kc, S.r, S.pV, S.pW, S.Kr, S.scal + 8));
   S.probes_used = m;
   S.stats[2] = m;
   return XLBOMD_OK;
@@ -320,6 +341,49 @@ xlbomd_status energy(xlbomd_ctx* ctx, Sys& S) {
   return XLBOMD_OK;
 }
 
+// Most negative eigenvalue of J = dq/dn by power iteration on the response
+// (J has real non-positive spectrum: it is similar to -g^(1/2) chi g^(1/2)).
+xlbomd_status stiffest_mode(xlbomd_ctx* ctx, Sys& S, double* lambda) {
+  cudaStream_t st = ctx->stream;
+  std::vector<double> v(S.nat);
+  for (int I = 0; I < S.nat; ++I) v[I] = ((I * 7919) % 17) - 8.0;
+  double mean = 0.0;
+  for (double x : v) mean += x;
+  mean /= S.nat;
+  double nv = 0.0;
+  for (double& x : v) {
+    x -= mean;
+    nv += x * x;
+  }
+  nv = std::sqrt(nv);
+  if (nv == 0.0) {
+    *lambda = 0.0;
+    return XLBOMD_OK;
+  }
+  for (double& x : v) x /= nv;
+  double* dv = S.pV + (size_t)kMaxRank * S.nat;   // spare probe rows
+  double* dw = S.pW + (size_t)kMaxRank * S.nat;
+  double lam = 0.0;
+  std::vector<double> w(S.nat);
+  for (int it = 0; it < 12; ++it) {
+    CK(cudaMemcpyAsync(dv, v.data(), sizeof(double) * S.nat, cudaMemcpyHostToDevice, st));
+    CKS(response(ctx, S, dv, dw));
+    CK(cudaMemcpyAsync(w.data(), dw, sizeof(double) * S.nat, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double dot = 0.0, nw = 0.0;
+    for (int I = 0; I < S.nat; ++I) {
+      dot += v[I] * w[I];
+      nw += w[I] * w[I];
+    }
+    nw = std::sqrt(nw);
+    lam = dot;
+    if (!(nw > 0.0) || !std::isfinite(nw)) break;
+    for (int I = 0; I < S.nat; ++I) v[I] = w[I] / nw;
+  }
+  *lambda = lam;
+  return XLBOMD_OK;
+}
+
 xlbomd_status scf(xlbomd_ctx* ctx, Sys& S) {
   cudaStream_t st = ctx->stream;
   const xlbomd_params& p = ctx->p;
@@ -327,16 +391,28 @@ xlbomd_status scf(xlbomd_ctx* ctx, Sys& S) {
     CK(launch_gemv(st, S.nat, S.gam, S.natp, S.nh, S.pot));
     CK(launch_apply_potential(st, S.nat, S.np, S.H0, S.pot, S.H));
     CKS(density(ctx, S, false));
+    if (it == 0 && p.kernel_auto) {
+      double lam = 0.0;
+      CKS(stiffest_mode(ctx, S, &lam));
+      if (lam < 0.0) S.kc = 1.2 * lam;
+      if (debug_enabled()) std::fprintf(stderr, "[xlbomd] stiffest mode %.4f -> c = %.4f\n", lam, S.kc);
+    }
     CK(launch_absmax(st, S.nat, S.r, S.scal + 9));
     CKS(sync_read(ctx, S.scal + 9, 1));
     const double res = ctx->pinned[0];
+    if (debug_enabled()) std::fprintf(stderr, "[xlbomd] scf it %d max|q - n| %.3e mu %.8f\n", it, res, S.mu);
     if (!std::isfinite(res) || res > 1e3) return fail(ctx, XLBOMD_ERR_DIVERGED, "t0 SCF diverged");
     if (res < p.scf_tol) {
       CK(launch_fill_history(st, S.nat, p.kmax, S.nh));
       CK(launch_forces(st, model_of(p), S.nat, S.L, S.eta, S.ng, S.G4, S.R, S.Dm, S.np, S.q, S.nh, S.F, S.work));
       return kernel_update(ctx, S);
     }
-    CK(launch_axpy(st, S.nat, p.mix_alpha, S.r, S.nh));
+    if (p.scf_mode == 1 && p.rank_m > 0) {
+      CKS(kernel_update(ctx, S));                      // n <- n - K_m r (Eq. SCF_K)
+      CK(launch_axpy(st, S.nat, -1.0, S.Kr, S.nh));
+    } else {
+      CK(launch_axpy(st, S.nat, p.mix_alpha, S.r, S.nh));
+    }
   }
   return fail(ctx, XLBOMD_ERR_NOT_CONVERGED, "t0 SCF did not converge");
 }
@@ -406,6 +482,8 @@ void xlbomd_default_params(xlbomd_params* p) {
   p->diverge_tol = 1.0;
   p->prec = XLBOMD_FP64;
   p->energy_every = 0;
+  p->scf_mode = 0;
+  p->kernel_auto = 0;
 }
 
 xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* systems, int nsys, void* cuda_stream,
@@ -414,7 +492,7 @@ xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* syst
   *out = nullptr;
   const xlbomd_params& p = *params;
   if (p.n_sq < 1 || p.n_sq > 40 || p.kmax < 1 || p.kmax > 7 || p.rank_m < 0 || p.rank_m > kMaxRank ||
-      p.kernel_c == 1.0 || !(p.Te > 0) || !(p.dt > 0) || p.mu_max_iter < 1)
+      p.kernel_c == 1.0 || !(p.Te > 0) || !(p.dt > 0) || p.mu_max_iter < 1 || p.scf_mode < 0 || p.scf_mode > 1)
     return XLBOMD_ERR_ARG;
   if (p.prec != XLBOMD_FP64 && p.prec != XLBOMD_FP16x3 && p.prec != XLBOMD_BF16x3) return XLBOMD_ERR_ARG;
   for (int i = 0; i < nsys; ++i) {
@@ -448,6 +526,7 @@ xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* syst
     S.natp = (S.nat + 63) / 64 * 64;
     S.L = s.box_L;
     S.mass = s.mass;
+    S.kc = p.kernel_c;
     double zs = 0;
     for (int a = 0; a < S.nat; ++a) zs += s.Z[a];
     S.nocc = 0.5 * zs;
@@ -657,6 +736,25 @@ xlbomd_status xlbomd_clear_error(xlbomd_ctx* ctx) {
 const char* xlbomd_last_error(xlbomd_ctx* ctx) {
   if (!ctx) return "null context";
   return ctx->msg.c_str();
+}
+
+long long xlbomd_launch_count(void) { return g_launch_count.load(); }
+
+xlbomd_status xlbomd_gemm_profile(xlbomd_ctx* ctx, int mode, double* out) {
+  if (!ctx) return XLBOMD_ERR_ARG;
+  Engine& E = *ctx->eng;
+  if (mode == 0) {
+    E.prof = false;
+  } else if (mode == 1) {
+    E.prof = true;
+    E.prof_reset();
+  } else if (mode == 2) {
+    if (!out) return fail(ctx, XLBOMD_ERR_ARG, "null output");
+    CK(E.prof_collect(out));
+  } else {
+    return fail(ctx, XLBOMD_ERR_ARG, "unknown profile mode");
+  }
+  return XLBOMD_OK;
 }
 
 xlbomd_status xlbomd_selftest_gemm(int n, int prec, int sym, double* result) {

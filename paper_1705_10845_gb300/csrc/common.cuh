@@ -2,10 +2,15 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
+#include <atomic>
 #include <cstdint>
 #include <cstddef>
 
 namespace xl {
+
+// Number of kernels this library has launched (all contexts, all streams).
+extern std::atomic<long long> g_launch_count;
+inline void note_launch() { g_launch_count.fetch_add(1, std::memory_order_relaxed); }
 
 constexpr int kMaxRank = 8;
 constexpr double kPi = 3.14159265358979323846;

@@ -20,14 +20,16 @@ namespace {
     if (e_ != cudaSuccess) return e_;     \
   } while (0)
 
-cudaError_t gemm(cudaStream_t s, int np, const double* A, const double* B, double* C, const EpiF64& e, bool sym,
-                 double* stats) {
-  if (stats) stats[3] += sym ? 0.5 : 1.0;
-  return gemm_f64_nt(s, np, np, np, A, np, B, np, C, np, e, sym);
-}
-
 class EngineF64 : public Engine {
  public:
+  cudaError_t gemm(cudaStream_t s, int np, const double* A, const double* B, double* C, const EpiF64& e, bool sym,
+                   double* stats) {
+    if (stats) stats[3] += sym ? 0.5 : 1.0;
+    RET(prof_begin(s));
+    RET(gemm_f64_nt(s, np, np, np, A, np, B, np, C, np, e, sym));
+    return prof_end(s, 2.0 * (double)np * np * np * (sym ? 0.5 : 1.0));
+  }
+
   cudaError_t foe(cudaStream_t s, MatSet& m, const double* H, int N, double mu, double sc,
                   const std::vector<int>& ns, const std::vector<double>& nc, double* stats) override {
     const int np = m.np, n = m.n;

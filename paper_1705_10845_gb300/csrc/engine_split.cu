@@ -167,6 +167,7 @@ class EngineSplit : public Engine {
       convert_split_kernel<true><<<g, 256, 0, s>>>(count, m.f, m.amax, m.hi, m.lo, m.scale);
     else
       convert_split_kernel<false><<<g, 256, 0, s>>>(count, m.f, m.amax, m.hi, m.lo, m.scale);
+    note_launch();
     return cudaGetLastError();
   }
 
@@ -211,7 +212,9 @@ class EngineSplit : public Engine {
     a.sb = B.scale;
     a.err = err_;
     const int n128 = tl.second.first, n256 = tl.second.second;
+    RET(prof_begin(s));
     RET(gemm_tc(s, np, A.hi, A.lo, B.hi, B.lo, a, tl.first, tl.first + 2 * n128, n128, n256));
+    RET(prof_end(s, 2.0 * (double)np * np * np * (sym ? 0.5 : 1.0)));
     if (stats) stats[3] += sym ? 0.5 : 1.0;
     return convert(s, C, np);
   }
@@ -222,6 +225,7 @@ class EngineSplit : public Engine {
     const size_t cnt = (size_t)np * np;
     RET(cudaMemsetAsync(m.sT[0].amax, 0, sizeof(unsigned), s));
     t0_init_f32_kernel<<<nblk(cnt), 256, 0, s>>>(N, np, H, mu, sc, m.sT[0].f, m.sT[0].amax);
+    note_launch();
     RET(cudaGetLastError());
     RET(convert(s, m.sT[0], np));
     for (int k = 0; k < n; ++k) {
@@ -232,6 +236,7 @@ class EngineSplit : public Engine {
         axpi_f32_kernel<<<nblk(cnt), 256, 0, s>>>(np, 1.f, -1.f, m.sS.f, Y.f, Y.amax);
       else
         axpi_f32_kernel<<<nblk(cnt), 256, 0, s>>>(np, 0.f, (float)nc[k], m.sY[k - 1].f, Y.f, Y.amax);
+      note_launch();
       RET(cudaGetLastError());
       RET(convert(s, Y, np));
       for (int it = 0; it < ns[k]; ++it) {
@@ -256,6 +261,7 @@ class EngineSplit : public Engine {
       RET(cudaMemsetAsync(m.sA1.amax, 0, sizeof(unsigned), s));
       if (k == 0) {
         level0_A1_f32_kernel<<<nblk(cnt), 256, 0, s>>>(np, m.sT[0].f, dvec, m.sA1.f, m.sA1.amax);
+        note_launch();
         RET(cudaGetLastError());
         RET(convert(s, m.sA1, np));
         RET(gemm(s, np, m.sT[1], m.sA1, m.sMt, -1.f, nullptr, 0.f, 0.f, dvec, 2.f, false, stats));
@@ -263,18 +269,21 @@ class EngineSplit : public Engine {
         RET(gemm(s, np, m.sT[k], *T1, m.sG, 1.f, nullptr, 0.f, 0.f, nullptr, 1.f, false, stats));
         dim3 grid(np / 32, np / 32), block(32, 8);
         transpose_add_f32_kernel<<<grid, block, 0, s>>>(np, m.sG.f, m.sA1.f, m.sA1.amax);
+        note_launch();
         RET(cudaGetLastError());
         RET(convert(s, m.sA1, np));
         RET(gemm(s, np, m.sT[k + 1], m.sA1, m.sMt, -1.f, T1, 2.f, 0.f, nullptr, 1.f, false, stats));
       }
       if (last && !full_last) {
         row_dot_f32_kernel<<<(N + 7) / 8, 256, 0, s>>>(N, np, m.sY[k].f, m.sMt.f, out_diag);
+        note_launch();
         return cudaGetLastError();
       }
       SplitMat* dst = (last && full_last) ? &m.sTmu : T1n;
       RET(gemm(s, np, m.sY[k], m.sMt, *dst, 1.f, nullptr, 0.f, 0.f, nullptr, 1.f, true, stats));
       if (last) {
         get_diag_f32_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, np, dst->f, out_diag);
+        note_launch();
         return cudaGetLastError();
       }
       T1n = T1;
@@ -285,18 +294,21 @@ class EngineSplit : public Engine {
 
   cudaError_t trace_tn(cudaStream_t s, MatSet& m, int N, double* out) override {
     diag_sum_f32_kernel<<<1, 1024, 0, s>>>(N, m.np, m.sT[m.n].f, out);
+    note_launch();
     return cudaGetLastError();
   }
 
   cudaError_t density_out(cudaStream_t s, MatSet& m, int N, double dmu, const double*, double* ddiag,
                           double* D) override {
     density_out_f32_kernel<<<nblk((size_t)m.np * m.np), 256, 0, s>>>(N, m.np, m.sT[m.n].f, m.sTmu.f, dmu, ddiag, D);
+    note_launch();
     return cudaGetLastError();
   }
 
   cudaError_t entropy(cudaStream_t s, MatSet&, int, double, int, double, double, const double*, const double*,
                       double*, double* out) override {
     fill_nan_kernel<<<1, 1, 0, s>>>(out);
+    note_launch();
     return cudaGetLastError();
   }
 
@@ -450,9 +462,13 @@ int selftest_gemm(int n, int prec, int sym, double* result) {
       alloc_split(sc, n, scal + 2, (unsigned*)scal + 5))
     goto done;
   fill_random_kernel<<<nblk(cnt), 256>>>(cnt, n, 11, 0, A);
+  note_launch();
   fill_random_kernel<<<nblk(cnt), 256>>>(cnt, n, 23, sym, B);
+  note_launch();
   to_f32_kernel<<<nblk(cnt), 256>>>(cnt, A, sa.f, sa.amax);
+  note_launch();
   to_f32_kernel<<<nblk(cnt), 256>>>(cnt, B, sb.f, sb.amax);
+  note_launch();
   if (eng.convert(s, sa, n) || eng.convert(s, sb, n)) goto done;
   {
     EpiF64 e;
@@ -469,6 +485,7 @@ int selftest_gemm(int n, int prec, int sym, double* result) {
   cudaEventElapsedTime(&ms, e0, e1);
   cudaMemset(out, 0, 8);
   max_abs_diff_kernel<<<304, 256>>>(cnt, sc.f, Cref, out);
+  note_launch();
   if (cudaDeviceSynchronize() != cudaSuccess) goto done;
   {
     double h[1];

@@ -106,10 +106,12 @@ __global__ void entropy_combine_kernel(EntW w, const double* __restrict__ ld, co
 cudaError_t logdet_spd(cudaStream_t s, double* W, int np, double* part, double* out) {
   for (int kb = 0; kb < np; kb += CB) {
     chol_panel_kernel<<<1, 256, 0, s>>>(W, np, kb, part);
+    note_launch();
     RET(cudaGetLastError());
     const int rest = np - kb - CB;
     if (rest > 0) {
       chol_trsm_kernel<<<rest / CB, CB, 0, s>>>(W, np, kb);
+      note_launch();
       RET(cudaGetLastError());
       EpiF64 e;
       e.alpha = -1.0;
@@ -142,6 +144,7 @@ cudaError_t launch_entropy_f64(cudaStream_t s, MatSet& m, int N, double beta, in
   const size_t count = (size_t)np * np;
   // logdet(I - T_0)
   ident_minus_f64_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(count, np, m.T[0], m.G);
+  note_launch();
   RET(cudaGetLastError());
   RET(logdet_spd(s, m.G, np, part, ld + 0));
   // logdet(Y_k)
@@ -170,6 +173,7 @@ cudaError_t launch_entropy_f64(cudaStream_t s, MatSet& m, int N, double beta, in
   for (int j = 0; j < 6; ++j) w.w_tr[j] = std::ldexp(1.0, n_sq + 1) / (2.0 * j + 1.0);
   w.cst = N * std::log(2.0);
   entropy_combine_kernel<<<1, 32, 0, s>>>(w, ld, tr, out);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -290,58 +290,69 @@ inline unsigned blocks_for(size_t count, int tpb) { return (unsigned)((count + t
 
 cudaError_t launch_expand_potential(cudaStream_t s, int nat, int np, double scale, const double* pot, double* dvec) {
   expand_potential_kernel<<<blocks_for(np, 256), 256, 0, s>>>(nat, np, scale, pot, dvec);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_response_finish(cudaStream_t s, int nat, int N, const double* d1, const double* dmu,
                                    double* scal, double* w) {
   response_finish_kernel<<<1, 1024, 0, s>>>(nat, N, d1, dmu, scal, w);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_absmax(cudaStream_t s, int n, const double* x, double* out) {
   absmax_kernel<<<1, 1024, 0, s>>>(n, x, out);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_fill_history(cudaStream_t s, int nat, int kmax, double* nh) {
   fill_history_kernel<<<blocks_for(nat, 128), 128, 0, s>>>(nat, kmax, nh);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpy(cudaStream_t s, int n, double a, const double* x, double* y) {
   axpy_kernel<<<blocks_for(n, 128), 128, 0, s>>>(n, a, x, y);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_diag_sum(cudaStream_t s, int n, int np, const double* X, double* out) {
   diag_sum_kernel<<<1, 1024, 0, s>>>(n, np, X, out);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_density_out_f64(cudaStream_t s, int N, int np, const double* Tn, const double* Tmu, double dmu,
                                    double* ddiag, double* D) {
   density_out_kernel<<<blocks_for((size_t)np * np, 256), 256, 0, s>>>(N, np, Tn, Tmu, dmu, ddiag, D);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_t0_init(cudaStream_t s, int n, int np, const double* H, double mu, double scale, double* T0) {
   t0_init_kernel<<<blocks_for((size_t)np * np, 256), 256, 0, s>>>(n, np, H, mu, scale, T0);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_ident_minus(cudaStream_t s, int np, const double* S, double* Y) {
   ident_minus_kernel<<<blocks_for((size_t)np * np, 256), 256, 0, s>>>(np, S, Y);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_scale(cudaStream_t s, size_t count, double c, const double* X, double* Y) {
   scale_kernel<<<blocks_for(count, 256), 256, 0, s>>>(count, c, X, Y);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_level0_A1(cudaStream_t s, int np, const double* T0, const double* d, double* A1) {
   level0_A1_kernel<<<blocks_for((size_t)np * np, 256), 256, 0, s>>>(np, T0, d, A1);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -349,21 +360,25 @@ cudaError_t launch_transpose_add(cudaStream_t s, int np, const double* G, double
   if (np % 32) return cudaErrorInvalidValue;
   dim3 grid(np / 32, np / 32), block(32, 8);
   transpose_add_kernel<<<grid, block, 0, s>>>(np, G, A1);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_row_dot(cudaStream_t s, int n, int np, const double* Y, const double* M, double* out) {
   row_dot_kernel<<<(n + 7) / 8, 256, 0, s>>>(n, np, Y, M, out);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_get_diag(cudaStream_t s, int n, int np, const double* X, double* out) {
   get_diag_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, np, X, out);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_sum(cudaStream_t s, int n, const double* x, double* out) {
   sum_kernel<<<1, 1024, 0, s>>>(n, x, out);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -371,13 +386,16 @@ cudaError_t launch_frob_dot(cudaStream_t s, int n, int np, const double* A, cons
                             double* out) {
   const int nb = n < 1024 ? n : 1024;
   frob_partial_kernel<<<nb, 256, 0, s>>>(n, np, A, B, work);
+  note_launch();
   sum_kernel<<<1, 1024, 0, s>>>(nb, work, out);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_kernel_vec(cudaStream_t s, int mode, int nat, int m, double c, const double* r, double* V,
                               const double* W, double* out, double* flag) {
   kernel_vec_kernel<<<1, 1024, 0, s>>>(mode, nat, m, c, r, V, W, out, flag);
+  note_launch();
   return cudaGetLastError();
 }
 

@@ -90,9 +90,11 @@ cudaError_t gemm_f64_nt(cudaStream_t s, int M, int N, int K, const double* A, in
     if (M != N) return cudaErrorInvalidValue;
     const int nt = N / BN;
     gemm_f64_kernel<true><<<nt * (nt + 1) / 2, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, e);
+    note_launch();
   } else {
     dim3 grid(N / BN, M / BM);
     gemm_f64_kernel<false><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, e);
+    note_launch();
   }
   return cudaGetLastError();
 }

@@ -8,10 +8,16 @@
 // Per CTA: one 128 x BN output tile.  Warp 0 issues TMA loads (128-byte
 // swizzle, K-major) into a STAGES-deep ring guarded by mbarriers; warp 1
 // allocates TMEM and one elected thread issues tcgen05.mma (M = 128,
-// N = BN, K = 16) per 32-byte K step; warps 2-5 wait for the accumulator,
-// read it with tcgen05.ld (32 lanes x 32 columns per load), apply the
+// N = BN, K = 16) per 32-byte K step; warps 2-5 wait for the accumulators,
+// read them with tcgen05.ld (32 lanes x 32 columns per load), apply the
 // epilogue and store FP32 rows (and the mirrored columns of a symmetric
-// product).  Every mbarrier wait is bounded: on timeout the kernel records an
+// product).
+//
+// The tensor core adds each K = 16 step into its FP32 accumulator with
+// truncation, so a small term added to a large accumulator loses bits.  The
+// hi*hi segment and the two correction segments (hi*lo, lo*hi, about 2^-11
+// smaller) therefore go to two separate TMEM accumulators (2 x BN columns)
+// that the epilogue adds in FP32.  Every mbarrier wait is bounded: on timeout the kernel records an
 // error code and leaves its loops, and TMEM is always released.
 #include <cuda.h>
 
@@ -123,7 +129,7 @@ __global__ void __launch_bounds__(192, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                    const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, TcArgs a) {
   constexpr int B_BYTES = BN * BK * 2;
-  constexpr uint32_t TMEM_COLS = BN;   // 128 or 256 (power of two >= 32)
+  constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators: 256 or 512 columns
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -198,11 +204,14 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const bool corr = kb >= nk;                       // hi*lo or lo*hi segment
+        const uint32_t dcol = corr ? (uint32_t)BN : 0u;
+        const bool first = (kb == 0) || (kb == nk);
 #pragma unroll
         for (int j = 0; j < BK / 16; ++j) {
           const uint64_t ad = smem_desc(sA + s * A_BYTES + j * 32);
           const uint64_t bd = smem_desc(sB + s * B_BYTES + j * 32);
-          mma_f16(tmem, ad, bd, idesc, (kb > 0 || j > 0) ? 1u : 0u);
+          mma_f16(tmem + dcol, ad, bd, idesc, (first && j == 0) ? 0u : 1u);
         }
         mma_commit(&empty[s]);
       }
@@ -222,6 +231,12 @@ __global__ void __launch_bounds__(192, 1)
       for (int ch = 0; ch < BN / 32; ++ch) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 32), v);
+        if (a.nseg > 1) {
+          float w[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(BN + ch * 32), w);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] += w[i];
+        }
         const int col0 = tn * BN + ch * 32;
         const float* er = a.E ? a.E + (size_t)row * a.ldc + col0 : nullptr;
         float* cr = a.C + (size_t)row * a.ldc + col0;
@@ -370,6 +385,7 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
       attr = true;
     }
     gemm_tc_kernel<256><<<nblocks, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, args);
+    note_launch();
   } else {
     static bool attr = false;
     const int sb = smem_bytes<128>();
@@ -379,6 +395,7 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
       attr = true;
     }
     gemm_tc_kernel<128><<<nblocks, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, args);
+    note_launch();
   }
   return cudaGetLastError();
 }

@@ -426,6 +426,7 @@ cudaError_t launch_build_H0(cudaStream_t s, const ModelConst& m, int nat, double
                             int np) {
   const int wpb = 8;
   build_H0_kernel<<<(nat + wpb - 1) / wpb, 32 * wpb, 0, s>>>(m, nat, L, R, H0, np);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -433,6 +434,7 @@ cudaError_t launch_gamma_real(cudaStream_t s, const ModelConst& m, int nat, doub
                               double* gam, int natp) {
   dim3 grid((natp + 127) / 128, nat);
   gamma_real_kernel<<<grid, 128, 0, s>>>(m, nat, L, eta, R, gam, natp);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -441,12 +443,14 @@ cudaError_t launch_structure_factors(cudaStream_t s, int nat, int ng, const doub
   const int natp = (nat + 63) / 64 * 64;
   dim3 grid((kp + 127) / 128, natp);
   structure_factor_kernel<<<grid, 128, 0, s>>>(nat, ng, G4, R, SF, kp, natp);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_gemv(cudaStream_t s, int nat, const double* gam, int natp, const double* x, double* y) {
   const int wpb = 8;
   gemv_kernel<<<(nat + wpb - 1) / wpb, 32 * wpb, 0, s>>>(nat, gam, natp, x, y);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -455,13 +459,16 @@ cudaError_t launch_apply_potential(cudaStream_t s, int nat, int np, const double
   cudaError_t e = cudaMemcpyAsync(H, H0, sizeof(double) * (size_t)np * np, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
   add_potential_kernel<<<(4 * nat + 255) / 256, 256, 0, s>>>(nat, np, pot, H);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_gershgorin(cudaStream_t s, int n, int np, const double* H, double* out) {
   // out[0..1] result; out[2 .. 2+2n) scratch
   gershgorin_rows_kernel<<<n, 256, 0, s>>>(n, np, H, out + 2);
+  note_launch();
   minmax_kernel<<<1, 1024, 0, s>>>(n, out + 2, out);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -471,10 +478,14 @@ cudaError_t launch_forces(cudaStream_t s, const ModelConst& m, int nat, double L
   const int wpb = 8;
   const int nb = (nat + wpb - 1) / wpb;
   forces_band_kernel<<<nb, 32 * wpb, 0, s>>>(m, nat, L, R, D, np, F);
+  note_launch();
   if (m.k != 0.0) {
     forces_coul_real_kernel<<<nb, 32 * wpb, 0, s>>>(m, nat, L, eta, R, q, n, F);
+    note_launch();
     coul_sums_kernel<<<ng, 256, 0, s>>>(nat, ng, G4, R, q, n, work);
+    note_launch();
     forces_coul_recip_kernel<<<nb, 32 * wpb, 0, s>>>(m.k, nat, ng, G4, R, q, n, work, F);
+    note_launch();
   }
   return cudaGetLastError();
 }
@@ -482,6 +493,7 @@ cudaError_t launch_forces(cudaStream_t s, const ModelConst& m, int nat, double L
 cudaError_t launch_charges(cudaStream_t s, int nat, const double* ddiag, const double* Z, const double* n,
                            double* q, double* r) {
   charges_kernel<<<(nat + 127) / 128, 128, 0, s>>>(nat, ddiag, Z, n, q, r);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -489,17 +501,20 @@ cudaError_t launch_verlet_first(cudaStream_t s, int nat, double L, double dt, do
                                 const double* F, double* nh, int kmax, const double* Kr, double kappa,
                                 double alpha, const double* c) {
   verlet_first_kernel<<<(nat + 127) / 128, 128, 0, s>>>(nat, L, dt, minv, R, V, F, nh, kmax, Kr, kappa, alpha, c);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_verlet_second(cudaStream_t s, int nat, double dt, double minv, double* V, const double* F) {
   verlet_second_kernel<<<(3 * nat + 127) / 128, 128, 0, s>>>(nat, dt, minv, V, F);
+  note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_energy_vec(cudaStream_t s, int nat, const double* q, const double* n, const double* pot,
                               const double* V, double mass, double* out) {
   energy_vec_kernel<<<1, 1024, 0, s>>>(nat, q, n, pot, V, mass, out);
+  note_launch();
   return cudaGetLastError();
 }
 

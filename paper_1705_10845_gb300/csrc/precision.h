@@ -41,7 +41,48 @@ void free_matset(MatSet& m);
 
 class Engine {
  public:
-  virtual ~Engine() {}
+  virtual ~Engine() {
+    for (auto e : ev_) cudaEventDestroy(e);
+  }
+  // Timing of the matrix products with CUDA events on their stream.
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_;
+  std::vector<double> prof_flops_;
+  size_t nprof_ = 0;
+  void prof_reset() { nprof_ = 0; }
+  cudaError_t prof_begin(cudaStream_t s) {
+    if (!prof) return cudaSuccess;
+    while (ev_.size() < 2 * (nprof_ + 1)) {
+      cudaEvent_t e;
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return r;
+      ev_.push_back(e);
+    }
+    return cudaEventRecord(ev_[2 * nprof_], s);
+  }
+  cudaError_t prof_end(cudaStream_t s, double flops) {
+    if (!prof) return cudaSuccess;
+    cudaError_t r = cudaEventRecord(ev_[2 * nprof_ + 1], s);
+    if (prof_flops_.size() <= nprof_) prof_flops_.resize(nprof_ + 1);
+    prof_flops_[nprof_++] = flops;
+    return r;
+  }
+  // out = [launches, total ms, algorithmic flops]
+  cudaError_t prof_collect(double* out) {
+    out[0] = (double)nprof_;
+    out[1] = 0.0;
+    out[2] = 0.0;
+    for (size_t i = 0; i < nprof_; ++i) {
+      cudaError_t r = cudaEventSynchronize(ev_[2 * i + 1]);
+      if (r != cudaSuccess) return r;
+      float ms = 0.f;
+      r = cudaEventElapsedTime(&ms, ev_[2 * i], ev_[2 * i + 1]);
+      if (r != cudaSuccess) return r;
+      out[1] += ms;
+      out[2] += prof_flops_[i];
+    }
+    return cudaSuccess;
+  }
   // T_0 = -sc (H - mu I); n levels T_{k+1} = 2 T_k Y_k, Y_k = (I + T_k^2)^-1 by
   // plan.s[k] Newton-Schulz steps (2I - Y B) Y from Y = I - S (k = 0) or c_k Y_{k-1}.
   virtual cudaError_t foe(cudaStream_t s, MatSet& m, const double* H, int N, double mu, double sc,
