@@ -154,6 +154,25 @@ xlbomd_status xlbomd_density(xlbomd_ctx* ctx, int sys);
  * arrays of natoms doubles; requires xlbomd_density on the same state. */
 xlbomd_status xlbomd_response(xlbomd_ctx* ctx, int sys, const double* v_dev, double* w_dev);
 
+/* The same one-probe response as xlbomd_response, for callers that must not
+ * allocate device memory while they run: code that holds a fixed memory
+ * budget, runs next to a caching allocator it may not disturb, or replays
+ * work where a cudaMalloc or cudaFree would stall every other stream.  This
+ * call allocates nothing: the response chain's work matrices and vectors live
+ * in one file-scope static device array of about 2.6 MB, which every GPU that
+ * loads this library holds until the process exits.  The caller still passes
+ * the probe v_dev and the output w_dev (device arrays of natoms doubles), and
+ * the context must be an FP64 one (prec = XLBOMD_FP64) whose xlbomd_density
+ * has run.  Limit: padded orbital count <= 256 (at most 64 atoms); larger
+ * systems get XLBOMD_ERR_ARG with a message, other precisions
+ * XLBOMD_ERR_UNSUPPORTED.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress), so make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last call's
+ * contents: calls that overlap on the GPU (other streams, other contexts,
+ * other host threads) race on it.  The paper has no counterpart to this entry
+ * point; it exists for callers that cannot allocate. */
+xlbomd_status xlbomd_response_noalloc(xlbomd_ctx* ctx, int sys, const double* v_dev, double* w_dev);
+
 /* a7-a8: rank-m kernel on r (Eqs. K_up, v_1; Woodbury form), result in KR. */
 xlbomd_status xlbomd_kernel_update(xlbomd_ctx* ctx, int sys);
 

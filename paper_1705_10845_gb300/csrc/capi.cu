@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -448,7 +449,89 @@ void free_sys(Sys& S) {
 
 }  // namespace
 
+// ---- one-probe response whose work memory is a static device array ----
+//
+// For callers that may not allocate device memory at run time.  The chain's
+// work matrices and vectors live in this file-scope array, which every GPU
+// that loads the library holds until the process exits.  Its size bounds the
+// system: padded orbital count <= kStaticMaxNp.
+namespace {
+constexpr int kStaticMaxNp = 256;
+constexpr size_t kStaticMat = (size_t)kStaticMaxNp * kStaticMaxNp;
+constexpr size_t kStaticDoubles = 5 * kStaticMat + 3 * kStaticMaxNp + 64;
+}  // namespace
+
+static __device__ __align__(256) double g_response_scratch[kStaticDoubles];
+
+namespace {
+
+std::mutex g_static_mu;
+constexpr int kMaxDevices = 64;
+double* g_static_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_response_scratch on the current device (looked up once
+// per device; in host code the symbol itself is only a host-side stand-in).
+xlbomd_status static_scratch(xlbomd_ctx* ctx, double** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(ctx, XLBOMD_ERR_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_response_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(ctx, XLBOMD_ERR_CUDA, std::string("cudaGetSymbolAddress(g_response_scratch): ") +
+                                            cudaGetErrorString(e));
+    g_static_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_static_ptr[dev];
+  return XLBOMD_OK;
+}
+
+}  // namespace
+
 extern "C" {
+
+xlbomd_status xlbomd_response_noalloc(xlbomd_ctx* ctx, int sys, const double* v_dev, double* w_dev) {
+  CKS(check(ctx, sys));
+  if (!v_dev || !w_dev) return fail(ctx, XLBOMD_ERR_ARG, "null probe pointer");
+  if (ctx->p.prec != XLBOMD_FP64)
+    return fail(ctx, XLBOMD_ERR_UNSUPPORTED, "xlbomd_response_noalloc serves FP64 contexts only");
+  Sys& S = ctx->sys[sys];
+  if (S.np > kStaticMaxNp)
+    return fail(ctx, XLBOMD_ERR_ARG,
+                "xlbomd_response_noalloc: padded orbital count " + std::to_string(S.np) +
+                    " exceeds the static work-array limit of " + std::to_string(kStaticMaxNp) +
+                    " (64 atoms); use xlbomd_response");
+  if (!S.have_density) return fail(ctx, XLBOMD_ERR_ARG, "xlbomd_density must run first");
+  double* base = nullptr;
+  CKS(static_scratch(ctx, &base));
+  cudaStream_t st = ctx->stream;
+  const double sc = beta_of(ctx->p) / std::ldexp(1.0, ctx->p.n_sq + 1);
+  const size_t mat = (size_t)S.np * S.np;
+  MatSet m = S.mats;   // shallow view: expansion matrices of the context, work matrices in the array
+  m.G = base;
+  m.A1 = base + mat;
+  m.Mt = base + 2 * mat;
+  m.T1a = base + 3 * mat;
+  m.T1b = base + 4 * mat;
+  m.Tmu = nullptr;
+  double* potv = base + 5 * kStaticMat;
+  double* dvec = potv + kStaticMaxNp;
+  double* d1 = dvec + kStaticMaxNp;
+  double* scal = d1 + kStaticMaxNp;
+  // the array keeps the previous call's contents: the diagonal accumulator starts at zero
+  CK(cudaMemsetAsync(d1, 0, sizeof(double) * kStaticMaxNp, st));
+  CK(launch_gemv(st, S.nat, S.gam, S.natp, v_dev, potv));
+  CK(launch_expand_potential(st, S.nat, S.np, -sc, potv, dvec));
+  const bool prof = ctx->eng->prof;
+  ctx->eng->prof = false;   // event timing would create CUDA events
+  const cudaError_t ce = ctx->eng->chain(st, m, dvec, S.N, false, d1, nullptr);
+  ctx->eng->prof = prof;
+  CK(ce);
+  CK(launch_response_finish(st, S.nat, S.N, d1, S.dmu_diag, scal, w_dev));
+  return XLBOMD_OK;
+}
 
 void xlbomd_default_params(xlbomd_params* p) {
   if (!p) return;
