@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=0,
                     help="also time this many plain-FP64 GPU steps of the same workload")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="profiling run: t0 SCF, --warmup steps, then one step inside the NVTX range "
+                         "'xlbomd_step'; prints no JSON")
     return ap.parse_args()
 
 
@@ -204,6 +207,17 @@ def main():
     p = make_params(X, a, a.prec)
     stream = torch.cuda.current_stream()
     ctx = X.Context(p, [sysd], stream=stream.cuda_stream)
+
+    if a.profile_step:
+        ctx.scf(0)
+        ctx.step(a.warmup)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("xlbomd_step")
+        ctx.step(1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        ctx.close()
+        return 0
 
     # t0 ground state (untimed), then warm-up steps
     t_scf = time.perf_counter()

@@ -28,10 +28,21 @@ namespace {
 
 inline unsigned nblk(size_t count, int tpb = 256) { return (unsigned)((count + tpb - 1) / tpb); }
 
+// Raise *amax to the block's max |v| with one atomic per block (all threads
+// of the block must call it).
 __device__ __forceinline__ void raise_amax(unsigned* amax, float v) {
+  __shared__ float wmax[32];
   v = fabsf(v);
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(amax, __float_as_uint(v));
+  const int nthr = blockDim.x * blockDim.y;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if ((tid & 31) == 0) wmax[tid >> 5] = v;
+  __syncthreads();
+  if (tid == 0) {
+    float m = 0.0f;
+    for (int w = 0; w < (nthr + 31) / 32; ++w) m = fmaxf(m, wmax[w]);
+    atomicMax(amax, __float_as_uint(m));
+  }
 }
 
 // Conversion to the split operand pair.  All threads derive the same scale
@@ -152,6 +163,133 @@ __global__ void density_out_f32_kernel(int N, int np, const float* __restrict__ 
 
 __global__ void fill_nan_kernel(double* out) { *out = nan(""); }
 
+template <bool BF16>
+__global__ void convert_split_d_kernel(size_t count, const float2* __restrict__ d, const unsigned* __restrict__ amax,
+                                       uint16_t* __restrict__ hi, uint16_t* __restrict__ lo,
+                                       float* __restrict__ scale) {
+  const float m = __uint_as_float(*amax);
+  float s = 1.0f;
+  if (m > 0.0f && isfinite(m)) s = ldexpf(1.0f, 10 - ilogbf(m));
+  if (blockIdx.x == 0 && threadIdx.x == 0) *scale = s;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = d[i];
+    const float xh = v.x * s, xl = v.y * s;      // exact: s is a power of two
+    if (BF16) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(xh);
+      const __nv_bfloat16 l = __float2bfloat16_rn((xh - __bfloat162float(h)) + xl);
+      hi[i] = __bfloat16_as_ushort(h);
+      lo[i] = __bfloat16_as_ushort(l);
+    } else {
+      const __half h = __float2half_rn(xh);
+      const __half l = __float2half_rn((xh - __half2float(h)) + xl);
+      hi[i] = __half_as_ushort(h);
+      lo[i] = __half_as_ushort(l);
+    }
+  }
+}
+
+// T0 = -sc (H - mu I) as a double-float (hi = rn32(v), lo = rn32(v - hi))
+__global__ void t0_init_d_kernel(int n, int np, const double* __restrict__ H, double mu, double sc,
+                                 float2* __restrict__ T0, unsigned* amax) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float vh = 0.0f;
+  if (idx < (size_t)np * np) {
+    const int i = (int)(idx / np), j = (int)(idx % np);
+    double v = 0.0;
+    if (i < n && j < n) v = -sc * (H[idx] - (i == j ? mu : 0.0));
+    vh = (float)v;
+    T0[idx] = make_float2(vh, (float)(v - (double)vh));
+  }
+  raise_amax(amax, vh);
+}
+
+__global__ void level0_A1_d_kernel(int np, const float2* __restrict__ T0, const double* __restrict__ d,
+                                   float* __restrict__ A1, unsigned* amax) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float v = 0.0f;
+  if (idx < (size_t)np * np) {
+    const int i = (int)(idx / np), j = (int)(idx % np);
+    const float2 t = T0[idx];
+    v = (t.x + t.y) * (float)(d[i] + d[j]);
+    A1[idx] = v;
+  }
+  raise_amax(amax, v);
+}
+
+__device__ __forceinline__ double df_val(float2 v) { return (double)v.x + (double)v.y; }
+
+// out_i = (Y M)_ii = Mt_ii - sum_j W_ij Mt_ij  (Y = I - W, Mt = M^T), one warp per row
+__global__ void row_dot_last_kernel(int n, int np, const float* __restrict__ W, const float2* __restrict__ Mt,
+                                    double* __restrict__ out) {
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  float accf = 0.0f;
+  double acc = 0.0;
+  for (int j = lane, c = 0; j < np; j += 32, ++c) {
+    const float2 m = Mt[(size_t)i * np + j];
+    accf += W[(size_t)i * np + j] * (m.x + m.y);
+    if ((c & 15) == 15) {
+      acc += (double)accf;
+      accf = 0.0f;
+    }
+  }
+  acc += (double)accf;
+  acc = warp_sum(acc);
+  if (lane == 0) out[i] = df_val(Mt[(size_t)i * np + i]) - acc;
+}
+
+__global__ void get_diag_d_kernel(int n, int np, const float2* __restrict__ X, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = df_val(X[(size_t)i * np + i]);
+}
+
+__global__ void diag_sum_d_kernel(int n, int np, const float2* __restrict__ X, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += df_val(X[(size_t)i * np + i]);
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) *out = acc;
+}
+
+__global__ void density_out_d_kernel(int N, int np, const float2* __restrict__ Tn, const float2* __restrict__ Tmu,
+                                     double dmu, double* __restrict__ ddiag, double* __restrict__ D) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)np * np) return;
+  const int i = (int)(idx / np), j = (int)(idx % np);
+  double v = 0.0;
+  if (i < N && j < N) {
+    v = 0.5 * (df_val(Tn[idx]) + dmu * df_val(Tmu[idx]) + (i == j ? 1.0 : 0.0));
+    if (i == j) ddiag[i] = 2.0 * v;
+  }
+  D[idx] = v;
+}
+
+// Epilogue options of one split product.
+struct Epi {
+  float alpha = 1.0f;
+  const SplitMat* E = nullptr;
+  float beta = 0.0f;
+  const SplitMat* E2 = nullptr;
+  float beta2 = 0.0f;
+  const float2* E64 = nullptr;
+  float beta64 = 0.0f;
+  int e64_trans = 0;
+  float diag = 0.0f;
+  const double* dvec = nullptr;
+  float dvec_scale = 1.0f;
+  bool out64 = false;       // write C.d (and convert from it) instead of C.f
+  bool convert = true;      // produce the split operand pair of C
+};
+
+// The recursion is carried in correction form so that its exact leading
+// terms never pass through 16-bit operands:
+//   T_{k+1} = 2 T_k - 2 T_k W_k,  W_k = I - Y_k = I - (I + T_k^2)^-1,
+// W_k from the Newton-Schulz step written for W (Q = S - W - W S,
+// W <- W + Q - Q W), and the response chains as
+//   M = 2 T1_k - A1 T_{k+1},  T1_{k+1} = M - W_k M.
+// T_k, M and T1_k are FP64 values; W, S, Q, A1 FP32 values; every product
+// operand is the hi/lo split of a value.
 class EngineSplit : public Engine {
  public:
   explicit EngineSplit(int prec) : bf16_(prec == XLBOMD_BF16x3_ID ? 1 : 0) {}
@@ -167,6 +305,17 @@ class EngineSplit : public Engine {
       convert_split_kernel<true><<<g, 256, 0, s>>>(count, m.f, m.amax, m.hi, m.lo, m.scale);
     else
       convert_split_kernel<false><<<g, 256, 0, s>>>(count, m.f, m.amax, m.hi, m.lo, m.scale);
+    note_launch();
+    return cudaGetLastError();
+  }
+
+  cudaError_t convert_d(cudaStream_t s, SplitMat& m, int np) {
+    const size_t count = (size_t)np * np;
+    const unsigned g = std::min<size_t>(nblk(count), 152 * 16);
+    if (bf16_)
+      convert_split_d_kernel<true><<<g, 256, 0, s>>>(count, m.d, m.amax, m.hi, m.lo, m.scale);
+    else
+      convert_split_d_kernel<false><<<g, 256, 0, s>>>(count, m.d, m.amax, m.hi, m.lo, m.scale);
     note_launch();
     return cudaGetLastError();
   }
@@ -187,10 +336,8 @@ class EngineSplit : public Engine {
     return cudaSuccess;
   }
 
-  // C = alpha A B^T + beta E + diag I + dvec_scale diag(dvec), then split conversion of C
-  cudaError_t gemm(cudaStream_t s, int np, const SplitMat& A, const SplitMat& B, SplitMat& C, float alpha,
-                   const SplitMat* E, float beta, float diag, const double* dvec, float dvec_scale, bool sym,
-                   double* stats) {
+  cudaError_t gemm(cudaStream_t s, int np, const SplitMat& A, const SplitMat& B, SplitMat& C, const Epi& e,
+                   bool sym, double* stats) {
     RET(prep_tiles(np));
     auto& tl = tiles_[np];
     RET(cudaMemsetAsync(C.amax, 0, sizeof(unsigned), s));
@@ -198,14 +345,20 @@ class EngineSplit : public Engine {
     a.nseg = 3;
     a.sym = sym ? 1 : 0;
     a.bf16 = bf16_;
-    a.alpha = alpha;
-    a.E = E ? E->f : nullptr;
-    a.beta = beta;
-    a.diag = diag;
-    a.dvec = dvec;
-    a.ndvec = dvec ? np : 0;
-    a.dvec_scale = dvec_scale;
-    a.C = C.f;
+    a.alpha = e.alpha;
+    a.E = e.E ? e.E->f : nullptr;
+    a.beta = e.beta;
+    a.E2 = e.E2 ? e.E2->f : nullptr;
+    a.beta2 = e.beta2;
+    a.E64 = e.E64;
+    a.beta64 = e.beta64;
+    a.e64_trans = e.e64_trans;
+    a.diag = e.diag;
+    a.dvec = e.dvec;
+    a.ndvec = e.dvec ? np : 0;
+    a.dvec_scale = e.dvec_scale;
+    a.C = e.out64 ? nullptr : C.f;
+    a.C64 = e.out64 ? C.d : nullptr;
     a.ldc = np;
     a.amax = C.amax;
     a.sa = A.scale;
@@ -216,7 +369,8 @@ class EngineSplit : public Engine {
     RET(gemm_tc(s, np, A.hi, A.lo, B.hi, B.lo, a, tl.first, tl.first + 2 * n128, n128, n256));
     RET(prof_end(s, 2.0 * (double)np * np * np * (sym ? 0.5 : 1.0)));
     if (stats) stats[3] += sym ? 0.5 : 1.0;
-    return convert(s, C, np);
+    if (!e.convert) return cudaSuccess;
+    return e.out64 ? convert_d(s, C, np) : convert(s, C, np);
   }
 
   cudaError_t foe(cudaStream_t s, MatSet& m, const double* H, int N, double mu, double sc,
@@ -224,28 +378,47 @@ class EngineSplit : public Engine {
     const int np = m.np, n = m.n;
     const size_t cnt = (size_t)np * np;
     RET(cudaMemsetAsync(m.sT[0].amax, 0, sizeof(unsigned), s));
-    t0_init_f32_kernel<<<nblk(cnt), 256, 0, s>>>(N, np, H, mu, sc, m.sT[0].f, m.sT[0].amax);
+    t0_init_d_kernel<<<nblk(cnt), 256, 0, s>>>(N, np, H, mu, sc, m.sT[0].d, m.sT[0].amax);
     note_launch();
     RET(cudaGetLastError());
-    RET(convert(s, m.sT[0], np));
+    RET(convert_d(s, m.sT[0], np));
     for (int k = 0; k < n; ++k) {
-      RET(gemm(s, np, m.sT[k], m.sT[k], m.sS, 1.f, nullptr, 0.f, 0.f, nullptr, 1.f, true, stats));
-      SplitMat& Y = m.sY[k];
-      RET(cudaMemsetAsync(Y.amax, 0, sizeof(unsigned), s));
+      Epi es;
+      RET(gemm(s, np, m.sT[k], m.sT[k], m.sS, es, true, stats));                 // S = T^2
+      SplitMat& W = m.sY[k];
+      RET(cudaMemsetAsync(W.amax, 0, sizeof(unsigned), s));
       if (k == 0)
-        axpi_f32_kernel<<<nblk(cnt), 256, 0, s>>>(np, 1.f, -1.f, m.sS.f, Y.f, Y.amax);
+        axpi_f32_kernel<<<nblk(cnt), 256, 0, s>>>(np, 0.f, 1.f, m.sS.f, W.f, W.amax);          // W = S
       else
-        axpi_f32_kernel<<<nblk(cnt), 256, 0, s>>>(np, 0.f, (float)nc[k], m.sY[k - 1].f, Y.f, Y.amax);
+        axpi_f32_kernel<<<nblk(cnt), 256, 0, s>>>(np, (float)(1.0 - nc[k]), (float)nc[k], m.sY[k - 1].f, W.f,
+                                                 W.amax);                                  // W = (1-c) I + c W_{k-1}
       note_launch();
       RET(cudaGetLastError());
-      RET(convert(s, Y, np));
+      RET(convert(s, W, np));
       for (int it = 0; it < ns[k]; ++it) {
-        RET(gemm(s, np, m.sY[k], m.sS, m.sQ, -1.f, &m.sY[k], -1.f, 2.f, nullptr, 1.f, false, stats));
-        RET(gemm(s, np, m.sQ, m.sY[k], m.sYw, 1.f, nullptr, 0.f, 0.f, nullptr, 1.f, true, stats));
+        Epi eq;                                                                   // Q = S - W - W S
+        eq.alpha = -1.f;
+        eq.E = &m.sS;
+        eq.beta = 1.f;
+        eq.E2 = &m.sY[k];
+        eq.beta2 = -1.f;
+        RET(gemm(s, np, m.sY[k], m.sS, m.sQ, eq, false, stats));
+        Epi ew;                                                                   // W <- W + Q - Q W
+        ew.alpha = -1.f;
+        ew.E = &m.sY[k];
+        ew.beta = 1.f;
+        ew.E2 = &m.sQ;
+        ew.beta2 = 1.f;
+        RET(gemm(s, np, m.sQ, m.sY[k], m.sYw, ew, true, stats));
         std::swap(m.sY[k], m.sYw);
         if (stats) stats[1] += 1;
       }
-      RET(gemm(s, np, m.sT[k], m.sY[k], m.sT[k + 1], 2.f, nullptr, 0.f, 0.f, nullptr, 1.f, true, stats));
+      Epi et;                                                                     // T' = 2T - 2 T W
+      et.alpha = -2.f;
+      et.E64 = m.sT[k].d;
+      et.beta64 = 2.0f;
+      et.out64 = true;
+      RET(gemm(s, np, m.sT[k], m.sY[k], m.sT[k + 1], et, true, stats));
     }
     return cudaSuccess;
   }
@@ -259,30 +432,44 @@ class EngineSplit : public Engine {
     for (int k = 0; k < n; ++k) {
       const bool last = (k == n - 1);
       RET(cudaMemsetAsync(m.sA1.amax, 0, sizeof(unsigned), s));
+      Epi em;                                                                    // Mt = 2 T1 - T_{k+1} A1
+      em.alpha = -1.f;
+      em.out64 = true;
       if (k == 0) {
-        level0_A1_f32_kernel<<<nblk(cnt), 256, 0, s>>>(np, m.sT[0].f, dvec, m.sA1.f, m.sA1.amax);
+        level0_A1_d_kernel<<<nblk(cnt), 256, 0, s>>>(np, m.sT[0].d, dvec, m.sA1.f, m.sA1.amax);
         note_launch();
         RET(cudaGetLastError());
-        RET(convert(s, m.sA1, np));
-        RET(gemm(s, np, m.sT[1], m.sA1, m.sMt, -1.f, nullptr, 0.f, 0.f, dvec, 2.f, false, stats));
+        em.dvec = dvec;
+        em.dvec_scale = 2.f;
       } else {
-        RET(gemm(s, np, m.sT[k], *T1, m.sG, 1.f, nullptr, 0.f, 0.f, nullptr, 1.f, false, stats));
+        Epi eg;
+        eg.convert = false;
+        RET(gemm(s, np, m.sT[k], *T1, m.sG, eg, false, stats));                  // G = T T1
         dim3 grid(np / 32, np / 32), block(32, 8);
         transpose_add_f32_kernel<<<grid, block, 0, s>>>(np, m.sG.f, m.sA1.f, m.sA1.amax);
         note_launch();
         RET(cudaGetLastError());
-        RET(convert(s, m.sA1, np));
-        RET(gemm(s, np, m.sT[k + 1], m.sA1, m.sMt, -1.f, T1, 2.f, 0.f, nullptr, 1.f, false, stats));
+        em.E64 = T1->d;
+        em.beta64 = 2.0f;
       }
+      RET(convert(s, m.sA1, np));
+      RET(gemm(s, np, m.sT[k + 1], m.sA1, m.sMt, em, false, stats));
       if (last && !full_last) {
-        row_dot_f32_kernel<<<(N + 7) / 8, 256, 0, s>>>(N, np, m.sY[k].f, m.sMt.f, out_diag);
+        row_dot_last_kernel<<<(N + 7) / 8, 256, 0, s>>>(N, np, m.sY[k].f, m.sMt.d, out_diag);
         note_launch();
         return cudaGetLastError();
       }
       SplitMat* dst = (last && full_last) ? &m.sTmu : T1n;
-      RET(gemm(s, np, m.sY[k], m.sMt, *dst, 1.f, nullptr, 0.f, 0.f, nullptr, 1.f, true, stats));
+      Epi ey;                                                                    // T1' = M - W M
+      ey.alpha = -1.f;
+      ey.E64 = m.sMt.d;
+      ey.beta64 = 1.0f;
+      ey.e64_trans = 1;
+      ey.out64 = true;
+      ey.convert = !last;
+      RET(gemm(s, np, m.sY[k], m.sMt, *dst, ey, true, stats));
       if (last) {
-        get_diag_f32_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, np, dst->f, out_diag);
+        get_diag_d_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, np, dst->d, out_diag);
         note_launch();
         return cudaGetLastError();
       }
@@ -293,14 +480,14 @@ class EngineSplit : public Engine {
   }
 
   cudaError_t trace_tn(cudaStream_t s, MatSet& m, int N, double* out) override {
-    diag_sum_f32_kernel<<<1, 1024, 0, s>>>(N, m.np, m.sT[m.n].f, out);
+    diag_sum_d_kernel<<<1, 1024, 0, s>>>(N, m.np, m.sT[m.n].d, out);
     note_launch();
     return cudaGetLastError();
   }
 
   cudaError_t density_out(cudaStream_t s, MatSet& m, int N, double dmu, const double*, double* ddiag,
                           double* D) override {
-    density_out_f32_kernel<<<nblk((size_t)m.np * m.np), 256, 0, s>>>(N, m.np, m.sT[m.n].f, m.sTmu.f, dmu, ddiag, D);
+    density_out_d_kernel<<<nblk((size_t)m.np * m.np), 256, 0, s>>>(N, m.np, m.sT[m.n].d, m.sTmu.d, dmu, ddiag, D);
     note_launch();
     return cudaGetLastError();
   }
@@ -319,12 +506,21 @@ class EngineSplit : public Engine {
   std::unordered_map<int, std::pair<int*, std::pair<int, int>>> tiles_;
 };
 
-cudaError_t alloc_split(SplitMat& m, int np, float* scal_f, unsigned* scal_u) {
+// which value arrays a matrix keeps
+enum { kF = 1, kD = 2 };
+
+cudaError_t alloc_split(SplitMat& m, int np, float* scal_f, unsigned* scal_u, int what = kF) {
   const size_t cnt = (size_t)np * np;
-  RET(cudaMalloc((void**)&m.f, cnt * sizeof(float)));
+  if (what & kF) {
+    RET(cudaMalloc((void**)&m.f, cnt * sizeof(float)));
+    RET(cudaMemset(m.f, 0, cnt * sizeof(float)));
+  }
+  if (what & kD) {
+    RET(cudaMalloc((void**)&m.d, cnt * sizeof(float2)));
+    RET(cudaMemset(m.d, 0, cnt * sizeof(float2)));
+  }
   RET(cudaMalloc((void**)&m.hi, cnt * sizeof(uint16_t)));
   RET(cudaMalloc((void**)&m.lo, cnt * sizeof(uint16_t)));
-  RET(cudaMemset(m.f, 0, cnt * sizeof(float)));
   RET(cudaMemset(m.hi, 0, cnt * sizeof(uint16_t)));
   RET(cudaMemset(m.lo, 0, cnt * sizeof(uint16_t)));
   m.scale = scal_f;
@@ -334,6 +530,7 @@ cudaError_t alloc_split(SplitMat& m, int np, float* scal_f, unsigned* scal_u) {
 
 void free_split(SplitMat& m) {
   if (m.f) cudaFree(m.f);
+  if (m.d) cudaFree(m.d);
   if (m.hi) {
     tc_forget_maps(m.hi);
     cudaFree(m.hi);
@@ -343,6 +540,7 @@ void free_split(SplitMat& m) {
     cudaFree(m.lo);
   }
   m.f = nullptr;
+  m.d = nullptr;
   m.hi = m.lo = nullptr;
 }
 
@@ -356,7 +554,6 @@ Engine* make_split_engine(int prec) {
 cudaError_t alloc_matset_split(MatSet& m) {
   const int np = m.np, n = m.n;
   const int nmat = (n + 1) + n + 9;
-  // one block of device scalars: scales (float) then amax (unsigned)
   float* scal = nullptr;
   RET(cudaMalloc((void**)&scal, sizeof(float) * 2 * nmat));
   RET(cudaMemset(scal, 0, sizeof(float) * 2 * nmat));
@@ -367,16 +564,20 @@ cudaError_t alloc_matset_split(MatSet& m) {
   m.sT.assign(n + 1, SplitMat());
   m.sY.assign(n, SplitMat());
   for (auto& x : m.sT) {
-    RET(alloc_split(x, np, sf + idx, su + idx));
+    RET(alloc_split(x, np, sf + idx, su + idx, kD));
     ++idx;
   }
   for (auto& x : m.sY) {
-    RET(alloc_split(x, np, sf + idx, su + idx));
+    RET(alloc_split(x, np, sf + idx, su + idx, kF));
     ++idx;
   }
-  SplitMat* w[] = {&m.sS, &m.sQ, &m.sYw, &m.sG, &m.sA1, &m.sMt, &m.sT1a, &m.sT1b, &m.sTmu};
-  for (SplitMat* x : w) {
-    RET(alloc_split(*x, np, sf + idx, su + idx));
+  struct W {
+    SplitMat* m;
+    int what;
+  } w[] = {{&m.sS, kF},  {&m.sQ, kF},  {&m.sYw, kF},  {&m.sG, kF},  {&m.sA1, kF},
+           {&m.sMt, kD}, {&m.sT1a, kD}, {&m.sT1b, kD}, {&m.sTmu, kD}};
+  for (auto& x : w) {
+    RET(alloc_split(*x.m, np, sf + idx, su + idx, x.what));
     ++idx;
   }
   return cudaSuccess;
@@ -476,10 +677,10 @@ int selftest_gemm(int n, int prec, int sym, double* result) {
   }
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  if (eng.gemm(s, n, sa, sb, sc, 1.f, nullptr, 0.f, 0.f, nullptr, 1.f, sym != 0, nullptr)) goto done;
+  if (eng.gemm(s, n, sa, sb, sc, Epi(), sym != 0, nullptr)) goto done;
   cudaEventRecord(e0, s);
   for (int r = 0; r < 5; ++r)
-    if (eng.gemm(s, n, sa, sb, sc, 1.f, nullptr, 0.f, 0.f, nullptr, 1.f, sym != 0, nullptr)) goto done;
+    if (eng.gemm(s, n, sa, sb, sc, Epi(), sym != 0, nullptr)) goto done;
   cudaEventRecord(e1, s);
   if (cudaDeviceSynchronize() != cudaSuccess) goto done;
   cudaEventElapsedTime(&ms, e0, e1);

@@ -21,6 +21,7 @@
 // error code and leaves its loops, and TMEM is always released.
 #include <cuda.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <mutex>
 #include <unordered_map>
@@ -36,6 +37,7 @@ constexpr int BK = 64;           // 64 x 16-bit = 128 bytes: one swizzle row
 constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int kWaitLimit = 1 << 24;
+constexpr int kGroupM = 16;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -124,6 +126,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// a + b for a double-float a and a float b (Knuth two-sum, then renormalise)
+__device__ __forceinline__ float2 df_add(float2 a, float b) {
+  const float s = a.x + b;
+  const float bb = s - a.x;
+  const float err = (a.x - (s - bb)) + (b - bb) + a.y;
+  const float hi = s + err;
+  return make_float2(hi, err - (hi - s));
+}
+
 template <int BN>
 __global__ void __launch_bounds__(192, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
@@ -145,8 +156,15 @@ __global__ void __launch_bounds__(192, 1)
     tm = a.tile_list[2 * blockIdx.x];
     tn = a.tile_list[2 * blockIdx.x + 1];
   } else {
-    tm = blockIdx.x / a.tiles_n;
-    tn = blockIdx.x % a.tiles_n;
+    // grouped raster: GROUP_M row panels at a time, so that the CTAs in flight
+    // share their A and B panels in L2
+    const int tiles_m = a.K / BM;
+    const int per_group = kGroupM * a.tiles_n;
+    const int g = blockIdx.x / per_group, r = blockIdx.x % per_group;
+    const int first = g * kGroupM;
+    const int gm = min(tiles_m - first, kGroupM);
+    tm = first + r % gm;
+    tn = r / gm;
   }
 
   if (warp == 0 && lane == 0) {
@@ -238,13 +256,41 @@ __global__ void __launch_bounds__(192, 1)
           for (int i = 0; i < 32; ++i) v[i] += w[i];
         }
         const int col0 = tn * BN + ch * 32;
-        const float* er = a.E ? a.E + (size_t)row * a.ldc + col0 : nullptr;
-        float* cr = a.C + (size_t)row * a.ldc + col0;
+        const size_t rbase = (size_t)row * a.ldc + col0;
+        if (a.C64) {
+          // double-float output: exact leading term beta64 E64 plus the product and
+          // FP32 side terms, added with error-free transformations in FP32
+#pragma unroll 4
+          for (int i = 0; i < 32; ++i) {
+            const int col = col0 + i;
+            if (a.sym && col < row) continue;
+            float t = inv * v[i];
+            if (a.E) t += a.beta * a.E[rbase + i];
+            if (a.E2) t += a.beta2 * a.E2[rbase + i];
+            if (col == row) {
+              t += a.diag;
+              if (a.dvec && row < a.ndvec) t += a.dvec_scale * (float)a.dvec[row];
+            }
+            float2 x = make_float2(t, 0.0f);
+            if (a.E64) {
+              const float2 e = a.e64_trans ? a.E64[(size_t)col * a.ldc + row] : a.E64[rbase + i];
+              x = df_add(make_float2(a.beta64 * e.x, a.beta64 * e.y), t);
+            }
+            a.C64[rbase + i] = x;
+            if (a.sym && col > row) a.C64[(size_t)col * a.ldc + row] = x;
+            vmax = fmaxf(vmax, fabsf(x.x));
+          }
+          continue;
+        }
+        const float* er = a.E ? a.E + rbase : nullptr;
+        const float* er2 = a.E2 ? a.E2 + rbase : nullptr;
+        float* cr = a.C + rbase;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int col = col0 + i;
           float x = inv * v[i];
           if (er) x += a.beta * er[i];
+          if (er2) x += a.beta2 * er2[i];
           if (col == row) {
             x += a.diag;
             if (a.dvec && row < a.ndvec) x += a.dvec_scale * (float)a.dvec[row];
@@ -404,12 +450,16 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
 // upper triangle (bn tn + bn > BM tm), row-major order.
 std::vector<int> tc_sym_tiles(int n, int bn) {
   std::vector<int> t;
-  for (int tm = 0; tm < n / BM; ++tm)
-    for (int tn = 0; tn < n / bn; ++tn)
-      if (bn * tn + bn > BM * tm) {
-        t.push_back(tm);
-        t.push_back(tn);
-      }
+  const int tiles_m = n / BM, tiles_n = n / bn;
+  for (int first = 0; first < tiles_m; first += kGroupM) {
+    const int gm = std::min(tiles_m - first, kGroupM);
+    for (int tn = 0; tn < tiles_n; ++tn)
+      for (int tm = first; tm < first + gm; ++tm)
+        if (bn * tn + bn > BM * tm) {
+          t.push_back(tm);
+          t.push_back(tn);
+        }
+  }
   return t;
 }
 

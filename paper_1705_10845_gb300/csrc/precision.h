@@ -17,7 +17,8 @@ constexpr int XLBOMD_BF16x3_ID = 2;
 // logical matrix is a double array; the split engines keep an FP32 value
 // array plus hi/lo 16-bit operand arrays with a power-of-two scale.
 struct SplitMat {
-  float* f = nullptr;        // value (np x np)
+  float2* d = nullptr;       // double-float value hi + lo (matrices carried with an exact leading term)
+  float* f = nullptr;        // FP32 value (np x np)
   uint16_t* hi = nullptr;    // operand hi part of value * scale
   uint16_t* lo = nullptr;    // operand lo part
   float* scale = nullptr;    // device scalar

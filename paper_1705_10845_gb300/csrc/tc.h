@@ -14,9 +14,15 @@ struct TcArgs {
   int bf16 = 0;                   // operand type: 0 FP16, 1 BF16
   int tiles_n = 0;                // set by gemm_tc
   const int* tile_list = nullptr; // set by gemm_tc
-  float alpha = 1.0f;             // C = alpha acc / (sa sb) + beta E + diag I + dvec_scale diag(dvec)
-  const float* E = nullptr;
+  float alpha = 1.0f;             // C = alpha acc / (sa sb) + beta E + beta2 E2 + beta64 E64
+  const float* E = nullptr;       //     + diag I + dvec_scale diag(dvec)
   float beta = 0.0f;
+  const float* E2 = nullptr;
+  float beta2 = 0.0f;
+  const float2* E64 = nullptr;    // double-float side input, read transposed when e64_trans
+  float beta64 = 0.0f;            // a power of two, so that beta64 E64 is exact
+  int e64_trans = 0;
+  float2* C64 = nullptr;          // double-float output (written instead of C when set)
   float diag = 0.0f;
   const double* dvec = nullptr;
   int ndvec = 0;

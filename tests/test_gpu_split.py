@@ -65,3 +65,24 @@ def test_split_density_against_oracle(X, prec, case):
     assert np.max(np.abs(q - ref.q)) < tol_q
     assert np.max(np.abs(F - ref.F)) < tol_f
     assert np.max(np.abs(Kr - ref.Kr)) < 100 * tol_q
+
+
+def test_full_size_charges_against_oracle(X):
+    # the bench workload: 1536 atoms (N = 6144), Te = 1500 K, 14 squarings,
+    # FP16x3, at the t0 ground state that the MD starts from (kernel SCF with
+    # the automatic J_0); the oracle diagonalises H on the host at the same
+    # (R, n) and the charges must agree to 1e-5 e
+    s = synth.make_system(1536, 1705)
+    p = X.default_params(Te=1500.0, n_sq=14, rank_m=4, mix_alpha=ALPHA_MIX, kernel_c=1 - 1 / ALPHA_MIX,
+                         prec="fp16x3", mu_tol=1e-3, scf_mode=1, kernel_auto=1, scf_tol=1e-5,
+                         scf_max_iter=200)
+    with X.Context(p, [sysdict(s)]) as ctx:
+        ctx.scf(0)
+        n = ctx.get(0, X.N)
+        ctx.build_H(0)
+        ctx.density(0)
+        q = ctx.get(0, X.Q)
+    q_ref = O.charges_at(s.R, s.L, s.Z, n, O.Model(Te=1500.0, n_sq=14))
+    err = np.max(np.abs(q - q_ref))
+    print("full size fp16x3 |dq|", err)
+    assert err < 1e-5
