@@ -265,7 +265,10 @@ __global__ void density_out_d_kernel(int N, int np, const float2* __restrict__ T
   D[idx] = v;
 }
 
-// Epilogue options of one split product.
+// Epilogue options of one split product.  The FP32 side inputs E, E2 are
+// read transposed by the product kernel, so they must be symmetric (S, W and
+// the Newton-Schulz residual Q, whose rounding asymmetry the iteration
+// removes).
 struct Epi {
   float alpha = 1.0f;
   const SplitMat* E = nullptr;
@@ -367,7 +370,10 @@ class EngineSplit : public Engine {
     const int n128 = tl.second.first, n256 = tl.second.second;
     RET(prof_begin(s));
     RET(gemm_tc(s, np, A.hi, A.lo, B.hi, B.lo, a, tl.first, tl.first + 2 * n128, n128, n256));
-    RET(prof_end(s, 2.0 * (double)np * np * np * (sym ? 0.5 : 1.0)));
+    // kind bits: 1 sym, 2 E, 4 E2, 8 E64, 16 E64 transposed, 32 FP64 output
+    const int kind = (sym ? 1 : 0) | (e.E ? 2 : 0) | (e.E2 ? 4 : 0) | (e.E64 ? 8 : 0) | (e.e64_trans ? 16 : 0) |
+                     (e.out64 ? 32 : 0);
+    RET(prof_end(s, 2.0 * (double)np * np * np * (sym ? 0.5 : 1.0), kind));
     if (stats) stats[3] += sym ? 0.5 : 1.0;
     if (!e.convert) return cudaSuccess;
     return e.out64 ? convert_d(s, C, np) : convert(s, C, np);
@@ -415,7 +421,8 @@ class EngineSplit : public Engine {
       }
       Epi et;                                                                     // T' = 2T - 2 T W
       et.alpha = -2.f;
-      et.E64 = m.sT[k].d;
+      et.E64 = m.sT[k].d;                                                         // symmetric: read transposed
+      et.e64_trans = 1;
       et.beta64 = 2.0f;
       et.out64 = true;
       RET(gemm(s, np, m.sT[k], m.sY[k], m.sT[k + 1], et, true, stats));
@@ -449,7 +456,8 @@ class EngineSplit : public Engine {
         transpose_add_f32_kernel<<<grid, block, 0, s>>>(np, m.sG.f, m.sA1.f, m.sA1.amax);
         note_launch();
         RET(cudaGetLastError());
-        em.E64 = T1->d;
+        em.E64 = T1->d;                                                           // symmetric: read transposed
+        em.e64_trans = 1;
         em.beta64 = 2.0f;
       }
       RET(convert(s, m.sA1, np));

@@ -69,6 +69,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<uint64_t>(p)));
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -239,12 +243,35 @@ __global__ void __launch_bounds__(192, 1)
   } else {
     // epilogue warps 2..5: TMEM lanes 32 * (warp % 4) ..
     const int q = warp & 3;
+    {
+      // while the tensor cores run, pull this tile's side inputs into L2
+      const int t = (warp - 2) * 32 + lane;            // 0..127
+      const int r = tm * BM + t;
+      const float* fsides[2] = {a.E, a.E2};
+      for (int k = 0; k < 2; ++k)
+        if (fsides[k])
+          for (int rr = t; rr < BN; rr += 128)
+            for (int c = 0; c < BM; c += 32) prefetch_l2(fsides[k] + (size_t)(tn * BN + rr) * a.ldc + tm * BM + c);
+      if (a.E64) {
+        if (a.e64_trans) {
+          for (int rr = t; rr < BN; rr += 128)
+            for (int c = 0; c < BM; c += 16) prefetch_l2(a.E64 + (size_t)(tn * BN + rr) * a.ldc + tm * BM + c);
+        } else {
+          for (int c = 0; c < BN; c += 16) prefetch_l2(a.E64 + (size_t)r * a.ldc + tn * BN + c);
+        }
+      }
+    }
     if (!mbar_wait(accf, 0)) {
       if (lane == 0) atomicExch(a.err, 3);
     } else {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int row = tm * BM + q * 32 + lane;
+      const int row0 = tm * BM + q * 32;
+      const int row = row0 + lane;
       const float inv = a.alpha / (__ldg(a.sa) * __ldg(a.sb));
+      // per-warp 32 x 33 staging tiles in the (now idle) operand ring, so that
+      // side inputs are loaded and outputs stored as whole 128-byte rows
+      float(*tx)[33] = reinterpret_cast<float(*)[33]>(sA + q * (2 * 32 * 33 * 4));
+      float(*ty)[33] = reinterpret_cast<float(*)[33]>(sA + q * (2 * 32 * 33 * 4) + 32 * 33 * 4);
       float vmax = 0.0f;
       for (int ch = 0; ch < BN / 32; ++ch) {
         float v[32];
@@ -256,64 +283,89 @@ __global__ void __launch_bounds__(192, 1)
           for (int i = 0; i < 32; ++i) v[i] += w[i];
         }
         const int col0 = tn * BN + ch * 32;
-        const size_t rbase = (size_t)row * a.ldc + col0;
+        // this lane holds row `row`, columns col0 .. col0 + 31
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] *= inv;
+        // FP32 side inputs of symmetric value, read transposed: for a fixed
+        // column the 32 lanes read 32 consecutive rows (coalesced)
+        if (a.E) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] += a.beta * a.E[(size_t)(col0 + i) * a.ldc + row];
+        }
+        if (a.E2) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] += a.beta2 * a.E2[(size_t)(col0 + i) * a.ldc + row];
+        }
+        const int dc = row - col0;   // diagonal column of this lane, if in the chunk
+        if (dc >= 0 && dc < 32) {
+          float dd = a.diag;
+          if (a.dvec && row < a.ndvec) dd += a.dvec_scale * (float)a.dvec[row];
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (i == dc) v[i] += dd;
+        }
         if (a.C64) {
-          // double-float output: exact leading term beta64 E64 plus the product and
-          // FP32 side terms, added with error-free transformations in FP32
-#pragma unroll 4
+          // double-float value: exact leading term beta64 E64 plus the FP32 part
+          float hi[32], lo[32];
+          if (a.E64 && a.e64_trans) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const float2 e = a.E64[(size_t)(col0 + i) * a.ldc + row];
+              const float2 x = df_add(make_float2(a.beta64 * e.x, a.beta64 * e.y), v[i]);
+              hi[i] = x.x;
+              lo[i] = x.y;
+            }
+          } else if (a.E64) {
+#pragma unroll 8
+            for (int i = 0; i < 32; ++i) {
+              const float2 e = a.E64[(size_t)(row0 + i) * a.ldc + col0 + lane];
+              tx[i][lane] = e.x;
+              ty[i][lane] = e.y;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const float2 x = df_add(make_float2(a.beta64 * tx[lane][i], a.beta64 * ty[lane][i]), v[i]);
+              hi[i] = x.x;
+              lo[i] = x.y;
+            }
+            __syncwarp();
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              hi[i] = v[i];
+              lo[i] = 0.0f;
+            }
+          }
+#pragma unroll
           for (int i = 0; i < 32; ++i) {
             const int col = col0 + i;
-            if (a.sym && col < row) continue;
-            float t = inv * v[i];
-            if (a.E) t += a.beta * a.E[rbase + i];
-            if (a.E2) t += a.beta2 * a.E2[rbase + i];
-            if (col == row) {
-              t += a.diag;
-              if (a.dvec && row < a.ndvec) t += a.dvec_scale * (float)a.dvec[row];
-            }
-            float2 x = make_float2(t, 0.0f);
-            if (a.E64) {
-              const float2 e = a.e64_trans ? a.E64[(size_t)col * a.ldc + row] : a.E64[rbase + i];
-              x = df_add(make_float2(a.beta64 * e.x, a.beta64 * e.y), t);
-            }
-            a.C64[rbase + i] = x;
-            if (a.sym && col > row) a.C64[(size_t)col * a.ldc + row] = x;
-            vmax = fmaxf(vmax, fabsf(x.x));
+            if (!a.sym || col >= row) vmax = fmaxf(vmax, fabsf(hi[i]));
+            if (a.sym && col > row) a.C64[(size_t)col * a.ldc + row] = make_float2(hi[i], lo[i]);
+            tx[lane][i] = hi[i];
+            ty[lane][i] = lo[i];
           }
+          __syncwarp();
+          for (int i = 0; i < 32; ++i) {
+            const int r = row0 + i, c = col0 + lane;
+            if (!a.sym || c >= r) a.C64[(size_t)r * a.ldc + c] = make_float2(tx[i][lane], ty[i][lane]);
+          }
+          __syncwarp();
           continue;
         }
-        const float* er = a.E ? a.E + rbase : nullptr;
-        const float* er2 = a.E2 ? a.E2 + rbase : nullptr;
-        float* cr = a.C + rbase;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int col = col0 + i;
-          float x = inv * v[i];
-          if (er) x += a.beta * er[i];
-          if (er2) x += a.beta2 * er2[i];
-          if (col == row) {
-            x += a.diag;
-            if (a.dvec && row < a.ndvec) x += a.dvec_scale * (float)a.dvec[row];
-          }
-          v[i] = x;
+          if (!a.sym || col >= row) vmax = fmaxf(vmax, fabsf(v[i]));
+          if (a.sym && col > row) a.C[(size_t)col * a.ldc + row] = v[i];
+          tx[lane][i] = v[i];
         }
-        if (!a.sym) {
-#pragma unroll
-          for (int i = 0; i < 32; i += 4) {
-            *reinterpret_cast<float4*>(cr + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-            vmax = fmaxf(vmax, fmaxf(fmaxf(fabsf(v[i]), fabsf(v[i + 1])), fmaxf(fabsf(v[i + 2]), fabsf(v[i + 3]))));
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const int col = col0 + i;
-            if (col >= row) {
-              cr[i] = v[i];
-              if (col > row) a.C[(size_t)col * a.ldc + row] = v[i];
-              vmax = fmaxf(vmax, fabsf(v[i]));
-            }
-          }
+        __syncwarp();
+        for (int i = 0; i < 32; ++i) {
+          const int r = row0 + i, c = col0 + lane;
+          if (!a.sym || c >= r) a.C[(size_t)r * a.ldc + c] = tx[i][lane];
         }
+        __syncwarp();
       }
       for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
       if (lane == 0 && a.amax) atomicMax(a.amax, __float_as_uint(vmax));

@@ -4,6 +4,8 @@
 // recursions in one arithmetic: plain FP64 products, or split-precision
 // tensor-core products (hi/lo 16-bit operands, FP32 accumulation).
 #pragma once
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "internal.h"
@@ -61,10 +63,13 @@ class Engine {
     }
     return cudaEventRecord(ev_[2 * nprof_], s);
   }
-  cudaError_t prof_end(cudaStream_t s, double flops) {
+  std::vector<int> prof_kind_;
+  cudaError_t prof_end(cudaStream_t s, double flops, int kind = 0) {
     if (!prof) return cudaSuccess;
     cudaError_t r = cudaEventRecord(ev_[2 * nprof_ + 1], s);
     if (prof_flops_.size() <= nprof_) prof_flops_.resize(nprof_ + 1);
+    if (prof_kind_.size() <= nprof_) prof_kind_.resize(nprof_ + 1);
+    prof_kind_[nprof_] = kind;
     prof_flops_[nprof_++] = flops;
     return r;
   }
@@ -81,9 +86,22 @@ class Engine {
       if (r != cudaSuccess) return r;
       out[1] += ms;
       out[2] += prof_flops_[i];
+      if (i < prof_kind_.size()) {
+        const int k = prof_kind_[i] & 63;
+        kind_ms_[k] += ms;
+        kind_n_[k] += 1;
+      }
     }
+    const char* e = std::getenv("XLBOMD_DEBUG");
+    if (e && e[0] && e[0] != '0')
+      for (int k = 0; k < 64; ++k)
+        if (kind_n_[k] > 0)
+          std::fprintf(stderr, "[xlbomd] product kind %2d: %6d launches, %8.3f ms avg\n", k, kind_n_[k],
+                       kind_ms_[k] / kind_n_[k]);
     return cudaSuccess;
   }
+  double kind_ms_[64] = {0};
+  int kind_n_[64] = {0};
   // T_0 = -sc (H - mu I); n levels T_{k+1} = 2 T_k Y_k, Y_k = (I + T_k^2)^-1 by
   // plan.s[k] Newton-Schulz steps (2I - Y B) Y from Y = I - S (k = 0) or c_k Y_{k-1}.
   virtual cudaError_t foe(cudaStream_t s, MatSet& m, const double* H, int N, double mu, double sc,

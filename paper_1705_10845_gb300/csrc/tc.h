@@ -14,8 +14,9 @@ struct TcArgs {
   int bf16 = 0;                   // operand type: 0 FP16, 1 BF16
   int tiles_n = 0;                // set by gemm_tc
   const int* tile_list = nullptr; // set by gemm_tc
-  float alpha = 1.0f;             // C = alpha acc / (sa sb) + beta E + beta2 E2 + beta64 E64
-  const float* E = nullptr;       //     + diag I + dvec_scale diag(dvec)
+  float alpha = 1.0f;             // C = alpha acc / (sa sb) + beta E^T + beta2 E2^T + beta64 E64(^T)
+  const float* E = nullptr;       //     + diag I + dvec_scale diag(dvec); E and E2 are read
+                                  //     transposed (callers pass symmetric side inputs)
   float beta = 0.0f;
   const float* E2 = nullptr;
   float beta2 = 0.0f;
