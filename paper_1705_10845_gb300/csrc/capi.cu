@@ -160,22 +160,22 @@ xlbomd_status sync_read(xlbomd_ctx* ctx, const double* dev, int count) {
   return XLBOMD_OK;
 }
 
+// y = gamma x (real-space matrix plus the reciprocal part through the structure factors)
+cudaError_t gamma_apply(xlbomd_ctx* ctx, Sys& S, const double* x, double* y, double* tmp) {
+  return launch_gamma_apply(ctx->stream, S.nat, S.gam, S.natp, S.SF, S.kp, ctx->p.coulomb_k, x, y, tmp);
+}
+
 // a1-a2
 xlbomd_status build_H(xlbomd_ctx* ctx, Sys& S) {
   cudaStream_t st = ctx->stream;
   const ModelConst m = model_of(ctx->p);
   CK(launch_build_H0(st, m, S.nat, S.L, S.R, S.H0, S.np));
+  const bool fp32_pairs = ctx->p.prec != XLBOMD_FP64;
   if (ctx->p.coulomb_k != 0.0) {
-    CK(launch_gamma_real(st, m, S.nat, S.L, S.eta, S.R, S.gam, S.natp));
+    CK(launch_gamma_real(st, m, S.nat, S.L, S.eta, S.R, S.gam, S.natp, fp32_pairs));
     CK(launch_structure_factors(st, S.nat, S.ng, S.G4, S.R, S.SF, S.kp));
-    EpiF64 e;
-    e.alpha = ctx->p.coulomb_k;
-    e.E = S.gam;
-    e.lde = S.natp;
-    e.beta = 1.0;
-    CK(gemm_f64_nt(st, S.natp, S.natp, S.kp, S.SF, S.kp, S.SF, S.kp, S.gam, S.natp, e, false));
   }
-  CK(launch_gemv(st, S.nat, S.gam, S.natp, S.nh, S.pot));
+  CK(gamma_apply(ctx, S, S.nh, S.pot, S.work));
   CK(launch_apply_potential(st, S.nat, S.np, S.H0, S.pot, S.H));
   S.have_density = false;
   return XLBOMD_OK;
@@ -291,7 +291,8 @@ xlbomd_status density(xlbomd_ctx* ctx, Sys& S, bool with_forces) {
   CK(E.density_out(st, S.mats, S.N, dmu, S.dmu_diag, S.ddiag, S.Dm));
   CK(launch_charges(st, S.nat, S.ddiag, S.Z, S.nh, S.q, S.r));
   if (with_forces) {
-    CK(launch_forces(st, model_of(p), S.nat, S.L, S.eta, S.ng, S.G4, S.R, S.Dm, S.np, S.q, S.nh, S.F, S.work));
+    CK(launch_forces(st, model_of(p), S.nat, S.L, S.eta, S.ng, S.G4, S.R, S.Dm, S.np, S.q, S.nh, S.F, S.work,
+                     p.prec != XLBOMD_FP64));
   }
   S.have_density = true;
   return XLBOMD_OK;
@@ -301,7 +302,7 @@ xlbomd_status density(xlbomd_ctx* ctx, Sys& S, bool with_forces) {
 xlbomd_status response(xlbomd_ctx* ctx, Sys& S, const double* v, double* w) {
   cudaStream_t st = ctx->stream;
   const double sc = beta_of(ctx->p) / std::ldexp(1.0, ctx->p.n_sq + 1);
-  CK(launch_gemv(st, S.nat, S.gam, S.natp, v, S.potv));
+  CK(gamma_apply(ctx, S, v, S.potv, S.work));
   CK(launch_expand_potential(st, S.nat, S.np, -sc, S.potv, S.dvec));
   CK(ctx->eng->chain(st, S.mats, S.dvec, S.N, false, S.d1, S.stats));
   CK(launch_response_finish(st, S.nat, S.N, S.d1, S.dmu_diag, S.scal + 4, w));
@@ -389,7 +390,7 @@ xlbomd_status scf(xlbomd_ctx* ctx, Sys& S) {
   cudaStream_t st = ctx->stream;
   const xlbomd_params& p = ctx->p;
   for (int it = 0; it < p.scf_max_iter; ++it) {
-    CK(launch_gemv(st, S.nat, S.gam, S.natp, S.nh, S.pot));
+    CK(gamma_apply(ctx, S, S.nh, S.pot, S.work));
     CK(launch_apply_potential(st, S.nat, S.np, S.H0, S.pot, S.H));
     CKS(density(ctx, S, false));
     if (it == 0 && p.kernel_auto) {
@@ -405,7 +406,8 @@ xlbomd_status scf(xlbomd_ctx* ctx, Sys& S) {
     if (!std::isfinite(res) || res > 1e3) return fail(ctx, XLBOMD_ERR_DIVERGED, "t0 SCF diverged");
     if (res < p.scf_tol) {
       CK(launch_fill_history(st, S.nat, p.kmax, S.nh));
-      CK(launch_forces(st, model_of(p), S.nat, S.L, S.eta, S.ng, S.G4, S.R, S.Dm, S.np, S.q, S.nh, S.F, S.work));
+      CK(launch_forces(st, model_of(p), S.nat, S.L, S.eta, S.ng, S.G4, S.R, S.Dm, S.np, S.q, S.nh, S.F, S.work,
+                       p.prec != XLBOMD_FP64));
       return kernel_update(ctx, S);
     }
     if (p.scf_mode == 1 && p.rank_m > 0) {
@@ -458,7 +460,8 @@ void free_sys(Sys& S) {
 namespace {
 constexpr int kStaticMaxNp = 256;
 constexpr size_t kStaticMat = (size_t)kStaticMaxNp * kStaticMaxNp;
-constexpr size_t kStaticDoubles = 5 * kStaticMat + 3 * kStaticMaxNp + 64;
+constexpr int kStaticSf = 4096;   // structure-factor work vector (reciprocal vectors x 2)
+constexpr size_t kStaticDoubles = 5 * kStaticMat + 3 * kStaticMaxNp + 64 + kStaticSf;
 }  // namespace
 
 static __device__ __align__(256) double g_response_scratch[kStaticDoubles];
@@ -522,7 +525,8 @@ xlbomd_status xlbomd_response_noalloc(xlbomd_ctx* ctx, int sys, const double* v_
   double* scal = d1 + kStaticMaxNp;
   // the array keeps the previous call's contents: the diagonal accumulator starts at zero
   CK(cudaMemsetAsync(d1, 0, sizeof(double) * kStaticMaxNp, st));
-  CK(launch_gemv(st, S.nat, S.gam, S.natp, v_dev, potv));
+  if (S.kp > kStaticSf) return fail(ctx, XLBOMD_ERR_ARG, "xlbomd_response_noalloc: too many reciprocal vectors");
+  CK(gamma_apply(ctx, S, v_dev, potv, scal + 64));
   CK(launch_expand_potential(st, S.nat, S.np, -sc, potv, dvec));
   const bool prof = ctx->eng->prof;
   ctx->eng->prof = false;   // event timing would create CUDA events
@@ -748,7 +752,23 @@ xlbomd_status xlbomd_get(xlbomd_ctx* ctx, int sys, int what, double* host_out) {
     case XLBOMD_MU: host_out[0] = S.mu; return XLBOMD_OK;
     case XLBOMD_D: return cp2d(S.Dm, S.N, S.np);
     case XLBOMD_H: return cp2d(S.H, S.N, S.np);
-    case XLBOMD_GAMMA: return cp2d(S.gam, S.nat, S.natp);
+    case XLBOMD_GAMMA: {
+      // gamma_real + k SF SF^T, formed on demand
+      double* full = nullptr;
+      if (cudaMalloc((void**)&full, sizeof(double) * (size_t)S.natp * S.natp) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, XLBOMD_ERR_OOM, "cudaMalloc failed");
+      }
+      EpiF64 e;
+      e.alpha = ctx->p.coulomb_k;
+      e.E = S.gam;
+      e.lde = S.natp;
+      e.beta = 1.0;
+      cudaError_t ce = gemm_f64_nt(ctx->stream, S.natp, S.natp, S.kp, S.SF, S.kp, S.SF, S.kp, full, S.natp, e, false);
+      xlbomd_status rs = ce == cudaSuccess ? cp2d(full, S.nat, S.natp) : fail(ctx, XLBOMD_ERR_CUDA, "gamma product");
+      cudaFree(full);
+      return rs;
+    }
     case XLBOMD_STATS: std::memcpy(host_out, S.stats, 5 * sizeof(double)); return XLBOMD_OK;
     case XLBOMD_PROBES: {
       CK(cudaMemcpyAsync(host_out, S.pV, sizeof(double) * ctx->p.rank_m * nat, cudaMemcpyDeviceToHost, ctx->stream));

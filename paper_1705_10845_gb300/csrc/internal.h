@@ -33,9 +33,14 @@ struct ModelConst {
 // H0 (np x np, zeroed padding) from positions R (natoms x 3) in a box L.
 cudaError_t launch_build_H0(cudaStream_t s, const ModelConst& m, int nat, double L, const double* R,
                             double* H0, int np);
-// Real-space part of gamma over 27 images of the minimum image (natp x natp, ld natp).
+// Real-space part of gamma over 27 images of the minimum image (natp x natp, ld natp);
+// fp32: pair terms in FP32 (sums in FP64), for the split-precision path.
 cudaError_t launch_gamma_real(cudaStream_t s, const ModelConst& m, int nat, double L, double eta,
-                              const double* R, double* gam, int natp);
+                              const double* R, double* gam, int natp, bool fp32);
+// y = gamma x with gamma = gamma_real + k SF SF^T applied through the structure
+// factors (tmp: kp doubles; SF may be null when k = 0).
+cudaError_t launch_gamma_apply(cudaStream_t s, int nat, const double* gam, int natp, const double* SF, int kp,
+                               double k, const double* x, double* y, double* tmp);
 // Structure-factor matrix SF (natp x kp): row I = sqrt(A_g) [cos(G_g.R_I), sin(G_g.R_I)].
 cudaError_t launch_structure_factors(cudaStream_t s, int nat, int ng, const double* G4, const double* R,
                                      double* SF, int kp);
@@ -49,7 +54,7 @@ cudaError_t launch_gershgorin(cudaStream_t s, int n, int np, const double* H, do
 // Forces: band part from D (np x np) and Coulomb real-space + reciprocal parts.
 cudaError_t launch_forces(cudaStream_t s, const ModelConst& m, int nat, double L, double eta, int ng,
                           const double* G4, const double* R, const double* D, int np, const double* q,
-                          const double* n, double* F, double* work /* >= 4*ng */);
+                          const double* n, double* F, double* work /* >= 4*ng */, bool fp32);
 // q_I = sum_{a in I} (1 + Tn_aa) + 2 dmu dmu_diag_a - Z_I, r = q - n
 cudaError_t launch_charges(cudaStream_t s, int nat, const double* ddiag, const double* Z,
                            const double* n, double* q, double* r);

@@ -156,19 +156,20 @@ __global__ void forces_band_kernel(ModelConst m, int nat, double L, const double
 
 __device__ __forceinline__ double min_image(double d, double L) { return d - L * rint(d / L); }
 
-// erfc(eta r)/r + [1/sqrt(r^2+a^2) - 1/r], the bracket in cancellation-free form.
-__device__ __forceinline__ double ok_real(double r, double a, double eta) {
-  const double s = sqrt(r * r + a * a);
+template <typename R>
+__device__ __forceinline__ R ok_real_t(R r, R a, R eta) {
+  const R s = sqrt(r * r + a * a);
   return erfc(eta * r) / r - a * a / (r * s * (s + r));
 }
 
-// d/dr of ok_real: erf(eta r)/r^2 - 2 eta/sqrt(pi) exp(-eta^2 r^2)/r - r/(r^2+a^2)^(3/2)
-__device__ __forceinline__ double ok_real_dr(double r, double a, double eta) {
-  const double s2 = r * r + a * a;
-  return erf(eta * r) / (r * r) - 2.0 * eta / sqrt(kPi) * exp(-eta * eta * r * r) / r - r / (s2 * sqrt(s2));
+template <typename R>
+__device__ __forceinline__ R ok_real_dr_t(R r, R a, R eta) {
+  const R s2 = r * r + a * a;
+  return erf(eta * r) / (r * r) - R(2) * eta / sqrt(R(kPi)) * exp(-eta * eta * r * r) / r - r / (s2 * sqrt(s2));
 }
 
-__global__ void gamma_real_kernel(ModelConst m, int nat, double L, double eta, const double* __restrict__ R,
+template <typename R>
+__global__ void gamma_real_kernel(ModelConst m, int nat, double L, double eta, const double* __restrict__ R_,
                                   double* __restrict__ gam, int natp) {
   const int J = blockIdx.x * blockDim.x + threadIdx.x;
   const int I = blockIdx.y;
@@ -178,9 +179,9 @@ __global__ void gamma_real_kernel(ModelConst m, int nat, double L, double eta, c
     return;
   }
   const double a = m.k / m.U;
-  const double dx0 = min_image(R[3 * J] - R[3 * I], L);
-  const double dy0 = min_image(R[3 * J + 1] - R[3 * I + 1], L);
-  const double dz0 = min_image(R[3 * J + 2] - R[3 * I + 2], L);
+  const double dx0 = min_image(R_[3 * J] - R_[3 * I], L);
+  const double dy0 = min_image(R_[3 * J + 1] - R_[3 * I + 1], L);
+  const double dz0 = min_image(R_[3 * J + 2] - R_[3 * I + 2], L);
   double acc = 0.0;
   for (int tx = -1; tx <= 1; ++tx)
     for (int ty = -1; ty <= 1; ++ty)
@@ -190,7 +191,7 @@ __global__ void gamma_real_kernel(ModelConst m, int nat, double L, double eta, c
           continue;
         }
         const double dx = dx0 + tx * L, dy = dy0 + ty * L, dz = dz0 + tz * L;
-        acc += ok_real(sqrt(dx * dx + dy * dy + dz * dz), a, eta);
+        acc += (double)ok_real_t<R>((R)sqrt(dx * dx + dy * dy + dz * dz), (R)a, (R)eta);
       }
   gam[(size_t)I * natp + J] = m.k * acc;
 }
@@ -222,6 +223,31 @@ __global__ void gemv_kernel(int nat, const double* __restrict__ gam, int natp, c
   double acc = 0.0;
   for (int J = lane; J < nat; J += 32) acc += gam[(size_t)I * natp + J] * x[J];
   acc = warp_sum(acc);
+  if (lane == 0) y[I] = acc;
+}
+
+// t[g] = sum_I SF[I][g] x[I]
+__global__ void sf_dot_kernel(int nat, int kp, const double* __restrict__ SF, const double* __restrict__ x,
+                              double* __restrict__ t) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= kp) return;
+  double acc = 0.0;
+  for (int I = 0; I < nat; ++I) acc += SF[(size_t)I * kp + g] * x[I];
+  t[g] = acc;
+}
+
+// y_I = sum_J gamma_real_IJ x_J + k sum_g SF[I][g] t[g]
+__global__ void gamma_apply_kernel(int nat, const double* __restrict__ gam, int natp, const double* __restrict__ SF,
+                                   int kp, double k, const double* __restrict__ t, const double* __restrict__ x,
+                                   double* __restrict__ y) {
+  const int I = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (I >= nat) return;
+  double acc = 0.0, rec = 0.0;
+  for (int J = lane; J < nat; J += 32) acc += gam[(size_t)I * natp + J] * x[J];
+  if (SF)
+    for (int g = lane; g < kp; g += 32) rec += SF[(size_t)I * kp + g] * t[g];
+  acc = warp_sum(acc + k * rec);
   if (lane == 0) y[I] = acc;
 }
 
@@ -275,7 +301,8 @@ __global__ void minmax_kernel(int n, const double* __restrict__ lohi, double* __
 
 // Coulomb real-space force: F_K -= k sum_{I != K} w_IK sum_T phi'(r) d/r,
 // d = mi(R_K - R_I) + T L, w_IK = (a_I b_K + a_K b_I)/2, a = 2q - n, b = n.
-__global__ void forces_coul_real_kernel(ModelConst m, int nat, double L, double eta, const double* __restrict__ R,
+template <typename R>
+__global__ void forces_coul_real_kernel(ModelConst m, int nat, double L, double eta, const double* __restrict__ R_,
                                         const double* __restrict__ q, const double* __restrict__ n,
                                         double* __restrict__ F) {
   const int K = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -287,15 +314,15 @@ __global__ void forces_coul_real_kernel(ModelConst m, int nat, double L, double 
   for (int I = lane; I < nat; I += 32) {
     if (I == K) continue;
     const double w = 0.5 * ((2.0 * q[I] - n[I]) * bK + aK * n[I]);
-    const double dx0 = min_image(R[3 * K] - R[3 * I], L);
-    const double dy0 = min_image(R[3 * K + 1] - R[3 * I + 1], L);
-    const double dz0 = min_image(R[3 * K + 2] - R[3 * I + 2], L);
+    const double dx0 = min_image(R_[3 * K] - R_[3 * I], L);
+    const double dy0 = min_image(R_[3 * K + 1] - R_[3 * I + 1], L);
+    const double dz0 = min_image(R_[3 * K + 2] - R_[3 * I + 2], L);
     for (int tx = -1; tx <= 1; ++tx)
       for (int ty = -1; ty <= 1; ++ty)
         for (int tz = -1; tz <= 1; ++tz) {
           const double dx = dx0 + tx * L, dy = dy0 + ty * L, dz = dz0 + tz * L;
-          const double r = sqrt(dx * dx + dy * dy + dz * dz);
-          const double g = w * ok_real_dr(r, a, eta) / r;
+          const R r = (R)sqrt(dx * dx + dy * dy + dz * dz);
+          const double g = w * (double)(ok_real_dr_t<R>(r, (R)a, (R)eta) / r);
           f[0] += g * dx;
           f[1] += g * dy;
           f[2] += g * dz;
@@ -431,9 +458,26 @@ cudaError_t launch_build_H0(cudaStream_t s, const ModelConst& m, int nat, double
 }
 
 cudaError_t launch_gamma_real(cudaStream_t s, const ModelConst& m, int nat, double L, double eta, const double* R,
-                              double* gam, int natp) {
+                              double* gam, int natp, bool fp32) {
   dim3 grid((natp + 127) / 128, nat);
-  gamma_real_kernel<<<grid, 128, 0, s>>>(m, nat, L, eta, R, gam, natp);
+  if (fp32)
+    gamma_real_kernel<float><<<grid, 128, 0, s>>>(m, nat, L, eta, R, gam, natp);
+  else
+    gamma_real_kernel<double><<<grid, 128, 0, s>>>(m, nat, L, eta, R, gam, natp);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gamma_apply(cudaStream_t s, int nat, const double* gam, int natp, const double* SF, int kp,
+                               double k, const double* x, double* y, double* tmp) {
+  if (SF && k != 0.0) {
+    sf_dot_kernel<<<(kp + 255) / 256, 256, 0, s>>>(nat, kp, SF, x, tmp);
+    note_launch();
+  } else {
+    SF = nullptr;
+  }
+  const int wpb = 8;
+  gamma_apply_kernel<<<(nat + wpb - 1) / wpb, 32 * wpb, 0, s>>>(nat, gam, natp, SF, kp, k, tmp, x, y);
   note_launch();
   return cudaGetLastError();
 }
@@ -474,13 +518,16 @@ cudaError_t launch_gershgorin(cudaStream_t s, int n, int np, const double* H, do
 
 cudaError_t launch_forces(cudaStream_t s, const ModelConst& m, int nat, double L, double eta, int ng,
                           const double* G4, const double* R, const double* D, int np, const double* q,
-                          const double* n, double* F, double* work) {
+                          const double* n, double* F, double* work, bool fp32) {
   const int wpb = 8;
   const int nb = (nat + wpb - 1) / wpb;
   forces_band_kernel<<<nb, 32 * wpb, 0, s>>>(m, nat, L, R, D, np, F);
   note_launch();
   if (m.k != 0.0) {
-    forces_coul_real_kernel<<<nb, 32 * wpb, 0, s>>>(m, nat, L, eta, R, q, n, F);
+    if (fp32)
+      forces_coul_real_kernel<float><<<nb, 32 * wpb, 0, s>>>(m, nat, L, eta, R, q, n, F);
+    else
+      forces_coul_real_kernel<double><<<nb, 32 * wpb, 0, s>>>(m, nat, L, eta, R, q, n, F);
     note_launch();
     coul_sums_kernel<<<ng, 256, 0, s>>>(nat, ng, G4, R, q, n, work);
     note_launch();
