@@ -30,6 +30,9 @@ if ROOT not in sys.path:
 
 METRIC = "XL-BOMD steps/s and FOE TFLOP/s vs peak, mixed vs FP64 GPU at |dq|<=1e-5 e"
 ALPHA_MIX = 0.06
+# DRAM bytes (read + write) of one dense n = 6144 launch of the product kernel,
+# from the ncu capture summarised in profiles/gemm_tc_fp16x3_n6144.md
+GEMM_TRAFFIC_N6144 = 1.211e9 + 0.142e9
 
 
 def parse():
@@ -338,7 +341,9 @@ def main():
         "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": a.prec, "data": "synthetic", "config": workload_config(a, f"replicas x{ws}"),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": GEMM_TRAFFIC_N6144 if (a.natoms == 1536 and a.prec == "fp16x3") else None,
+                     "traffic_note": "bytes per dense n = 6144 launch (ncu); algorithmic 0.453 GB",
                      "kernel": "gemm_tc_kernel (split-precision tcgen05 product)",
                      "note": f"algorithmic 2n^3 per product (n^3 when symmetric-output) over CUDA-event time of "
                              f"{int(gemm_launches)} launches; each split product runs 3 half-precision "
