@@ -47,7 +47,7 @@ typedef enum {
   XLBOMD_ERR_NOT_CONVERGED = -4, /* SCF or chemical-potential iteration budget spent */
   XLBOMD_ERR_SPECTRUM = -5,      /* |beta (e - mu)| / 2^(n+1) >= 1 for a Gershgorin bound */
   XLBOMD_ERR_DIVERGED = -6,      /* residual |q - n| above the divergence threshold */
-  XLBOMD_ERR_TIMEOUT = -7,       /* a bounded device wait gave up */
+  XLBOMD_ERR_TIMEOUT = -7,       /* a bounded device wait gave up, or a product tile fell outside the matrix */
   XLBOMD_ERR_UNSUPPORTED = -8    /* requested precision not built for this device */
 } xlbomd_status;
 
@@ -139,7 +139,11 @@ xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* syst
 /* t0 ground state of system sys (Eq. IBC): SCF to max|q - n| < scf_tol by
  * linear mixing n <- n + mix_alpha (q[n] - n) (Eq. SCF_K with K_0, scf_mode 0)
  * or by n <- n - K_m (q[n] - n) with the rank-m kernel (Eq. SCF_K, scf_mode 1);
- * then n-history = n(t0), forces and K r at t0.  sys = -1: every system. */
+ * then n-history = n(t0), forces and K r at t0.  sys = -1: every system.
+ * Split precisions also stop at the rounding floor of their products: when
+ * max|q - n| is below 100 scf_tol and has not fallen by 10% in 4 iterations.
+ * Errors: ERR_NOT_CONVERGED (scf_max_iter spent), ERR_DIVERGED (non-finite or
+ * max|q - n| > 1e3), and those of xlbomd_density. */
 xlbomd_status xlbomd_scf(xlbomd_ctx* ctx, int sys);
 
 /* a1-a2: H0 and gamma at the current R, H[n] = H0 + diag(gamma n). */

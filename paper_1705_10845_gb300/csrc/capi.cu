@@ -229,6 +229,8 @@ xlbomd_status density(xlbomd_ctx* ctx, Sys& S, bool with_forces) {
   CK(launch_gershgorin(st, S.N, S.np, S.H, S.work));
   CKS(sync_read(ctx, S.work, 2));
   const double glo = ctx->pinned[0], ghi = ctx->pinned[1];
+  if (!std::isfinite(glo) || !std::isfinite(ghi))
+    return fail(ctx, XLBOMD_ERR_SPECTRUM, "non-finite Hamiltonian (Gershgorin bounds)");
 
   double mu;
   if (S.mu_valid) {
@@ -242,6 +244,7 @@ xlbomd_status density(xlbomd_ctx* ctx, Sys& S, bool with_forces) {
   }
   double blo = glo - 1.0, bhi = ghi + 1.0;   // bracket of the root of Tr D(mu) = N_occ
   const double tol_ns = (p.prec == XLBOMD_FP64) ? 1e-16 : 1e-8;
+  const double occ_floor = ((p.prec == XLBOMD_FP64) ? 1e-12 : 1e-6) * S.N;
   std::vector<int> plan_s;
   std::vector<double> plan_c;
   double dmu = 0.0;
@@ -251,12 +254,18 @@ xlbomd_status density(xlbomd_ctx* ctx, Sys& S, bool with_forces) {
     const double t0max = sc * std::max(std::fabs(ghi - mu), std::fabs(mu - glo));
     if (!(t0max < 1.0)) return fail(ctx, XLBOMD_ERR_SPECTRUM, "|beta (e - mu)| / 2^(n+1) >= 1");
     ns_plan(t0max, n, tol_ns, plan_s, plan_c);
+    S.mats.t0max = t0max;
     CK(E.foe(st, S.mats, S.H, S.N, mu, sc, plan_s, plan_c, S.stats));
     // mu chain: T1_0 = +sc I, full last level
     CK(E.chain(st, S.mats, S.dvec_mu, S.N, true, S.dmu_diag, S.stats));
     CK(E.trace_tn(st, S.mats, S.N, S.scal));          // scal[0] = sum_i T_n,ii
     CK(launch_sum(st, S.N, S.dmu_diag, S.scal + 1));    // scal[1] = sum_i dT_n,ii/dmu
+    int* herr = reinterpret_cast<int*>(ctx->pinned + 63);
+    *herr = 0;
+    if (const int* derr = E.device_error())
+      CK(cudaMemcpyAsync(herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st));
     CKS(sync_read(ctx, S.scal, 2));
+    if (*herr != 0) return fail(ctx, XLBOMD_ERR_TIMEOUT, "tensor-core product: a bounded wait gave up or a tile was out of range");
     const double trD = 0.5 * (S.N + ctx->pinned[0]);
     const double trDmu = 0.5 * ctx->pinned[1];
     if (!std::isfinite(trD) || !std::isfinite(trDmu))
@@ -266,12 +275,19 @@ xlbomd_status density(xlbomd_ctx* ctx, Sys& S, bool with_forces) {
     else
       bhi = std::min(bhi, mu);
     const double dmu_prev = dmu;
-    dmu = (trDmu > 0.0) ? (S.nocc - trD) / trDmu : 0.0;
+    const double err = S.nocc - trD;
+    // Newton step; none where Tr D is flat in mu (mu in a gap or outside the spectrum)
+    dmu = (trDmu > 0.0) ? err / trDmu : HUGE_VAL;
     S.stats[0] += 1;
     if (debug_enabled())
       std::fprintf(stderr, "[xlbomd] mu pass %d: mu %.12f trD %.10f (nocc %.1f) trDmu %.6e dmu %.3e bracket [%.6f, %.6f] t0max %.4e\n",
                    pass, mu, trD, S.nocc, trDmu, dmu, blo, bhi, t0max);
     if (std::fabs(dmu) * beta < p.mu_tol) break;
+    // flat region with the occupation already met to the trace's rounding floor: keep mu
+    if (std::fabs(err) < occ_floor) {
+      dmu = 0.0;
+      break;
+    }
     // Newton converges quadratically; once a step is not much smaller than
     // the previous one (and already small), the rounding noise of the
     // product arithmetic has been reached: keep the first-order correction.
@@ -389,6 +405,8 @@ xlbomd_status stiffest_mode(xlbomd_ctx* ctx, Sys& S, double* lambda) {
 xlbomd_status scf(xlbomd_ctx* ctx, Sys& S) {
   cudaStream_t st = ctx->stream;
   const xlbomd_params& p = ctx->p;
+  double best = HUGE_VAL;
+  int since_best = 0;
   for (int it = 0; it < p.scf_max_iter; ++it) {
     CK(gamma_apply(ctx, S, S.nh, S.pot, S.work));
     CK(launch_apply_potential(st, S.nat, S.np, S.H0, S.pot, S.H));
@@ -404,7 +422,16 @@ xlbomd_status scf(xlbomd_ctx* ctx, Sys& S) {
     const double res = ctx->pinned[0];
     if (debug_enabled()) std::fprintf(stderr, "[xlbomd] scf it %d max|q - n| %.3e mu %.8f\n", it, res, S.mu);
     if (!std::isfinite(res) || res > 1e3) return fail(ctx, XLBOMD_ERR_DIVERGED, "t0 SCF diverged");
-    if (res < p.scf_tol) {
+    // split precisions: the residual stops falling at the rounding floor of the products
+    if (res < 0.9 * best) {
+      best = res;
+      since_best = 0;
+    } else {
+      ++since_best;
+    }
+    const bool floor = p.prec != XLBOMD_FP64 && since_best >= 4 && res < 100.0 * p.scf_tol;
+    if (floor && debug_enabled()) std::fprintf(stderr, "[xlbomd] scf stops at the rounding floor %.3e\n", res);
+    if (res < p.scf_tol || floor) {
       CK(launch_fill_history(st, S.nat, p.kmax, S.nh));
       CK(launch_forces(st, model_of(p), S.nat, S.L, S.eta, S.ng, S.G4, S.R, S.Dm, S.np, S.q, S.nh, S.F, S.work,
                        p.prec != XLBOMD_FP64));
@@ -600,7 +627,8 @@ xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* syst
   };
   if (cudaMallocHost((void**)&ctx->pinned, 64 * sizeof(double)) != cudaSuccess) return bail(XLBOMD_ERR_OOM);
   if (dalloc(ctx, &ctx->cdev, 8) != XLBOMD_OK) return bail(XLBOMD_ERR_OOM);
-  if (cudaMemcpy(ctx->cdev, p.c, sizeof(double) * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+  // every upload and memset below runs on the context's stream, which may be non-blocking
+  if (cudaMemcpyAsync(ctx->cdev, p.c, sizeof(double) * 8, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
     return bail(XLBOMD_ERR_CUDA);
   ctx->sys.resize(nsys);
   const double sc = beta_of(p) / std::ldexp(1.0, p.n_sq + 1);
@@ -652,18 +680,20 @@ xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* syst
     A(&S.work, std::max<size_t>({(size_t)4 * S.ng + 16, (size_t)2 * S.N + 16, (size_t)4096}));
     A(&S.energy, 8);
     if (st != XLBOMD_OK) return bail(st);
-    if (alloc_matset(S.mats, p.prec, S.np, p.n_sq) != cudaSuccess) return bail(XLBOMD_ERR_OOM);
+    if (alloc_matset(S.mats, p.prec, S.np, p.n_sq, ctx->stream) != cudaSuccess) return bail(XLBOMD_ERR_OOM);
     // R wrapped into [0, L)
     std::vector<double> Rw(3 * nat);
     for (size_t a = 0; a < 3 * nat; ++a) Rw[a] = s.R[a] - S.L * std::floor(s.R[a] / S.L);
-    if (cudaMemcpy(S.R, Rw.data(), sizeof(double) * 3 * nat, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(S.V, s.V, sizeof(double) * 3 * nat, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(S.Z, s.Z, sizeof(double) * nat, cudaMemcpyHostToDevice) != cudaSuccess ||
-        (S.ng && cudaMemcpy(S.G4, S.G4h.data(), sizeof(double) * S.G4h.size(), cudaMemcpyHostToDevice) != cudaSuccess))
-      return bail(XLBOMD_ERR_CUDA);
     std::vector<double> dmu(S.np, 0.0);
     for (int a = 0; a < S.N; ++a) dmu[a] = sc;
-    if (cudaMemcpy(S.dvec_mu, dmu.data(), sizeof(double) * S.np, cudaMemcpyHostToDevice) != cudaSuccess)
+    const cudaStream_t cs = ctx->stream;
+    if (cudaMemcpyAsync(S.R, Rw.data(), sizeof(double) * 3 * nat, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaMemcpyAsync(S.V, s.V, sizeof(double) * 3 * nat, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaMemcpyAsync(S.Z, s.Z, sizeof(double) * nat, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        (S.ng && cudaMemcpyAsync(S.G4, S.G4h.data(), sizeof(double) * S.G4h.size(), cudaMemcpyHostToDevice, cs) !=
+                     cudaSuccess) ||
+        cudaMemcpyAsync(S.dvec_mu, dmu.data(), sizeof(double) * S.np, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaStreamSynchronize(cs) != cudaSuccess)   // Rw and dmu are host temporaries
       return bail(XLBOMD_ERR_CUDA);
     if (build_H(ctx, S) != XLBOMD_OK) return bail((xlbomd_status)ctx->status);
   }

@@ -112,19 +112,19 @@ class EngineF64 : public Engine {
 
 }  // namespace
 
-cudaError_t alloc_matset(MatSet& m, int prec, int np, int n) {
+cudaError_t alloc_matset(MatSet& m, int prec, int np, int n, cudaStream_t s) {
   m.prec = prec;
   m.np = np;
   m.n = n;
   const size_t bytes = sizeof(double) * (size_t)np * np;
-  if (prec != 0) return alloc_matset_split(m);
+  if (prec != 0) return alloc_matset_split(m, s);
   auto A = [&](double** p) -> cudaError_t {
     cudaError_t e = cudaMalloc((void**)p, bytes);
     if (e != cudaSuccess) {
       *p = nullptr;
       return e;
     }
-    return cudaMemset(*p, 0, bytes);
+    return cudaMemsetAsync(*p, 0, bytes, s);
   };
   m.T.assign(n + 1, nullptr);
   m.Y.assign(n, nullptr);

@@ -161,7 +161,19 @@ __global__ void density_out_f32_kernel(int N, int np, const float* __restrict__ 
   D[idx] = v;
 }
 
-__global__ void fill_nan_kernel(double* out) { *out = nan(""); }
+__global__ void df_to_f64_kernel(size_t count, const float2* __restrict__ x, double* __restrict__ y) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) y[i] = (double)x[i].x + (double)x[i].y;
+}
+
+// dst = I - W (W an FP32 value, dst FP64)
+__global__ void ident_minus_f32_to_f64_kernel(size_t count, int np, const float* __restrict__ W,
+                                              double* __restrict__ dst) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int r = (int)(i / np), c = (int)(i % np);
+  dst[i] = (r == c ? 1.0 : 0.0) - (double)W[i];
+}
 
 template <bool BF16>
 __global__ void convert_split_d_kernel(size_t count, const float2* __restrict__ d, const unsigned* __restrict__ amax,
@@ -323,25 +335,28 @@ class EngineSplit : public Engine {
     return cudaGetLastError();
   }
 
-  cudaError_t prep_tiles(int np) {
+  // Symmetric-product tile lists for size np, uploaded on the stream that uses them (the
+  // context's stream may be non-blocking, so a legacy-stream copy would not be ordered
+  // before the first product).
+  cudaError_t prep_tiles(int np, cudaStream_t s) {
     if (tiles_.count(np)) return cudaSuccess;
     std::vector<int> t128 = tc_sym_tiles(np, 128), t256 = (np % 256 == 0) ? tc_sym_tiles(np, 256) : std::vector<int>();
     std::vector<int> all(t128);
     all.insert(all.end(), t256.begin(), t256.end());
     int* d = nullptr;
     RET(cudaMalloc((void**)&d, sizeof(int) * std::max<size_t>(all.size(), 2)));
-    RET(cudaMemcpy(d, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice));
+    RET(cudaMemcpyAsync(d, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice, s));
     tiles_[np] = {d, {(int)t128.size() / 2, (int)t256.size() / 2}};
     if (!err_) {
       RET(cudaMalloc((void**)&err_, sizeof(int)));
-      RET(cudaMemset(err_, 0, sizeof(int)));
+      RET(cudaMemsetAsync(err_, 0, sizeof(int), s));
     }
-    return cudaSuccess;
+    return cudaStreamSynchronize(s);   // `all` is a host temporary
   }
 
   cudaError_t gemm(cudaStream_t s, int np, const SplitMat& A, const SplitMat& B, SplitMat& C, const Epi& e,
                    bool sym, double* stats) {
-    RET(prep_tiles(np));
+    RET(prep_tiles(np, s));
     auto& tl = tiles_[np];
     RET(cudaMemsetAsync(C.amax, 0, sizeof(unsigned), s));
     TcArgs a;
@@ -487,6 +502,8 @@ class EngineSplit : public Engine {
     return cudaSuccess;
   }
 
+  const int* device_error() const override { return err_; }
+
   cudaError_t trace_tn(cudaStream_t s, MatSet& m, int N, double* out) override {
     diag_sum_d_kernel<<<1, 1024, 0, s>>>(N, m.np, m.sT[m.n].d, out);
     note_launch();
@@ -500,11 +517,28 @@ class EngineSplit : public Engine {
     return cudaGetLastError();
   }
 
-  cudaError_t entropy(cudaStream_t s, MatSet&, int, double, int, double, double, const double*, const double*,
-                      double*, double* out) override {
-    fill_nan_kernel<<<1, 1, 0, s>>>(out);
+  cudaError_t entropy(cudaStream_t s, MatSet& m, int N, double, int n_sq, double, double, const double* D,
+                      const double*, double* work, double* out) override {
+    // FP64 route from the split values: T_0 from its double-float value, Y_k = I - W_k
+    const size_t cnt = (size_t)m.np * m.np;
+    for (double*& p : m.e64)
+      if (!p) RET(cudaMalloc((void**)&p, cnt * sizeof(double)));
+    double* T0 = m.e64[6];
+    df_to_f64_kernel<<<nblk(cnt), 256, 0, s>>>(cnt, m.sT[0].d, T0);
     note_launch();
-    return cudaGetLastError();
+    RET(cudaGetLastError());
+    auto load_Y = [&](int k, double* dst) -> cudaError_t {
+      ident_minus_f32_to_f64_kernel<<<nblk(cnt), 256, 0, s>>>(cnt, m.np, m.sY[k].f, dst);
+      note_launch();
+      return cudaGetLastError();
+    };
+    // artanh series: terms until 2^(n+1) t0max^(2j+1) / (2j+1) N < 1e-10
+    int nterms = 1;
+    const double t = m.t0max;
+    while (nterms < 6 && std::ldexp(1.0, n_sq + 1) * std::pow(t, 2 * nterms + 1) / (2 * nterms + 1) * N > 1e-10)
+      ++nterms;
+    return entropy_fp64(s, N, m.np, m.n, n_sq, T0, load_Y, m.e64[0], m.e64[1], m.e64[2], m.e64[3], m.e64[4],
+                        m.e64[5], nterms, D, work, out);
   }
 
   int* err_ = nullptr;
@@ -517,20 +551,21 @@ class EngineSplit : public Engine {
 // which value arrays a matrix keeps
 enum { kF = 1, kD = 2 };
 
-cudaError_t alloc_split(SplitMat& m, int np, float* scal_f, unsigned* scal_u, int what = kF) {
+// Zeroing runs on the stream `s` that later uses the matrix.
+cudaError_t alloc_split(SplitMat& m, int np, float* scal_f, unsigned* scal_u, int what, cudaStream_t s) {
   const size_t cnt = (size_t)np * np;
   if (what & kF) {
     RET(cudaMalloc((void**)&m.f, cnt * sizeof(float)));
-    RET(cudaMemset(m.f, 0, cnt * sizeof(float)));
+    RET(cudaMemsetAsync(m.f, 0, cnt * sizeof(float), s));
   }
   if (what & kD) {
     RET(cudaMalloc((void**)&m.d, cnt * sizeof(float2)));
-    RET(cudaMemset(m.d, 0, cnt * sizeof(float2)));
+    RET(cudaMemsetAsync(m.d, 0, cnt * sizeof(float2), s));
   }
   RET(cudaMalloc((void**)&m.hi, cnt * sizeof(uint16_t)));
   RET(cudaMalloc((void**)&m.lo, cnt * sizeof(uint16_t)));
-  RET(cudaMemset(m.hi, 0, cnt * sizeof(uint16_t)));
-  RET(cudaMemset(m.lo, 0, cnt * sizeof(uint16_t)));
+  RET(cudaMemsetAsync(m.hi, 0, cnt * sizeof(uint16_t), s));
+  RET(cudaMemsetAsync(m.lo, 0, cnt * sizeof(uint16_t), s));
   m.scale = scal_f;
   m.amax = scal_u;
   return cudaSuccess;
@@ -559,12 +594,12 @@ Engine* make_split_engine(int prec) {
   return new EngineSplit(prec);
 }
 
-cudaError_t alloc_matset_split(MatSet& m) {
+cudaError_t alloc_matset_split(MatSet& m, cudaStream_t s) {
   const int np = m.np, n = m.n;
   const int nmat = (n + 1) + n + 9;
   float* scal = nullptr;
   RET(cudaMalloc((void**)&scal, sizeof(float) * 2 * nmat));
-  RET(cudaMemset(scal, 0, sizeof(float) * 2 * nmat));
+  RET(cudaMemsetAsync(scal, 0, sizeof(float) * 2 * nmat, s));
   m.tc_plan = scal;
   float* sf = scal;
   unsigned* su = reinterpret_cast<unsigned*>(scal + nmat);
@@ -572,11 +607,11 @@ cudaError_t alloc_matset_split(MatSet& m) {
   m.sT.assign(n + 1, SplitMat());
   m.sY.assign(n, SplitMat());
   for (auto& x : m.sT) {
-    RET(alloc_split(x, np, sf + idx, su + idx, kD));
+    RET(alloc_split(x, np, sf + idx, su + idx, kD, s));
     ++idx;
   }
   for (auto& x : m.sY) {
-    RET(alloc_split(x, np, sf + idx, su + idx, kF));
+    RET(alloc_split(x, np, sf + idx, su + idx, kF, s));
     ++idx;
   }
   struct W {
@@ -585,7 +620,7 @@ cudaError_t alloc_matset_split(MatSet& m) {
   } w[] = {{&m.sS, kF},  {&m.sQ, kF},  {&m.sYw, kF},  {&m.sG, kF},  {&m.sA1, kF},
            {&m.sMt, kD}, {&m.sT1a, kD}, {&m.sT1b, kD}, {&m.sTmu, kD}};
   for (auto& x : w) {
-    RET(alloc_split(*x.m, np, sf + idx, su + idx, x.what));
+    RET(alloc_split(*x.m, np, sf + idx, su + idx, x.what, s));
     ++idx;
   }
   return cudaSuccess;
@@ -600,6 +635,10 @@ void free_matset_split(MatSet& m) {
   for (SplitMat* x : w) free_split(*x);
   if (m.tc_plan) cudaFree(m.tc_plan);
   m.tc_plan = nullptr;
+  for (double*& p : m.e64) {
+    if (p) cudaFree(p);
+    p = nullptr;
+  }
 }
 
 // ---- self-test of the tensor-core product against the FP64 product ----
@@ -667,8 +706,8 @@ int selftest_gemm(int n, int prec, int sym, double* result) {
       cudaMalloc((void**)&out, 8) || cudaMalloc((void**)&scal, 6 * sizeof(float)))
     goto done;
   cudaMemset(scal, 0, 6 * sizeof(float));
-  if (alloc_split(sa, n, scal, (unsigned*)scal + 3) || alloc_split(sb, n, scal + 1, (unsigned*)scal + 4) ||
-      alloc_split(sc, n, scal + 2, (unsigned*)scal + 5))
+  if (alloc_split(sa, n, scal, (unsigned*)scal + 3, kF, s) || alloc_split(sb, n, scal + 1, (unsigned*)scal + 4, kF, s) ||
+      alloc_split(sc, n, scal + 2, (unsigned*)scal + 5, kF, s))
     goto done;
   fill_random_kernel<<<nblk(cnt), 256>>>(cnt, n, 11, 0, A);
   note_launch();

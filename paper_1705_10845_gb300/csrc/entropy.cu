@@ -11,6 +11,7 @@
 // by a blocked FP64 Cholesky factorisation; artanh(T_0) is its odd power
 // series (|t_0| << 1), whose traces against D come from Frobenius products.
 #include <cmath>
+#include <functional>
 
 #include "precision.h"
 
@@ -127,14 +128,14 @@ cudaError_t logdet_spd(cudaStream_t s, double* W, int np, double* part, double* 
 
 }  // namespace
 
-cudaError_t launch_entropy_f64(cudaStream_t s, MatSet& m, int N, double beta, int n_sq, double mu, double dmu,
-                               const double* D, const double* H, double* work, double* out) {
-  (void)beta;
-  (void)mu;
-  (void)dmu;
-  (void)H;
-  const int np = m.np, n = m.n;
-  if (n + 1 > 42) return cudaErrorInvalidValue;
+// Entropy from FP64 inputs.  T0: FP64 T_0; load_Y(k, dst) writes Y_k as an
+// FP64 matrix into dst; G, S, Q, Yw, A1, Mt: FP64 work matrices (np x np);
+// nterms: terms j = 0..nterms-1 of the artanh series.
+cudaError_t entropy_fp64(cudaStream_t s, int N, int np, int n, int n_sq, const double* T0,
+                         const std::function<cudaError_t(int, double*)>& load_Y, double* G, double* S, double* Q,
+                         double* Yw, double* A1, double* Mt, int nterms, const double* D, double* work,
+                         double* out) {
+  if (n + 1 > 42 || nterms < 1 || nterms > 6) return cudaErrorInvalidValue;
   // work layout: [0, 64): logdet slots, [64, 72): trace slots, [128, 128 + np/CB): Cholesky partials,
   // [1024, 2048): Frobenius partials
   double* ld = work;
@@ -143,38 +144,60 @@ cudaError_t launch_entropy_f64(cudaStream_t s, MatSet& m, int N, double beta, in
   double* fwork = work + 1024;
   const size_t count = (size_t)np * np;
   // logdet(I - T_0)
-  ident_minus_f64_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(count, np, m.T[0], m.G);
+  ident_minus_f64_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(count, np, T0, G);
   note_launch();
   RET(cudaGetLastError());
-  RET(logdet_spd(s, m.G, np, part, ld + 0));
+  RET(logdet_spd(s, G, np, part, ld + 0));
   // logdet(Y_k)
   for (int k = 0; k < n; ++k) {
-    RET(cudaMemcpyAsync(m.G, m.Y[k], sizeof(double) * count, cudaMemcpyDeviceToDevice, s));
-    RET(logdet_spd(s, m.G, np, part, ld + 1 + k));
+    RET(load_Y(k, G));
+    RET(logdet_spd(s, G, np, part, ld + 1 + k));
   }
-  // Tr[D T0^(2j+1)], j = 0..5, from S0 = T0^2, S2 = S0^2, S4 = S2^2, P1 = D T0, P3 = P1 S0
+  // Tr[D T0^(2j+1)] from S0 = T0^2, S2 = S0^2, S4 = S2^2, P1 = D T0, P3 = P1 S0
   EpiF64 e;
-  RET(gemm_f64_nt(s, np, np, np, m.T[0], np, m.T[0], np, m.S, np, e, true));   // S0
-  RET(gemm_f64_nt(s, np, np, np, m.S, np, m.S, np, m.Q, np, e, true));         // S2 = S0^2
-  RET(gemm_f64_nt(s, np, np, np, m.Q, np, m.Q, np, m.Yw, np, e, true));        // S4
-  RET(gemm_f64_nt(s, np, np, np, D, np, m.T[0], np, m.A1, np, e, false));      // P1 = D T0
-  RET(gemm_f64_nt(s, np, np, np, m.A1, np, m.S, np, m.Mt, np, e, false));      // P3 = P1 S0
-  RET(launch_frob_dot(s, N, np, D, m.T[0], fwork, tr + 0));     // Tr D T0
-  RET(launch_frob_dot(s, N, np, m.A1, m.S, fwork, tr + 1));     // Tr D T0^3
-  RET(launch_frob_dot(s, N, np, m.A1, m.Q, fwork, tr + 2));     // Tr D T0^5
-  RET(launch_frob_dot(s, N, np, m.Mt, m.Q, fwork, tr + 3));     // Tr D T0^7
-  RET(launch_frob_dot(s, N, np, m.A1, m.Yw, fwork, tr + 4));    // Tr D T0^9
-  RET(launch_frob_dot(s, N, np, m.Mt, m.Yw, fwork, tr + 5));    // Tr D T0^11
+  RET(cudaMemsetAsync(tr, 0, 8 * sizeof(double), s));
+  RET(launch_frob_dot(s, N, np, D, T0, fwork, tr + 0));                                    // Tr D T0
+  if (nterms > 1) {
+    RET(gemm_f64_nt(s, np, np, np, T0, np, T0, np, S, np, e, true));                        // S0
+    RET(gemm_f64_nt(s, np, np, np, D, np, T0, np, A1, np, e, false));                       // P1 = D T0
+    RET(launch_frob_dot(s, N, np, A1, S, fwork, tr + 1));                                   // Tr D T0^3
+  }
+  if (nterms > 2) {
+    RET(gemm_f64_nt(s, np, np, np, S, np, S, np, Q, np, e, true));                          // S2 = S0^2
+    RET(launch_frob_dot(s, N, np, A1, Q, fwork, tr + 2));                                   // Tr D T0^5
+  }
+  if (nterms > 3) {
+    RET(gemm_f64_nt(s, np, np, np, A1, np, S, np, Mt, np, e, false));                       // P3 = P1 S0
+    RET(launch_frob_dot(s, N, np, Mt, Q, fwork, tr + 3));                                   // Tr D T0^7
+  }
+  if (nterms > 4) {
+    RET(gemm_f64_nt(s, np, np, np, Q, np, Q, np, Yw, np, e, true));                         // S4
+    RET(launch_frob_dot(s, N, np, A1, Yw, fwork, tr + 4));                                  // Tr D T0^9
+  }
+  if (nterms > 5) RET(launch_frob_dot(s, N, np, Mt, Yw, fwork, tr + 5));                    // Tr D T0^11
   EntW w{};
   w.nld = n + 1;
   w.w_ld[0] = std::ldexp(1.0, n_sq);
   for (int k = 0; k < n; ++k) w.w_ld[1 + k] = std::ldexp(1.0, n_sq - 1 - k);
-  w.ntr = 6;
-  for (int j = 0; j < 6; ++j) w.w_tr[j] = std::ldexp(1.0, n_sq + 1) / (2.0 * j + 1.0);
+  w.ntr = nterms;
+  for (int j = 0; j < nterms; ++j) w.w_tr[j] = std::ldexp(1.0, n_sq + 1) / (2.0 * j + 1.0);
   w.cst = N * std::log(2.0);
   entropy_combine_kernel<<<1, 32, 0, s>>>(w, ld, tr, out);
   note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_entropy_f64(cudaStream_t s, MatSet& m, int N, double beta, int n_sq, double mu, double dmu,
+                               const double* D, const double* H, double* work, double* out) {
+  (void)beta;
+  (void)mu;
+  (void)dmu;
+  (void)H;
+  const size_t count = (size_t)m.np * m.np;
+  auto load_Y = [&](int k, double* dst) {
+    return cudaMemcpyAsync(dst, m.Y[k], sizeof(double) * count, cudaMemcpyDeviceToDevice, s);
+  };
+  return entropy_fp64(s, N, m.np, m.n, n_sq, m.T[0], load_Y, m.G, m.S, m.Q, m.Yw, m.A1, m.Mt, 6, D, work, out);
 }
 
 }  // namespace xl

@@ -170,6 +170,11 @@ __global__ void __launch_bounds__(192, 1)
     tm = first + r % gm;
     tn = r / gm;
   }
+  // a tile outside the matrix (a bad tile list) is reported, never stored
+  if (tm < 0 || tm >= a.K / BM || tn < 0 || tn >= a.tiles_n) {
+    if (threadIdx.x == 0 && a.err) atomicExch(a.err, 4);
+    return;
+  }
 
   if (warp == 0 && lane == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -475,23 +480,23 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
     nblocks = (n / BM) * (n / bn);
   }
   if (wide) {
-    static bool attr = false;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
     const int sb = smem_bytes<256>();
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    std::call_once(once, [&] {
+      attr = cudaFuncSetAttribute(gemm_tc_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+    });
+    if (attr != cudaSuccess) return attr;
     gemm_tc_kernel<256><<<nblocks, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, args);
     note_launch();
   } else {
-    static bool attr = false;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
     const int sb = smem_bytes<128>();
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    std::call_once(once, [&] {
+      attr = cudaFuncSetAttribute(gemm_tc_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+    });
+    if (attr != cudaSuccess) return attr;
     gemm_tc_kernel<128><<<nblocks, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, args);
     note_launch();
   }

@@ -274,9 +274,16 @@ __global__ void gershgorin_rows_kernel(int n, int np, const double* __restrict__
 __global__ void minmax_kernel(int n, const double* __restrict__ lohi, double* __restrict__ out) {
   __shared__ double sl[32], sh[32];
   double lo = 1e300, hi = -1e300;
+  bool bad = false;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    bad |= !isfinite(lohi[i]) || !isfinite(lohi[n + i]);
     lo = fmin(lo, lohi[i]);
     hi = fmax(hi, lohi[n + i]);
+  }
+  // fmin/fmax drop NaN: a non-finite row poisons both bounds so that the host sees it
+  if (__syncthreads_or(bad)) {
+    if (threadIdx.x == 0) out[0] = out[1] = nan("");
+    return;
   }
   lo = warp_min(lo);
   hi = warp_max(hi);

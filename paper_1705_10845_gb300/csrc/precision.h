@@ -6,6 +6,7 @@
 #pragma once
 #include <cstdio>
 #include <cstdlib>
+#include <functional>
 #include <vector>
 
 #include "internal.h"
@@ -36,10 +37,13 @@ struct MatSet {
   // split engines
   std::vector<SplitMat> sT, sY;
   SplitMat sS, sQ, sYw, sG, sA1, sMt, sT1a, sT1b, sTmu;
-  void* tc_plan = nullptr;   // tensor-map cache of the tensor-core engine
+  void* tc_plan = nullptr;   // device scalars (scales, max |x|) of the split engine
+  double t0max = 0.0;        // spectral bound |T_0| of the last expansion
+  // FP64 work matrices of the split engine's entropy (allocated on first use)
+  double* e64[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
-cudaError_t alloc_matset(MatSet& m, int prec, int np, int n);
+cudaError_t alloc_matset(MatSet& m, int prec, int np, int n, cudaStream_t s);
 void free_matset(MatSet& m);
 
 class Engine {
@@ -111,6 +115,9 @@ class Engine {
   virtual cudaError_t chain(cudaStream_t s, MatSet& m, const double* dvec, int N, bool full_last,
                             double* out_diag, double* stats) = 0;
   // out[0] = sum_{i<N} (T_n)_ii
+  // Device flag that the tensor-core product sets when a bounded wait gives up or a
+  // tile falls outside the matrix (null: this engine has none).
+  virtual const int* device_error() const { return nullptr; }
   virtual cudaError_t trace_tn(cudaStream_t s, MatSet& m, int N, double* out) = 0;
   // ddiag = 1 + diag(T_n) + dmu dmu_diag (= 2 D_aa);  D = (I + T_n)/2 + dmu Tmu / 2 (FP64)
   virtual cudaError_t density_out(cudaStream_t s, MatSet& m, int N, double dmu, const double* dmu_diag,
@@ -124,13 +131,17 @@ Engine* make_engine(int prec);
 
 // split-precision engines (engine_split.cu)
 Engine* make_split_engine(int prec);
-cudaError_t alloc_matset_split(MatSet& m);
+cudaError_t alloc_matset_split(MatSet& m, cudaStream_t s);
 void free_matset_split(MatSet& m);
 
 // tensor-core product self-test (engine_split.cu)
 int selftest_gemm(int n, int prec, int sym, double* result);
 
 // FP64 eigenvalue-free entropy (entropy.cu)
+cudaError_t entropy_fp64(cudaStream_t s, int N, int np, int n, int n_sq, const double* T0,
+                         const std::function<cudaError_t(int, double*)>& load_Y, double* G, double* S, double* Q,
+                         double* Yw, double* A1, double* Mt, int nterms, const double* D, double* work,
+                         double* out);
 cudaError_t launch_entropy_f64(cudaStream_t s, MatSet& m, int N, double beta, int n_sq, double mu, double dmu,
                                const double* D, const double* H, double* work, double* out);
 

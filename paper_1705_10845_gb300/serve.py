@@ -1,0 +1,269 @@
+"""Batched and served XL-BOMD on one GPU over the C ABI.
+
+Each job is one trajectory with its own context (device state and CUDA
+stream).  Worker threads each own a slice of the active jobs and advance them
+one MD step at a time; every C call releases the GIL, so the kernels of
+different trajectories overlap on the GPU (continuous batching at the level
+of whole steps).  A job is admitted when its estimated device memory fits the
+budget; a finished job frees its memory and the next queued job is admitted.
+
+``python -m paper_1705_10845_gb300.serve --mode batch`` advances many
+trajectories of uneven size together; ``--mode serve`` feeds Poisson arrivals
+through the admission loop and reports per-step latency percentiles and the
+aggregate step rate.  Both print one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import heapq
+import json
+import math
+import os
+import sys
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+KB_EV = 8.617333262e-5
+
+
+def squarings_for(Te: float, width_ev: float = 40.0) -> int:
+    """n = max(10, ceil(log2(beta W / 0.1)) - 1) squarings for a spectral width W."""
+    beta = 1.0 / (KB_EV * Te)
+    return max(10, int(math.ceil(math.log2(beta * width_ev / 0.1))) - 1)
+
+
+def bytes_estimate(natoms: int, n_sq: int, prec: str = "fp16x3") -> int:
+    """Device memory of one context (expansion matrices dominate)."""
+    np_ = (4 * natoms + 127) // 128 * 128
+    e = np_ * np_
+    if prec == "fp64":
+        per = 8 * ((n_sq + 1) + n_sq + 9 + 3)
+    else:
+        per = 12 * (n_sq + 1) + 8 * n_sq + 8 * 5 + 12 * 4 + 8 * 3
+    return int(per * e * 1.05) + (64 << 20)
+
+
+@dataclass(eq=False)          # jobs compare by identity (list removal, membership)
+class Job:
+    arrival: float
+    jid: int
+    natoms: int
+    Te: float
+    steps: int
+    seed: int
+    prec: str = "fp16x3"
+    # runtime
+    ctx: object = None
+    stream: object = None
+    done_steps: int = 0
+    lat: list = field(default_factory=list)
+    admitted: float = 0.0
+    finished: float = 0.0
+    error: str = ""
+    mem: int = 0
+    result: dict = field(default_factory=dict)
+
+
+def make_context(X, job: Job, stream_ptr: int):
+    import synth
+    s = synth.make_system(job.natoms, job.seed)
+    n_sq = squarings_for(job.Te)
+    p = X.default_params(Te=job.Te, n_sq=n_sq, rank_m=2, dt=0.25, mix_alpha=0.06, kernel_c=1 - 1 / 0.06,
+                         prec=job.prec, scf_mode=1, kernel_auto=1, scf_tol=1e-5, scf_max_iter=200,
+                         mu_tol=1e-3)
+    ctx = X.Context(p, [dict(natoms=s.natoms, L=s.L, R=s.R, V=s.V, Z=s.Z, mass=s.mass)], stream=stream_ptr)
+    ctx.scf(0)
+    return ctx
+
+
+class Scheduler:
+    """Admission by device memory plus a worker pool that steps the admitted jobs."""
+
+    def __init__(self, X, budget_bytes: int, workers: int, make_ctx=make_context, clock=time.perf_counter,
+                 keep_results: bool = False):
+        self.X = X
+        self.keep_results = keep_results
+        self.budget = budget_bytes
+        self.used = 0
+        self.workers = workers
+        self.make_ctx = make_ctx
+        self.clock = clock
+        self.lock = threading.Lock()
+        self.pending: list[tuple] = []        # heap of (arrival, jid, job)
+        self.active: list[list[Job]] = [[] for _ in range(workers)]
+        self.finished: list[Job] = []
+        self.rejected: list[Job] = []
+
+    def submit(self, job: Job):
+        job.mem = bytes_estimate(job.natoms, squarings_for(job.Te), job.prec)
+        with self.lock:
+            if job.mem > self.budget:
+                job.error = "larger than the memory budget"
+                self.rejected.append(job)
+                return
+            heapq.heappush(self.pending, (job.arrival, job.jid, job))
+
+    def _admit(self, w: int, now: float):
+        """Admit arrived jobs that fit, into worker w's slice (least loaded first)."""
+        with self.lock:
+            if not self.pending or self.pending[0][0] > now:
+                return None
+            job = self.pending[0][2]
+            if self.used + job.mem > self.budget:
+                return None
+            heapq.heappop(self.pending)
+            self.used += job.mem
+            self.peak_used = max(getattr(self, "peak_used", 0), self.used)
+        return job
+
+    def _release(self, job: Job):
+        with self.lock:
+            self.used -= job.mem
+            self.finished.append(job)
+
+    def run(self, until: float | None = None, stream_factory=None):
+        """Run until every submitted job finished (or the clock passes `until`)."""
+        t0 = self.clock()
+        stop = threading.Event()
+
+        def worker(w: int):
+            stream = stream_factory() if stream_factory else None
+            mine = self.active[w]
+            while not stop.is_set():
+                now = self.clock() - t0
+                if until is not None and now > until:
+                    break
+                # only the least-loaded workers admit, so that the jobs spread out
+                job = None
+                if len(mine) <= min(len(a) for a in self.active):
+                    job = self._admit(w, now)
+                if job is not None:
+                    try:
+                        job.stream = stream
+                        job.ctx = self.make_ctx(self.X, job, stream.cuda_stream if stream is not None else 0)
+                        job.admitted = self.clock() - t0
+                        mine.append(job)
+                    except Exception as e:   # admission failure: report and free the reservation
+                        job.error = f"job {job.jid} ({job.natoms} atoms, Te {job.Te:.0f} K): {e}"
+                        self._release(job)
+                    continue
+                if not mine:
+                    with self.lock:
+                        empty = not self.pending
+                    if empty and all(not a for a in self.active):
+                        break
+                    time.sleep(0.001)
+                    continue
+                for job in list(mine):
+                    t = self.clock()
+                    try:
+                        job.ctx.step(1)
+                    except Exception as e:
+                        job.error = f"job {job.jid} ({job.natoms} atoms, Te {job.Te:.0f} K) step {job.done_steps}: {e}"
+                    job.lat.append(self.clock() - t)
+                    job.done_steps += 1
+                    if job.error or job.done_steps >= job.steps:
+                        job.finished = self.clock() - t0
+                        if self.keep_results and not job.error:
+                            job.result = {"q": job.ctx.get(0, self.X.Q), "R": job.ctx.get(0, self.X.R)}
+                        try:
+                            job.ctx.close()
+                        except Exception:
+                            pass
+                        job.ctx = None
+                        mine.remove(job)
+                        self._release(job)
+
+        threads = [threading.Thread(target=worker, args=(w,), daemon=True) for w in range(self.workers)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        stop.set()
+        wall = self.clock() - t0
+        for a in self.active:          # jobs still running when the window closed
+            for job in a:
+                if job.ctx is not None:
+                    try:
+                        job.ctx.close()
+                    except Exception:
+                        pass
+                    job.ctx = None
+        return wall
+
+
+def summarize(sched: Scheduler, wall: float):
+    lat = [x for j in sched.finished for x in j.lat]
+    steps = sum(j.done_steps for j in sched.finished) + sum(j.done_steps for a in sched.active for j in a)
+    out = {"steps_per_s": steps / wall if wall > 0 else None, "total_steps": steps, "wall_s": wall,
+           "jobs_finished": sum(1 for j in sched.finished if not j.error and j.done_steps >= j.steps),
+           "jobs_failed": [j.error for j in sched.finished if j.error][:5],
+           "jobs_pending": len(sched.pending), "jobs_rejected": len(sched.rejected)}
+    if lat:
+        a = np.array(lat) * 1000.0
+        out.update({"step_latency_ms_p50": float(np.percentile(a, 50)),
+                    "step_latency_ms_p99": float(np.percentile(a, 99))})
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--mode", choices=["batch", "serve"], default="batch")
+    ap.add_argument("--jobs", type=int, default=256)
+    ap.add_argument("--min-atoms", type=int, default=32)
+    ap.add_argument("--max-atoms", type=int, default=512)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--workers", type=int, default=16)
+    ap.add_argument("--rate", type=float, default=20.0, help="serve: Poisson arrivals per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve: arrival window (s)")
+    ap.add_argument("--budget-gb", type=float, default=None)
+    ap.add_argument("--prec", default="fp16x3")
+    ap.add_argument("--seed", type=int, default=1705)
+    a = ap.parse_args(argv)
+
+    sys.path.insert(0, ROOT)
+    import torch
+
+    import paper_1705_10845_gb300 as X
+    X.build.build()
+    X.load()
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(a.budget_gb * 2**30) if a.budget_gb else int(free * 0.85)
+    rng = np.random.default_rng(a.seed)
+    sched = Scheduler(X, budget, a.workers)
+    t = 0.0
+    for i in range(a.jobs):
+        nat = int(round(math.exp(rng.uniform(math.log(a.min_atoms), math.log(a.max_atoms)))))
+        if a.mode == "serve":
+            t += rng.exponential(1.0 / a.rate)
+            if t > a.duration:
+                break
+            Te = float(rng.uniform(300.0, 3000.0))
+        else:
+            Te = 1000.0
+        sched.submit(Job(arrival=t if a.mode == "serve" else 0.0, jid=i, natoms=nat, Te=Te, steps=a.steps,
+                         seed=a.seed + i, prec=a.prec))
+    l0 = X.binding.launch_count()
+    wall = sched.run(until=(a.duration + 60.0) if a.mode == "serve" else None,
+                     stream_factory=lambda: torch.cuda.Stream())
+    sync_error = ""
+    try:
+        torch.cuda.synchronize()
+    except Exception as e:           # report the jobs' own errors with it
+        sync_error = str(e).splitlines()[0]
+    res = summarize(sched, wall)
+    if sync_error:
+        res["sync_error"] = sync_error
+    res.update({"mode": a.mode, "workers": a.workers, "prec": a.prec, "budget_gb": budget / 2**30,
+                "atoms_range": [a.min_atoms, a.max_atoms], "steps_per_job": a.steps,
+                "gpu_launches": X.binding.launch_count() - l0})
+    print(json.dumps(res), flush=True)
+    return 1 if sync_error else 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

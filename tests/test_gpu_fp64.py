@@ -151,7 +151,7 @@ def test_trajectory_matches_oracle(X):
         ctx.density(0)
         ctx.kernel_update(0)
         assert np.max(np.abs(ctx.get(0, X.KR) - st.Kr)) < 1e-9
-        for k in range(20):
+        for k in range(50):
             st, ev = O.md_step(st, s.L, s.Z, s.mass, m, xl)
             ctx.step(1)
             ctx.energy(0)
@@ -162,6 +162,24 @@ def test_trajectory_matches_oracle(X):
             assert np.max(np.abs(ctx.get(0, X.N) - st.nhist[0])) < 1e-9, k
             E = ctx.get(0, X.ENERGY)
             assert E[0] == pytest.approx(ev.Omega, rel=1e-8), k
+
+
+@pytest.mark.parametrize("prec,tol_q", [("fp64", 1e-9), ("fp16x3", 1e-5), ("bf16x3", 1e-4)])
+def test_mu_search_through_flat_occupation(X, prec, tol_q):
+    # 33 atoms at n = 0, Te = 1000 K, 12 squarings: from the first guess (the
+    # middle of the Gershgorin interval) the safeguarded Newton search bisects
+    # to a mu above every level, where Tr D = N and dTr D/dmu = 0; it must
+    # keep bisecting to Tr D = N_occ rather than accept the zero step
+    s = synth.make_system(33, 1715)
+    p = model_params(X, Te=1000.0, n_sq=12, prec=prec, mu_tol=1e-9 if prec == "fp64" else 1e-3)
+    ref = O.evaluate(s.R, s.L, s.Z, np.zeros(s.natoms), O.Model(Te=1000.0, n_sq=12), None, with_kernel=False)
+    with X.Context(p, [sysdict(s)]) as ctx:
+        ctx.build_H(0)
+        ctx.density(0)
+        q = ctx.get(0, X.Q)
+    print(prec, "dq", np.abs(q - ref.q).max())
+    assert abs(q.sum() - ref.q.sum()) < s.natoms * tol_q
+    assert np.max(np.abs(q - ref.q)) < tol_q
 
 
 def test_single_atom_edge_case(X):

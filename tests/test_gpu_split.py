@@ -57,7 +57,9 @@ def test_split_density_against_oracle(X, prec, case):
         ctx.build_H(0)
         ctx.density(0)
         ctx.kernel_update(0)
+        ctx.energy(0)
         q, F, Kr = ctx.get(0, X.Q), ctx.get(0, X.F), ctx.get(0, X.KR)
+        E = ctx.get(0, X.ENERGY)
     tol_q = 1e-5 if prec == "fp16x3" else 1e-4
     tol_f = 1e-4 if prec == "fp16x3" else 1e-3
     print(prec, case, "dq", np.abs(q - ref.q).max(), "dF", np.abs(F - ref.F).max(), "dKr",
@@ -65,6 +67,10 @@ def test_split_density_against_oracle(X, prec, case):
     assert np.max(np.abs(q - ref.q)) < tol_q
     assert np.max(np.abs(F - ref.F)) < tol_f
     assert np.max(np.abs(Kr - ref.Kr)) < 100 * tol_q
+    # energy monitor: Omega and its parts against the oracle (eV)
+    print(prec, case, "dOmega", E[0] - ref.Omega, "dS", E[3] - ref.parts["entropy"])
+    assert abs(E[3] - ref.parts["entropy"]) < 1e-3
+    assert abs(E[0] - ref.Omega) < (2e-3 if prec == "fp16x3" else 2e-2)
 
 
 def test_full_size_charges_against_oracle(X):

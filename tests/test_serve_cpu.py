@@ -1,0 +1,113 @@
+"""Host logic of the batch/serve scheduler with a fake context (no GPU)."""
+import threading
+import time
+
+import pytest
+
+from paper_1705_10845_gb300 import serve
+
+
+class FakeCtx:
+    live = 0
+    lock = threading.Lock()
+
+    def __init__(self, job):
+        self.job = job
+        with FakeCtx.lock:
+            FakeCtx.live += 1
+
+    def step(self, n):
+        time.sleep(0.0005)
+
+    def get(self, sys, what):
+        return [self.job.jid]
+
+    def close(self):
+        with FakeCtx.lock:
+            FakeCtx.live -= 1
+
+
+class FakeX:
+    Q, R = 0, 4
+
+
+def fake_make(X, job, stream):
+    if job.natoms == 13:
+        raise RuntimeError("admission failed")
+    return FakeCtx(job)
+
+
+def test_squarings_rule():
+    assert serve.squarings_for(3000.0) == 10
+    assert serve.squarings_for(300.0) >= 13
+
+
+def test_memory_estimate_grows_with_size():
+    assert serve.bytes_estimate(512, 10) > 10 * serve.bytes_estimate(64, 10)
+
+
+def test_all_jobs_run_within_the_memory_budget():
+    jobs = [serve.Job(arrival=0.0, jid=i, natoms=32 + 8 * (i % 5), Te=1000.0, steps=5, seed=i) for i in range(20)]
+    budget = 3 * max(serve.bytes_estimate(j.natoms, serve.squarings_for(j.Te)) for j in jobs)
+    sch = serve.Scheduler(FakeX(), budget, workers=4, make_ctx=fake_make, keep_results=True)
+    for j in jobs:
+        sch.submit(j)
+    wall = sch.run()
+    assert wall > 0
+    assert len(sch.finished) == 20 and all(j.done_steps == 5 for j in sch.finished)
+    assert sch.peak_used <= budget
+    assert sch.used == 0 and FakeCtx.live == 0
+    assert sorted(j.result["q"][0] for j in sch.finished) == list(range(20))
+    res = serve.summarize(sch, wall)
+    assert res["total_steps"] == 100 and res["step_latency_ms_p99"] >= res["step_latency_ms_p50"]
+
+
+def test_too_large_jobs_are_rejected_and_failures_reported():
+    sch = serve.Scheduler(FakeX(), serve.bytes_estimate(64, 10), workers=2, make_ctx=fake_make)
+    sch.submit(serve.Job(arrival=0.0, jid=0, natoms=4096, Te=1000.0, steps=3, seed=0))
+    sch.submit(serve.Job(arrival=0.0, jid=1, natoms=13, Te=1000.0, steps=3, seed=1))
+    sch.submit(serve.Job(arrival=0.0, jid=2, natoms=32, Te=1000.0, steps=3, seed=2))
+    sch.run()
+    assert len(sch.rejected) == 1 and sch.rejected[0].jid == 0
+    errs = {j.jid: j.error for j in sch.finished}
+    assert errs[1].endswith(": admission failed") and errs[2] == ""
+
+
+def test_arrivals_are_admitted_in_time_order():
+    jobs = [serve.Job(arrival=0.02 * (5 - i), jid=i, natoms=32, Te=1000.0, steps=1, seed=i) for i in range(5)]
+    sch = serve.Scheduler(FakeX(), 10**12, workers=1, make_ctx=fake_make)
+    for j in jobs:
+        sch.submit(j)
+    sch.run()
+    order = [j.jid for j in sorted(sch.finished, key=lambda j: j.admitted)]
+    assert order == [4, 3, 2, 1, 0]
+
+
+class CountingCtx(FakeCtx):
+    """Counts steps per job; job 3 fails at its second step."""
+    steps = {}
+
+    def step(self, n):
+        if self.job.jid in CountingCtx.steps and self.job.ctx is not self:
+            raise AssertionError("stepped through another job's context")
+        CountingCtx.steps[self.job.jid] = CountingCtx.steps.get(self.job.jid, 0) + n
+        if self.job.jid == 3 and CountingCtx.steps[3] == 2:
+            raise RuntimeError("step failed")
+
+
+def test_equal_arrivals_each_job_steps_exactly_its_own_count():
+    # jobs with the same arrival time are distinct: finishing or failing one
+    # must not remove or step another.  One worker admits all twelve before
+    # the first step, so later jobs in its list finish before earlier ones.
+    CountingCtx.steps = {}
+    jobs = [serve.Job(arrival=0.0, jid=i, natoms=32, Te=1000.0, steps=3 + (i % 4), seed=i) for i in range(12)]
+    sch = serve.Scheduler(FakeX(), 10**12, workers=1, make_ctx=lambda X, j, s: CountingCtx(j))
+    for j in jobs:
+        sch.submit(j)
+    sch.run()
+    assert len(sch.finished) == 12 and FakeCtx.live == 0
+    for j in sch.finished:
+        if j.jid == 3:
+            assert "step failed" in j.error and j.done_steps == 2
+        else:
+            assert j.error == "" and j.done_steps == j.steps == CountingCtx.steps[j.jid]
