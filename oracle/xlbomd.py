@@ -91,6 +91,8 @@ class XLParams:
     c: tuple = (-6.0, 14.0, -8.0, -3.0, 4.0, -1.0)
     rank_m: int = 2
     kernel_c: float = 0.0                   # J_0 = c I
+    kernel_mode: str = "rank"               # "rank": rank-m every step; "exact": K = (J - I)^-1
+    kernel_every: int = 0                   # exact: recompute every this many steps (0: kept from t0)
     mix_alpha: float = 0.5                  # linear mixing at t0
     scf_tol: float = 1e-10
     scf_max_iter: int = 1000
@@ -546,6 +548,26 @@ def kernel_sherman_morrison_dense(c, V, W):
     return K, J
 
 
+def jacobian(dens: Density, gamma, P=None, gmu=None):
+    """J = dq/dn (N_at x N_at): column I is the response to the unit direction e_I, i.e. the
+    N_at orthonormal probes with which the sequence of Eq. K_up ends at the exact kernel."""
+    if P is None:
+        P, gmu = divided_differences(dens)
+    nat = gamma.shape[0]
+    J = np.zeros((nat, nat))
+    for I in range(nat):
+        e = np.zeros(nat)
+        e[I] = 1.0
+        J[:, I] = response(dens, gamma, e, P, gmu)
+    return J
+
+
+def kernel_exact(dens: Density, gamma):
+    """The exact kernel K = (J - I)^-1 of Eq. KK, J = dq/dn."""
+    J = jacobian(dens, gamma)
+    return np.linalg.inv(J - np.eye(J.shape[0]))
+
+
 # --------------------------------------------------------------------------
 # Energy and forces (Section IV.B-IV.C, Eq. EqMotFT)
 # --------------------------------------------------------------------------
@@ -706,6 +728,7 @@ class MDState:
     F: np.ndarray
     Kr: np.ndarray
     step: int = 0
+    K: np.ndarray | None = None     # exact kernel held between recomputations
 
 
 def kinetic_energy(V, mass):
@@ -727,9 +750,14 @@ def md_init(sys_R, sys_V, L, Z, mass, model: Model, xl: XLParams, n0=None):
     R = wrap(np.asarray(sys_R, dtype=float), L)
     if n0 is None:
         n0, _ = scf(R, L, Z, model, xl.mix_alpha, tol=xl.scf_tol, max_iter=xl.scf_max_iter)
-    ev = evaluate(R, L, Z, n0, model, xl)
+    exact = xl.kernel_mode == "exact"
+    ev = evaluate(R, L, Z, n0, model, xl, with_kernel=not exact)
+    K = None
+    if exact:
+        K = kernel_exact(ev.dens, ev.gamma)
+        ev.Kr = K @ ev.r
     nh = np.tile(np.asarray(n0, dtype=float), (xl.kmax + 1, 1))
-    st = MDState(R=R, V=np.array(sys_V, dtype=float), nhist=nh, F=ev.F, Kr=ev.Kr)
+    st = MDState(R=R, V=np.array(sys_V, dtype=float), nhist=nh, F=ev.F, Kr=ev.Kr, K=K)
     return st, ev
 
 
@@ -741,7 +769,15 @@ def md_step(st: MDState, L, Z, mass, model: Model, xl: XLParams):
     Vh = st.V + 0.5 * dt * st.F / mass * ACC
     R = wrap(st.R + dt * Vh, L)
     n_new = n_update(st.nhist, st.Kr, xl)
-    ev = evaluate(R, L, Z, n_new, model, xl)
+    step = st.step + 1
+    exact = xl.kernel_mode == "exact"
+    ev = evaluate(R, L, Z, n_new, model, xl, with_kernel=not exact)
+    K = st.K
+    if exact:
+        # the full kernel of the t0 state, recomputed every kernel_every steps (Section VI.A, Figs. 3, 5)
+        if xl.kernel_every > 0 and step % xl.kernel_every == 0:
+            K = kernel_exact(ev.dens, ev.gamma)
+        ev.Kr = K @ ev.r
     V = Vh + 0.5 * dt * ev.F / mass * ACC
     nh = np.vstack([n_new[None, :], st.nhist[:-1]])
-    return MDState(R=R, V=V, nhist=nh, F=ev.F, Kr=ev.Kr, step=st.step + 1), ev
+    return MDState(R=R, V=V, nhist=nh, F=ev.F, Kr=ev.Kr, step=step, K=K), ev

@@ -116,3 +116,25 @@ def test_energy_is_conserved_over_a_short_run():
     # no systematic drift: slope of a linear fit over the run is tiny
     slope = np.polyfit(np.arange(len(E)), E, 1)[0]
     assert abs(slope) < 1e-6
+
+
+def test_full_kernel_keeps_the_residual_below_the_scaled_delta_kernel():
+    # Section VI.A, Figs. 3-4: the full kernel computed at t0 and kept constant
+    # keeps n closer to the ground state than K = K_0 = I/(c - 1) alone
+    s = synth.make_system(24, 1705, L=7.0)
+    base = dict(kernel_c=1 - 1 / 0.06, mix_alpha=0.06)
+    rms = {}
+    for name, xl in (("delta", O.XLParams(rank_m=0, **base)),
+                     ("full", O.XLParams(kernel_mode="exact", kernel_every=0, **base)),
+                     ("full10", O.XLParams(kernel_mode="exact", kernel_every=10, **base))):
+        st, ev = O.md_init(s.R, s.V, s.L, s.Z, s.mass, M, xl)
+        E0 = O.kinetic_energy(st.V, s.mass) + ev.Omega
+        res, dE = [], []
+        for _ in range(40):
+            st, ev = O.md_step(st, s.L, s.Z, s.mass, M, xl)
+            res.append(np.sqrt(np.mean(ev.r ** 2)))
+            dE.append(O.kinetic_energy(st.V, s.mass) + ev.Omega - E0)
+        rms[name] = np.mean(res)
+        assert np.max(np.abs(dE)) < 1e-3, name
+    assert rms["full"] < 0.5 * rms["delta"]
+    assert rms["full10"] <= 1.2 * rms["full"]

@@ -190,3 +190,22 @@ def test_mixing_scan_picks_converging_alpha():
     d = O.density(O.hamiltonian(O.build_H0(s.R, s.L, M), O.build_gamma(s.R, s.L, M), n),
                   M.beta, M.n_sq, 16)
     assert np.max(np.abs(O.mulliken(d.D, s.Z) - n)) < 1e-10
+
+
+def test_exact_kernel_is_inverse_of_finite_difference_jacobian(tiny):
+    # Eq. KK from the unit-probe Jacobian, against central differences of q[n]
+    s, H0, gam, n = tiny
+    nat, h = 8, 1e-5
+    Jfd = np.zeros((nat, nat))
+    for j in range(nat):
+        e = np.zeros(nat)
+        e[j] = 1.0
+        Jfd[:, j] = (O.charges_at(s.R, s.L, s.Z, n + h * e, M)
+                     - O.charges_at(s.R, s.L, s.Z, n - h * e, M)) / (2 * h)
+    d = O.density(O.hamiltonian(H0, gam, n), M.beta, M.n_sq, 16)
+    assert np.allclose(O.jacobian(d, gam), Jfd, atol=1e-7)
+    K = O.kernel_exact(d, gam)
+    Kfd = np.linalg.inv(Jfd - np.eye(nat))
+    assert np.allclose(K, Kfd, atol=1e-6 * np.abs(Kfd).max())
+    # columns of J sum to zero (charge is conserved), so K maps sum-free residuals to sum-free steps
+    assert np.allclose(O.jacobian(d, gam).sum(axis=0), 0.0, atol=1e-12)
