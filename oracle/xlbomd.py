@@ -695,6 +695,27 @@ def scf(R, L, Z, model: Model, mix_alpha, tol=1e-10, max_iter=1000, n0=None):
     raise RuntimeError("SCF did not converge")
 
 
+def scf_kernel(R, L, Z, model: Model, rank_m, kernel_c, tol=1e-10, max_iter=200, n0=None):
+    """Kernel SCF of Eq. SCF_K: n_{j+1} = n_j - K_j (q[n_j] - n_j), with K_j the rank-m kernel
+    (Section V.F: v_1 from K_0 = (c - 1)^-1 I, later probes orthonormalised) built at n_j.
+    Returns (n, iterations) for the last n, whose residual is below tol."""
+    H0 = build_H0(R, L, model)
+    gam = build_gamma(R, L, model)
+    n_occ = 0.5 * np.sum(Z)
+    n = np.zeros(len(Z)) if n0 is None else np.array(n0, dtype=float)
+    for it in range(1, max_iter + 1):
+        dens = density(hamiltonian(H0, gam, n), model.beta, model.n_sq, n_occ)
+        res = mulliken(dens.D, Z) - n
+        if np.max(np.abs(res)) < tol:
+            return n, it
+        if not np.all(np.isfinite(res)) or np.max(np.abs(res)) > 1e3:
+            raise RuntimeError("SCF diverged")
+        P, gmu = divided_differences(dens)
+        Kr, _, _ = kernel_rank_m(res, rank_m, kernel_c, lambda v: response(dens, gam, v, P, gmu))
+        n = n - Kr
+    raise RuntimeError("SCF did not converge")
+
+
 def choose_mix_alpha(R, L, Z, model: Model, candidates=None, tol=1e-10, max_iter=400):
     """Linear-mixing coefficient with the fewest SCF iterations (Section VI: the
     constants are tuned once for the fastest initial ground state, to within 0.1).

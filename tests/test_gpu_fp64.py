@@ -138,6 +138,19 @@ def test_scf_ground_state(X):
     assert np.allclose(hist, hist[0][None, :])
 
 
+@pytest.mark.parametrize("rank", [2, 4])
+def test_kernel_scf_ground_state(X, rank):
+    # Eq. SCF_K with the rank-m kernel and a fixed c, against the oracle's kernel SCF
+    s = synth.make_system(24, 1705, L=7.0)
+    p = model_params(X, scf_mode=1, rank_m=rank)
+    m = oracle_model(p)
+    n_ref, it = O.scf_kernel(s.R, s.L, s.Z, m, rank, p.kernel_c, tol=p.scf_tol)
+    with X.Context(p, [sysdict(s)]) as ctx:
+        ctx.scf(0)
+        n = ctx.get(0, X.N)
+    assert np.max(np.abs(n - n_ref)) < 1e-9, it
+
+
 def test_trajectory_matches_oracle(X):
     s = synth.make_system(24, 1705, L=7.0)
     p = model_params(X)
@@ -210,3 +223,64 @@ def test_argument_errors_are_reported(X):
             ctx.build_H(0)           # sticky until cleared
         ctx._lib.xlbomd_clear_error(ctx.h)
         ctx.build_H(0)
+
+
+@pytest.mark.parametrize("name,make", CASES[:2])
+def test_exact_kernel_matches_oracle(X, name, make):
+    # Eq. KK: K = (J - I)^-1 with J from the natoms unit-direction responses
+    s = make()
+    p = model_params(X, kernel_mode=1)
+    m = oracle_model(p)
+    n = random_n(s.natoms, 6)
+    ev = O.evaluate(s.R, s.L, s.Z, n, m, None, with_kernel=False, with_forces=False)
+    Kref = O.kernel_exact(ev.dens, ev.gamma)
+    with X.Context(p, [sysdict(s)]) as ctx:
+        ctx.set(0, X.N, n)
+        ctx.set(0, X.MU, [ev.dens.mu])
+        ctx.build_H(0)
+        ctx.density(0)
+        ctx.kernel_update(0)           # computes the held kernel, then K r
+        K = ctx.get(0, X.KMAT)
+        Kr = ctx.get(0, X.KR)
+        assert ctx.get(0, X.STATS)[2] == s.natoms
+    assert np.max(np.abs(K - Kref)) < 1e-9 * max(1.0, np.abs(Kref).max())
+    assert np.max(np.abs(Kr - Kref @ ev.r)) < 1e-10
+
+
+@pytest.mark.parametrize("variant", ["exact_every5", "delta", "kmax6", "kmax7"])
+def test_kernel_and_dissipation_variants_follow_oracle(X, variant):
+    # the exact kernel held and recomputed every 5 steps (Section VI.A), K = K_0
+    # only (rank 0), and the K_max = 6, 7 rows of Table I (the library's table
+    # against the oracle's, typed independently)
+    s = synth.make_system(24, 1705, L=7.0)
+    kw, xlkw = {}, {}
+    if variant == "exact_every5":
+        kw, xlkw = dict(kernel_mode=1, kernel_every=5), dict(kernel_mode="exact", kernel_every=5)
+    elif variant == "delta":
+        kw, xlkw = dict(rank_m=0), dict(rank_m=0)
+    else:
+        kmax = int(variant[-1])
+        kappa, alpha, c = O.TABLE_I[kmax]
+        kw, xlkw = dict(kmax=kmax), dict(kappa=kappa, alpha=alpha, c=tuple(float(x) for x in c))
+    p = model_params(X, **kw)
+    m = oracle_model(p)
+    base = dict(rank_m=p.rank_m, kernel_c=p.kernel_c, mix_alpha=ALPHA_MIX)
+    base.update(xlkw)
+    xl = O.XLParams(**base)
+    assert p.kmax == xl.kmax and abs(p.kappa - xl.kappa) < 1e-15 and abs(p.alpha - xl.alpha) < 1e-15
+    assert all(abs(p.c[k] - xl.c[k]) < 1e-15 for k in range(xl.kmax + 1))
+    st, ev = O.md_init(s.R, s.V, s.L, s.Z, s.mass, m, xl)
+    with X.Context(p, [sysdict(s)]) as ctx:
+        ctx.set(0, X.N, st.nhist[0])
+        ctx.set(0, X.MU, [ev.dens.mu])
+        ctx.build_H(0)
+        ctx.density(0)
+        ctx.kernel_update(0)
+        assert np.max(np.abs(ctx.get(0, X.KR) - st.Kr)) < 1e-9
+        for k in range(12):
+            st, ev = O.md_step(st, s.L, s.Z, s.mass, m, xl)
+            ctx.step(1)
+            assert np.max(np.abs(O.min_image(ctx.get(0, X.R) - st.R, s.L))) < 1e-9, k
+            assert np.max(np.abs(ctx.get(0, X.Q) - ev.q)) < 1e-9, k
+            assert np.max(np.abs(ctx.get(0, X.N) - st.nhist[0])) < 1e-9, k
+            assert np.max(np.abs(ctx.get(0, X.KR) - ev.Kr)) < 1e-9, k

@@ -12,7 +12,7 @@ def run(X, jobs, workers):
     sch = serve.Scheduler(X, 10**12, workers=workers, keep_results=True)
     for j in jobs:
         sch.submit(j)
-    sch.run(stream_factory=lambda: torch.cuda.Stream())
+    sch.run(stream_factory=lambda job: torch.cuda.Stream(priority=serve.stream_priority(job.natoms)))
     torch.cuda.synchronize()
     return {j.jid: j for j in sch.finished}
 

@@ -92,3 +92,25 @@ def test_full_size_charges_against_oracle(X):
     err = np.max(np.abs(q - q_ref))
     print("full size fp16x3 |dq|", err)
     assert err < 1e-5
+
+
+@pytest.mark.parametrize("prec,tol", [("fp16x3", 1e-4), ("bf16x3", 1e-3)])
+def test_split_exact_kernel_against_oracle(X, prec, tol):
+    s = synth.make_system(37, 11)
+    p = X.default_params(mix_alpha=ALPHA_MIX, kernel_c=1 - 1 / ALPHA_MIX, prec=prec, mu_tol=1e-3, kernel_mode=1)
+    m = O.Model(Te=p.Te, n_sq=p.n_sq)
+    rng = np.random.default_rng(8)
+    n = rng.normal(scale=0.02, size=s.natoms)
+    n -= n.mean()
+    ev = O.evaluate(s.R, s.L, s.Z, n, m, None, with_kernel=False, with_forces=False)
+    Kref = O.kernel_exact(ev.dens, ev.gamma)
+    with X.Context(p, [sysdict(s)]) as ctx:
+        ctx.set(0, X.N, n)
+        ctx.set(0, X.MU, [ev.dens.mu])
+        ctx.build_H(0)
+        ctx.density(0)
+        ctx.kernel_exact(0)
+        K = ctx.get(0, X.KMAT)
+    err = np.max(np.abs(K - Kref)) / np.abs(Kref).max()
+    print(prec, "exact kernel rel err", err)
+    assert err < tol

@@ -138,3 +138,22 @@ def test_full_kernel_keeps_the_residual_below_the_scaled_delta_kernel():
         assert np.max(np.abs(dE)) < 1e-3, name
     assert rms["full"] < 0.5 * rms["delta"]
     assert rms["full10"] <= 1.2 * rms["full"]
+
+
+def test_residual_and_energy_fluctuations_scale_as_dt_squared():
+    # Section VI.C, Figs. 9-10: over the same 10 fs, halving dt divides the RMS
+    # residual |q[n] - n| and the total-energy fluctuation by about 4
+    s = synth.make_system(24, 1705, L=7.0)
+    res, fluct = [], []
+    for dt in (0.5, 0.25, 0.125):
+        xl = O.XLParams(dt=dt, rank_m=2, kernel_c=1 - 1 / 0.06, mix_alpha=0.06)
+        st, ev = O.md_init(s.R, s.V, s.L, s.Z, s.mass, M, xl)
+        r, E = [], []
+        for _ in range(int(round(10.0 / dt))):
+            st, ev = O.md_step(st, s.L, s.Z, s.mass, M, xl)
+            r.append(np.sqrt(np.mean(ev.r ** 2)))
+            E.append(O.kinetic_energy(st.V, s.mass) + ev.Omega)
+        res.append(np.mean(r))
+        fluct.append(np.std(E))
+    for a, b in ((res[0], res[1]), (res[1], res[2]), (fluct[0], fluct[1]), (fluct[1], fluct[2])):
+        assert 3.0 < a / b < 5.5, (res, fluct)

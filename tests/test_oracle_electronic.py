@@ -209,3 +209,16 @@ def test_exact_kernel_is_inverse_of_finite_difference_jacobian(tiny):
     assert np.allclose(K, Kfd, atol=1e-6 * np.abs(Kfd).max())
     # columns of J sum to zero (charge is conserved), so K maps sum-free residuals to sum-free steps
     assert np.allclose(O.jacobian(d, gam).sum(axis=0), 0.0, atol=1e-12)
+
+
+def test_kernel_scf_reaches_the_mixing_fixed_point_in_fewer_iterations():
+    # Eq. SCF_K with the rank-2 kernel against linear mixing (Section V.G, Fig. 6)
+    s = synth.make_system(24, 1705, L=7.0)
+    c = 1 - 1 / 0.06
+    n_mix, it_mix = O.scf(s.R, s.L, s.Z, M, 0.06, tol=1e-10)
+    n_k, it_k = O.scf_kernel(s.R, s.L, s.Z, M, 2, c, tol=1e-10)
+    assert np.max(np.abs(n_k - n_mix)) < 1e-9
+    assert it_k * 3 < it_mix, (it_k, it_mix)
+    # a rank-0 kernel is linear mixing with alpha = 1 / (1 - c)
+    n_0, it_0 = O.scf_kernel(s.R, s.L, s.Z, M, 0, c, tol=1e-10, max_iter=1000)
+    assert it_0 == it_mix and np.max(np.abs(n_0 - n_mix)) < 1e-12

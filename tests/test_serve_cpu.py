@@ -111,3 +111,27 @@ def test_equal_arrivals_each_job_steps_exactly_its_own_count():
             assert "step failed" in j.error and j.done_steps == 2
         else:
             assert j.error == "" and j.done_steps == j.steps == CountingCtx.steps[j.jid]
+
+
+def test_shortest_job_first_admission():
+    # one worker, all jobs arrived: sjf admits by estimated work (size, squarings, steps)
+    sizes = [400, 40, 200, 100, 800]
+    jobs = [serve.Job(arrival=0.0, jid=i, natoms=n, Te=1000.0, steps=1, seed=i) for i, n in enumerate(sizes)]
+    sch = serve.Scheduler(FakeX(), 10**13, workers=1, make_ctx=fake_make, policy="sjf")
+    for j in jobs:
+        sch.submit(j)
+    sch.run()
+    order = [j.natoms for j in sorted(sch.finished, key=lambda j: j.admitted)]
+    assert order == sorted(sizes)
+    with pytest.raises(ValueError):
+        serve.Scheduler(FakeX(), 1, workers=1, policy="lifo")
+
+
+def test_summary_counts_jobs_still_running():
+    sch = serve.Scheduler(FakeX(), 10**12, workers=1, make_ctx=fake_make)
+    j = serve.Job(arrival=0.0, jid=0, natoms=32, Te=1000.0, steps=10, seed=0)
+    j.done_steps, j.lat = 4, [0.01] * 4
+    sch.active[0].append(j)
+    res = serve.summarize(sch, 1.0)
+    assert res["total_steps"] == 4 and res["jobs_admitted"] == 1 and res["jobs_finished"] == 0
+    assert res["step_latency_ms_p50"] == pytest.approx(10.0)
