@@ -91,7 +91,8 @@ class XLParams:
     c: tuple = (-6.0, 14.0, -8.0, -3.0, 4.0, -1.0)
     rank_m: int = 2
     kernel_c: float = 0.0                   # J_0 = c I
-    kernel_mode: str = "rank"               # "rank": rank-m every step; "exact": K = (J - I)^-1
+    kernel_mode: str = "rank"               # "rank": rank-m every step; "exact": K = (J - I)^-1;
+                                            # "accumulated": one rank-1 update per step of the carried K
     kernel_every: int = 0                   # exact: recompute every this many steps (0: kept from t0)
     mix_alpha: float = 0.5                  # linear mixing at t0
     scf_tol: float = 1e-10
@@ -562,6 +563,22 @@ def jacobian(dens: Density, gamma, P=None, gmu=None):
     return J
 
 
+def kernel_rank1_accumulate(K, J, r, respond):
+    """One on-the-fly update of a carried kernel (end of Section V.F): v = K r / |K r|,
+    w = respond(v), u = w - J v, J <- J + u v^T, K <- K - K u v^T K / (1 + v^T K u) (Eq. K_up).
+    K stays (J - I)^-1.  Returns (K, J); unchanged when K r = 0."""
+    v = K @ r
+    nv = np.linalg.norm(v)
+    if nv == 0.0 or not np.isfinite(nv):
+        return K, J
+    v = v / nv
+    u = respond(v) - J @ v
+    J = J + np.outer(u, v)
+    Ku = K @ u
+    K = K - np.outer(Ku, v @ K) / (1.0 + v @ Ku)
+    return K, J
+
+
 def kernel_exact(dens: Density, gamma):
     """The exact kernel K = (J - I)^-1 of Eq. KK, J = dq/dn."""
     J = jacobian(dens, gamma)
@@ -749,7 +766,8 @@ class MDState:
     F: np.ndarray
     Kr: np.ndarray
     step: int = 0
-    K: np.ndarray | None = None     # exact kernel held between recomputations
+    K: np.ndarray | None = None     # exact or accumulated kernel carried between steps
+    J: np.ndarray | None = None     # accumulated mode: the Jacobian estimate with K = (J - I)^-1
 
 
 def kinetic_energy(V, mass):
@@ -771,14 +789,21 @@ def md_init(sys_R, sys_V, L, Z, mass, model: Model, xl: XLParams, n0=None):
     R = wrap(np.asarray(sys_R, dtype=float), L)
     if n0 is None:
         n0, _ = scf(R, L, Z, model, xl.mix_alpha, tol=xl.scf_tol, max_iter=xl.scf_max_iter)
-    exact = xl.kernel_mode == "exact"
-    ev = evaluate(R, L, Z, n0, model, xl, with_kernel=not exact)
-    K = None
-    if exact:
+    full = xl.kernel_mode in ("exact", "accumulated")
+    ev = evaluate(R, L, Z, n0, model, xl, with_kernel=not full)
+    K = J = None
+    if xl.kernel_mode == "exact":
         K = kernel_exact(ev.dens, ev.gamma)
+    elif xl.kernel_mode == "accumulated":
+        nat = len(n0)
+        c = xl.kernel_c
+        P, gmu = divided_differences(ev.dens)
+        K, J = kernel_rank1_accumulate(np.eye(nat) / (c - 1.0), c * np.eye(nat), ev.r,
+                                       lambda v: response(ev.dens, ev.gamma, v, P, gmu))
+    if full:
         ev.Kr = K @ ev.r
     nh = np.tile(np.asarray(n0, dtype=float), (xl.kmax + 1, 1))
-    st = MDState(R=R, V=np.array(sys_V, dtype=float), nhist=nh, F=ev.F, Kr=ev.Kr, K=K)
+    st = MDState(R=R, V=np.array(sys_V, dtype=float), nhist=nh, F=ev.F, Kr=ev.Kr, K=K, J=J)
     return st, ev
 
 
@@ -791,14 +816,18 @@ def md_step(st: MDState, L, Z, mass, model: Model, xl: XLParams):
     R = wrap(st.R + dt * Vh, L)
     n_new = n_update(st.nhist, st.Kr, xl)
     step = st.step + 1
-    exact = xl.kernel_mode == "exact"
-    ev = evaluate(R, L, Z, n_new, model, xl, with_kernel=not exact)
-    K = st.K
-    if exact:
+    full = xl.kernel_mode in ("exact", "accumulated")
+    ev = evaluate(R, L, Z, n_new, model, xl, with_kernel=not full)
+    K, J = st.K, st.J
+    if xl.kernel_mode == "exact":
         # the full kernel of the t0 state, recomputed every kernel_every steps (Section VI.A, Figs. 3, 5)
         if xl.kernel_every > 0 and step % xl.kernel_every == 0:
             K = kernel_exact(ev.dens, ev.gamma)
+    elif xl.kernel_mode == "accumulated":
+        P, gmu = divided_differences(ev.dens)
+        K, J = kernel_rank1_accumulate(K, J, ev.r, lambda v: response(ev.dens, ev.gamma, v, P, gmu))
+    if full:
         ev.Kr = K @ ev.r
     V = Vh + 0.5 * dt * ev.F / mass * ACC
     nh = np.vstack([n_new[None, :], st.nhist[:-1]])
-    return MDState(R=R, V=V, nhist=nh, F=ev.F, Kr=ev.Kr, step=step, K=K), ev
+    return MDState(R=R, V=V, nhist=nh, F=ev.F, Kr=ev.Kr, step=step, K=K, J=J), ev

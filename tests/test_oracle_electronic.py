@@ -222,3 +222,22 @@ def test_kernel_scf_reaches_the_mixing_fixed_point_in_fewer_iterations():
     # a rank-0 kernel is linear mixing with alpha = 1 / (1 - c)
     n_0, it_0 = O.scf_kernel(s.R, s.L, s.Z, M, 0, c, tol=1e-10, max_iter=1000)
     assert it_0 == it_mix and np.max(np.abs(n_0 - n_mix)) < 1e-12
+
+
+def test_accumulated_rank1_updates_keep_K_the_inverse_of_J_minus_I(tiny):
+    # the carried kernel of the on-the-fly scheme stays (J - I)^-1 through any
+    # sequence of updates (Eq. K_up), and each update makes J exact on its probe
+    s, H0, gam, n = tiny
+    nat, c = 8, -9.0
+    K, J = np.eye(nat) / (c - 1.0), c * np.eye(nat)
+    rng = np.random.default_rng(3)
+    for k in range(5):
+        nk = n + 0.01 * rng.normal(size=nat)
+        d = O.density(O.hamiltonian(H0, gam, nk), M.beta, M.n_sq, 16)
+        r = O.mulliken(d.D, s.Z) - nk
+        K1, J1 = O.kernel_rank1_accumulate(K, J, r, lambda v: O.response(d, gam, v))
+        v = K @ r
+        v /= np.linalg.norm(v)
+        assert np.allclose(J1 @ v, O.response(d, gam, v), atol=1e-12)
+        K, J = K1, J1
+        assert np.allclose(K, np.linalg.inv(J - np.eye(nat)), atol=1e-10 * np.abs(K).max())
