@@ -795,11 +795,12 @@ def md_init(sys_R, sys_V, L, Z, mass, model: Model, xl: XLParams, n0=None):
     if xl.kernel_mode == "exact":
         K = kernel_exact(ev.dens, ev.gamma)
     elif xl.kernel_mode == "accumulated":
+        # the carried kernel starts as K_0 = (c - 1)^-1 I, J_0 = c I; the first rank-1 update
+        # comes with the first MD step: at the SCF ground state r is rounding noise, and a
+        # probe along it would keep that noise in K
         nat = len(n0)
         c = xl.kernel_c
-        P, gmu = divided_differences(ev.dens)
-        K, J = kernel_rank1_accumulate(np.eye(nat) / (c - 1.0), c * np.eye(nat), ev.r,
-                                       lambda v: response(ev.dens, ev.gamma, v, P, gmu))
+        K, J = np.eye(nat) / (c - 1.0), c * np.eye(nat)
     if full:
         ev.Kr = K @ ev.r
     nh = np.tile(np.asarray(n0, dtype=float), (xl.kmax + 1, 1))
