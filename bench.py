@@ -50,6 +50,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=0,
                     help="also time this many plain-FP64 GPU steps of the same workload")
+    ap.add_argument("--trajectory-check", type=int, default=0, metavar="K",
+                    help="study run instead of the timing: --steps MD steps after the t0 SCF, the energy "
+                         "monitor every --energy-every steps, and every K steps the oracle re-evaluates q, "
+                         "F and Omega at the GPU's (R, n); prints one JSON line")
+    ap.add_argument("--energy-every", type=int, default=10)
+    ap.add_argument("--precision-study", default="",
+                    help="comma-separated precisions (e.g. fp16x3,bf16x3): at the t0 state of the first, "
+                         "each evaluates q, F and Omega against one oracle evaluation of the same (R, n), "
+                         "then times --steps MD steps; prints one JSON line")
     ap.add_argument("--profile-step", action="store_true",
                     help="profiling run: t0 SCF, --warmup steps, then one step inside the NVTX range "
                          "'xlbomd_step'; prints no JSON")
@@ -180,6 +189,97 @@ def run_reference(a, ws, rank):
     return 0
 
 
+def run_trajectory_study(a, X, ctx, s):
+    """State-wise parity along one trajectory: the MD diverges chaotically from any other
+    run, so at every K-th step the oracle evaluates the GPU's own (R, n) state."""
+    import numpy as np
+    import oracle as O
+    m = O.Model(Te=a.Te, n_sq=a.nsq)
+    t = time.perf_counter()
+    ctx.scf(0)
+    t_scf = time.perf_counter() - t
+    E, checks = [], []
+    t_md = 0.0
+    for k in range(1, a.steps + 1):
+        t = time.perf_counter()
+        ctx.step(1)
+        t_md += time.perf_counter() - t
+        if k % a.energy_every == 0 or k % a.trajectory_check == 0:
+            ctx.energy(0)
+            E.append((k, float(ctx.get(0, X.ENERGY)[5])))
+        if k % a.trajectory_check == 0:
+            R, n = ctx.get(0, X.R), ctx.get(0, X.N)
+            q, F, Om = ctx.get(0, X.Q), ctx.get(0, X.F), float(ctx.get(0, X.ENERGY)[0])
+            t = time.perf_counter()
+            ev = O.evaluate(R, s.L, s.Z, n, m, None, with_kernel=False)
+            checks.append({"step": k, "dq": float(np.abs(q - ev.q).max()), "dF": float(np.abs(F - ev.F).max()),
+                           "dOmega": Om - ev.Omega, "rms_residual": float(np.sqrt(np.mean((ev.q - n) ** 2))),
+                           "oracle_s": time.perf_counter() - t})
+            print(json.dumps({"check": checks[-1]}), file=sys.stderr, flush=True)
+    steps_e = np.array([e[0] for e in E], dtype=float)
+    Etot = np.array([e[1] for e in E])
+    slope = float(np.polyfit(steps_e * 0.25e-3, Etot, 1)[0]) if len(E) > 1 else None   # eV / ps
+    out = {"study": "trajectory state-wise parity", "natoms": s.natoms, "prec": a.prec, "Te": a.Te,
+           "n_sq": a.nsq, "rank_m": a.rank, "steps": a.steps, "dt_fs": 0.25, "scf_s": t_scf,
+           "md_steps_per_s": a.steps / t_md, "checks": checks,
+           "max_dq": max(c["dq"] for c in checks), "max_dF": max(c["dF"] for c in checks),
+           "max_abs_dOmega": max(abs(c["dOmega"]) for c in checks),
+           "energy_samples": len(E), "Etot_first": float(Etot[0]), "Etot_max_dev": float(np.abs(Etot - Etot[0]).max()),
+           "Etot_drift_eV_per_ps": slope}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_precision_study(a, X, ctx, s, sysd, stream):
+    """Error of each split precision against the FP64 oracle at one shared state, and its
+    MD step rate."""
+    import numpy as np
+    import torch
+    import oracle as O
+    precs = [x for x in a.precision_study.split(",") if x]
+    t = time.perf_counter()
+    ctx.scf(0)
+    t_scf = time.perf_counter() - t
+    R, n, mu = ctx.get(0, X.R), ctx.get(0, X.N), float(ctx.get(0, X.MU)[0])
+    ctx.close()
+    sysd = dict(sysd, R=R)
+    rows = []
+    for prec in precs:
+        c = X.Context(make_params(X, a, prec), [sysd], stream=stream.cuda_stream)
+        c.set(0, X.N, n)
+        c.set(0, X.MU, [mu])
+        c.build_H(0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        c.density(0)
+        torch.cuda.synchronize()
+        t_dens = time.perf_counter() - t
+        c.energy(0)
+        row = {"prec": prec, "q": c.get(0, X.Q), "F": c.get(0, X.F), "Omega": float(c.get(0, X.ENERGY)[0]),
+               "density_s": t_dens}
+        c.kernel_update(0)
+        c.step(1)                       # warm-up
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        c.step(a.steps)
+        torch.cuda.synchronize()
+        row["md_steps_per_s"] = a.steps / (time.perf_counter() - t)
+        c.close()
+        rows.append(row)
+    t = time.perf_counter()
+    ev = O.evaluate(R, s.L, s.Z, n, O.Model(Te=a.Te, n_sq=a.nsq), None, with_kernel=False)
+    t_or = time.perf_counter() - t
+    out = {"study": "precision", "natoms": s.natoms, "n_orbitals": 4 * s.natoms, "Te": a.Te, "n_sq": a.nsq,
+           "rank_m": a.rank, "scf_s": t_scf, "oracle_eval_s": t_or, "md_steps_timed": a.steps, "results": []}
+    for r in rows:
+        out["results"].append({"prec": r["prec"], "max_dq": float(np.abs(r["q"] - ev.q).max()),
+                               "max_dF": float(np.abs(r["F"] - ev.F).max()), "dOmega": r["Omega"] - ev.Omega,
+                               "density_s": r["density_s"], "md_steps_per_s": r["md_steps_per_s"]})
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     a = parse()
     ws, rank, local = dist_setup()
@@ -210,6 +310,11 @@ def main():
     p = make_params(X, a, a.prec)
     stream = torch.cuda.current_stream()
     ctx = X.Context(p, [sysd], stream=stream.cuda_stream)
+
+    if a.trajectory_check > 0:
+        return run_trajectory_study(a, X, ctx, s)
+    if a.precision_study:
+        return run_precision_study(a, X, ctx, s, sysd, stream)
 
     if a.profile_step:
         ctx.scf(0)

@@ -93,6 +93,16 @@ typedef struct {
                               1.2 x the most negative eigenvalue of dq/dn (power iteration on
                               the response, 12 probes), so that K_0 = (c - 1)^-1 I keeps the
                               stiffest charge mode stable */
+  int kernel_mode;         /* 0: rank-m kernel rebuilt every step (Eq. K_up, v_1);
+                              1: exact kernel K = (J - I)^-1 of Eq. KK, J = dq/dn from the
+                              responses to the natoms unit directions, held between
+                              recomputations (Section VI.A);
+                              2: accumulated kernel: K and J carried from step to step, one
+                              rank-1 update per kernel update with v = K r/|K r|; a started
+                              kernel (first update, or xlbomd_scf) is K_0 = (c - 1)^-1 I,
+                              J_0 = c I without an update (end of Section V.F) */
+  int kernel_every;        /* kernel_mode 1: recompute K every this many MD steps
+                              (0: keep the kernel of the t0 state) */
 } xlbomd_params;
 
 /* One trajectory.  R and V are natoms x 3 row-major (A, A/fs), Z natoms
@@ -122,11 +132,17 @@ typedef enum {
   XLBOMD_H = 11,       /* get: H[n] (N x N) */
   XLBOMD_GAMMA = 12,   /* get: Coulomb matrix gamma (natoms x natoms) */
   XLBOMD_STATS = 13,   /* get: [mu passes, NS products, probes used, GEMMs, steps] (5) */
-  XLBOMD_PROBES = 14   /* get: probes V then responses W (2 x rank_m x natoms) */
+  XLBOMD_PROBES = 14,  /* get: probes V then responses W (2 x rank_m x natoms) */
+  XLBOMD_KMAT = 15     /* get: held kernel K (natoms x natoms, row-major; kernel_mode 1, 2) */
 } xlbomd_quantity;
 
 /* Defaults of the 24-atom reference workload. */
 void xlbomd_default_params(xlbomd_params* p);
+
+/* Table I row kmax (5, 6 or 7): kappa, alpha and c_0..c_kmax of the dissipative
+ * n update (Eq. VRL_Damp) written into p (kmax, kappa, alpha, c; the other
+ * fields are untouched).  Errors: ERR_ARG for another kmax or a null p. */
+xlbomd_status xlbomd_table_i(xlbomd_params* p, int kmax);
 
 /* Allocate device state for nsys trajectories and upload R, V, Z (Eq. IBC
  * nuclear initial conditions).  Builds H0 and gamma; n = 0.  Does not run
@@ -177,8 +193,22 @@ xlbomd_status xlbomd_response(xlbomd_ctx* ctx, int sys, const double* v_dev, dou
  * point; it exists for callers that cannot allocate. */
 xlbomd_status xlbomd_response_noalloc(xlbomd_ctx* ctx, int sys, const double* v_dev, double* w_dev);
 
-/* a7-a8: rank-m kernel on r (Eqs. K_up, v_1; Woodbury form), result in KR. */
+/* a7-a8: K r into KR.  kernel_mode 0: rank-m kernel on r (Eqs. K_up, v_1;
+ * Woodbury form).  kernel_mode 1: the held exact kernel applied to r (computed
+ * first, by xlbomd_kernel_exact, when none is held).  kernel_mode 2: one rank-1
+ * update of the carried kernel at the current state, then K r (the first call,
+ * and the call that ends xlbomd_scf, start the kernel at K_0 instead). */
 xlbomd_status xlbomd_kernel_update(xlbomd_ctx* ctx, int sys);
+
+/* Exact kernel K = (J - I)^-1 (Eq. KK) at the current density: J = dq/dn
+ * column by column from the responses to the natoms unit directions (the
+ * full-rank end of the Eq. K_up sequence), inverted on the device in FP64 by
+ * Gauss-Jordan elimination with partial pivoting.  Costs natoms responses.
+ * The kernel is held in the context (XLBOMD_KMAT) and used by
+ * xlbomd_kernel_update, xlbomd_scf and xlbomd_step when kernel_mode = 1.
+ * Requires xlbomd_density on the same state.  Errors: ERR_ARG (no density),
+ * ERR_NOT_CONVERGED (J - I numerically singular), ERR_OOM. */
+xlbomd_status xlbomd_kernel_exact(xlbomd_ctx* ctx, int sys);
 
 /* a10: energy monitor (shadow free energy Omega and kinetic energy). */
 xlbomd_status xlbomd_energy(xlbomd_ctx* ctx, int sys);

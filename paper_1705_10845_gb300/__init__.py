@@ -5,5 +5,5 @@ The Python side only marshals arguments to libxlbomd.so; see binding.Context.
 from . import build  # noqa: F401
 from .binding import (  # noqa: F401
     Context, Params, XlbomdError, default_params, load, library_path,
-    Q, N, NHIST, F, R, V, KR, RES, ENERGY, MU, D, H, GAMMA, STATS, PROBES,
+    Q, N, NHIST, F, R, V, KR, RES, ENERGY, MU, D, H, GAMMA, STATS, PROBES, KMAT,
 )

@@ -17,7 +17,7 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_NOT_CO
           -5: "ERR_SPECTRUM", -6: "ERR_DIVERGED", -7: "ERR_TIMEOUT", -8: "ERR_UNSUPPORTED"}
 PREC = {"fp64": 0, "fp16x3": 1, "bf16x3": 2}
 
-Q, N, NHIST, F, R, V, KR, RES, ENERGY, MU, D, H, GAMMA, STATS, PROBES = range(15)
+Q, N, NHIST, F, R, V, KR, RES, ENERGY, MU, D, H, GAMMA, STATS, PROBES, KMAT = range(16)
 
 
 class XlbomdError(RuntimeError):
@@ -37,7 +37,7 @@ class Params(C.Structure):
         ("scf_tol", C.c_double), ("scf_max_iter", C.c_int), ("mu_tol", C.c_double),
         ("mu_max_iter", C.c_int), ("diverge_tol", C.c_double), ("prec", C.c_int),
         ("energy_every", C.c_int), ("scf_mode", C.c_int),
-        ("kernel_auto", C.c_int),
+        ("kernel_auto", C.c_int), ("kernel_mode", C.c_int), ("kernel_every", C.c_int),
     ]
 
 
@@ -66,8 +66,10 @@ def load(path: str | None = None):
     lib.xlbomd_default_params.argtypes = [C.POINTER(Params)]
     lib.xlbomd_default_params.restype = None
     lib.xlbomd_init.argtypes = [C.POINTER(Params), C.POINTER(System), I, VP, C.POINTER(P)]
-    for name in ("xlbomd_scf", "xlbomd_build_H", "xlbomd_density", "xlbomd_kernel_update", "xlbomd_energy"):
+    for name in ("xlbomd_scf", "xlbomd_build_H", "xlbomd_density", "xlbomd_kernel_update", "xlbomd_energy",
+                 "xlbomd_kernel_exact"):
         getattr(lib, name).argtypes = [P, I]
+    lib.xlbomd_table_i.argtypes = [C.POINTER(Params), I]
     lib.xlbomd_step.argtypes = [P, I]
     lib.xlbomd_response.argtypes = [P, I, VP, VP]
     lib.xlbomd_get.argtypes = [P, I, I, DP]
@@ -85,16 +87,24 @@ def load(path: str | None = None):
     lib.xlbomd_selftest_gemm.restype = C.c_int
     for name in ("xlbomd_init", "xlbomd_scf", "xlbomd_build_H", "xlbomd_density", "xlbomd_kernel_update",
                  "xlbomd_energy", "xlbomd_step", "xlbomd_response", "xlbomd_get", "xlbomd_set",
-                 "xlbomd_sizes", "xlbomd_clear_error", "xlbomd_free"):
+                 "xlbomd_sizes", "xlbomd_clear_error", "xlbomd_free", "xlbomd_kernel_exact", "xlbomd_table_i"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
 
 
 def default_params(**overrides) -> Params:
+    """xlbomd_default_params, then kmax (its Table I row, xlbomd_table_i), then the other overrides."""
     p = Params()
-    load().xlbomd_default_params(C.byref(p))
+    lib = load()
+    lib.xlbomd_default_params(C.byref(p))
+    if "kmax" in overrides:
+        st = lib.xlbomd_table_i(C.byref(p), int(overrides["kmax"]))
+        if st != XLBOMD_OK:
+            raise XlbomdError(st, "xlbomd_table_i")
     for k, v in overrides.items():
+        if k == "kmax":
+            continue
         if k == "prec" and isinstance(v, str):
             v = PREC[v]
         if k in ("t0", "c"):
@@ -172,6 +182,9 @@ class Context:
     def kernel_update(self, sys=0):
         self._check(self._lib.xlbomd_kernel_update(self.h, sys), "xlbomd_kernel_update")
 
+    def kernel_exact(self, sys=0):
+        self._check(self._lib.xlbomd_kernel_exact(self.h, sys), "xlbomd_kernel_exact")
+
     def energy(self, sys=0):
         self._check(self._lib.xlbomd_energy(self.h, sys), "xlbomd_energy")
 
@@ -189,7 +202,7 @@ class Context:
         m = self.params.rank_m
         return {Q: nat, N: nat, NHIST: k1 * nat, F: 3 * nat, R: 3 * nat, V: 3 * nat, KR: nat, RES: nat,
                 ENERGY: 6, MU: 1, D: (4 * nat) ** 2, H: (4 * nat) ** 2, GAMMA: nat * nat, STATS: 5,
-                PROBES: 2 * m * nat}[what]
+                PROBES: 2 * m * nat, KMAT: nat * nat}[what]
 
     def get(self, sys, what) -> np.ndarray:
         out = np.zeros(self._count(sys, what))
@@ -199,7 +212,7 @@ class Context:
             return out.reshape(nat, 3)
         if what in (D, H):
             return out.reshape(4 * nat, 4 * nat)
-        if what == GAMMA:
+        if what in (GAMMA, KMAT):
             return out.reshape(nat, nat)
         if what == NHIST:
             return out.reshape(-1, nat)

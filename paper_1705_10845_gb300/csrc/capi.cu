@@ -35,6 +35,7 @@ struct Sys {
   double *H0 = nullptr, *H = nullptr, *Dm = nullptr;
   double *ddiag = nullptr, *dmu_diag = nullptr, *d1 = nullptr, *dvec = nullptr, *dvec_mu = nullptr;
   double *pV = nullptr, *pW = nullptr, *scal = nullptr, *work = nullptr, *energy = nullptr;
+  double *Kfull = nullptr, *Jm = nullptr;   // exact kernel (natoms x natoms) and its work matrix
   MatSet mats;   // expansion matrices in the working precision
   // host
   double mu = 0.0;
@@ -44,6 +45,8 @@ struct Sys {
   double dmu_last = 0.0;
   double kc = 0.0;          // c of J_0 = c I for this system
   bool have_density = false;
+  bool have_K = false;      // Kfull holds an exact kernel
+  long long md_steps = 0;   // MD steps taken by this system
   int probes_used = 0;
   double stats[5] = {0, 0, 0, 0, 0};
   double eh[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -326,9 +329,81 @@ xlbomd_status response(xlbomd_ctx* ctx, Sys& S, const double* v, double* w) {
 }
 
 // a7-a8
+// Exact kernel K = (J - I)^-1 (Eq. KK): J column by column from the responses to the
+// unit directions e_I, then Gauss-Jordan with partial pivoting in FP64.
+xlbomd_status kernel_exact(xlbomd_ctx* ctx, Sys& S) {
+  cudaStream_t st = ctx->stream;
+  if (!S.have_density) return fail(ctx, XLBOMD_ERR_ARG, "xlbomd_density must run first");
+  const size_t nn = (size_t)S.nat * S.nat;
+  if (!S.Kfull) CKS(dalloc(ctx, &S.Kfull, nn));
+  if (!S.Jm) CKS(dalloc(ctx, &S.Jm, nn));
+  double* v = S.pV + (size_t)kMaxRank * S.nat;   // spare probe rows
+  double* w = S.pW + (size_t)kMaxRank * S.nat;
+  for (int I = 0; I < S.nat; ++I) {
+    CK(launch_unit_vector(st, S.nat, I, v));
+    CKS(response(ctx, S, v, w));
+    CK(launch_jacobian_column(st, S.nat, I, w, S.Jm, S.Kfull));
+  }
+  CK(cudaMemsetAsync(S.scal + 10, 0, sizeof(double), st));
+  CK(launch_gauss_jordan(st, S.nat, S.Jm, S.Kfull, S.work, S.scal + 10));
+  CKS(sync_read(ctx, S.scal + 10, 1));
+  if (ctx->pinned[0] != 0.0) return fail(ctx, XLBOMD_ERR_NOT_CONVERGED, "J - I is numerically singular");
+  S.have_K = true;
+  return XLBOMD_OK;
+}
+
+// Accumulated kernel: the carried K (= (J - I)^-1) gets one rank-1 update at the current
+// state (end of Section V.F): v = K r/|K r|, u = w - J v, J += u v^T,
+// K -= K u v^T K / (1 + v^T K u) (Eq. K_up).  A (re)started kernel is K_0 = (c-1)^-1 I,
+// J_0 = c I with no update: at the t0 ground state r is rounding noise, and a probe along it
+// would keep that noise in K.
+xlbomd_status kernel_accumulate(xlbomd_ctx* ctx, Sys& S) {
+  cudaStream_t st = ctx->stream;
+  if (!S.have_density) return fail(ctx, XLBOMD_ERR_ARG, "xlbomd_density must run first");
+  const int n = S.nat;
+  if (!S.Kfull) CKS(dalloc(ctx, &S.Kfull, (size_t)n * n));
+  if (!S.Jm) CKS(dalloc(ctx, &S.Jm, (size_t)n * n));
+  if (!S.have_K) {
+    CK(launch_scaled_identity(st, n, 1.0 / (S.kc - 1.0), S.Kfull));
+    CK(launch_scaled_identity(st, n, S.kc, S.Jm));
+    S.have_K = true;
+    return XLBOMD_OK;
+  }
+  double* v = S.pV + (size_t)kMaxRank * n;   // spare probe rows
+  double* w = S.pW + (size_t)kMaxRank * n;
+  double *t = S.work, *u = S.work + n, *Ku = S.work + 2 * n, *vK = S.work + 3 * n;
+  CK(launch_gemv(st, n, S.Kfull, n, S.r, v));
+  CK(launch_normalize(st, n, v, S.scal + 11));
+  CKS(sync_read(ctx, S.scal + 11, 1));
+  if (ctx->pinned[0] == 1.0) {
+    CKS(response(ctx, S, v, w));
+    CK(launch_gemv(st, n, S.Jm, n, v, t));
+    CK(launch_sub(st, n, w, t, u));
+    CK(launch_gemv(st, n, S.Kfull, n, u, Ku));
+    CK(launch_gemv_t(st, n, S.Kfull, v, vK));
+    CK(launch_dot1p(st, n, v, Ku, S.scal + 12));
+    CK(launch_rank1_update(st, n, u, v, Ku, vK, S.scal + 12, S.Jm, S.Kfull));
+  }
+  return XLBOMD_OK;
+}
+
 xlbomd_status kernel_update(xlbomd_ctx* ctx, Sys& S) {
   cudaStream_t st = ctx->stream;
   const xlbomd_params& p = ctx->p;
+  if (p.kernel_mode == 2) {
+    CKS(kernel_accumulate(ctx, S));
+    CK(launch_gemv(st, S.nat, S.Kfull, S.nat, S.r, S.Kr));
+    S.probes_used = 1;
+    S.stats[2] = 1;
+    return XLBOMD_OK;
+  }
+  if (p.kernel_mode == 1) {
+    if (!S.have_K) CKS(kernel_exact(ctx, S));
+    CK(launch_gemv(st, S.nat, S.Kfull, S.nat, S.r, S.Kr));
+    S.probes_used = S.nat;
+    S.stats[2] = S.nat;
+    return XLBOMD_OK;
+  }
   int m = 0;
   for (int i = 0; i < p.rank_m; ++i) {
     CK(launch_kernel_vec(st, 0, S.nat, i, S.kc, S.r, S.pV, S.pW, nullptr, S.scal + 8));
@@ -435,6 +510,7 @@ xlbomd_status scf(xlbomd_ctx* ctx, Sys& S) {
       CK(launch_fill_history(st, S.nat, p.kmax, S.nh));
       CK(launch_forces(st, model_of(p), S.nat, S.L, S.eta, S.ng, S.G4, S.R, S.Dm, S.np, S.q, S.nh, S.F, S.work,
                        p.prec != XLBOMD_FP64));
+      S.have_K = false;   // exact or accumulated kernel: start again at the t0 state
       return kernel_update(ctx, S);
     }
     if (p.scf_mode == 1 && p.rank_m > 0) {
@@ -455,6 +531,8 @@ xlbomd_status md_step(xlbomd_ctx* ctx, Sys& S, bool do_energy) {
                          ctx->cdev));
   CKS(build_H(ctx, S));
   CKS(density(ctx, S, true));
+  ++S.md_steps;
+  if (p.kernel_mode == 1 && p.kernel_every > 0 && S.md_steps % p.kernel_every == 0) S.have_K = false;
   CKS(kernel_update(ctx, S));
   CK(launch_verlet_second(st, S.nat, p.dt, minv, S.V, S.F));
   CK(launch_absmax(st, S.nat, S.r, S.scal + 9));
@@ -468,7 +546,8 @@ xlbomd_status md_step(xlbomd_ctx* ctx, Sys& S, bool do_energy) {
 void free_sys(Sys& S) {
   double** ptrs[] = {&S.R,  &S.V,        &S.F,    &S.Z,  &S.nh,  &S.q,    &S.r,     &S.Kr,    &S.pot,
                      &S.potv, &S.gam,    &S.SF,   &S.G4, &S.H0,  &S.H,    &S.Dm,    &S.ddiag, &S.dmu_diag,
-                     &S.d1, &S.dvec,     &S.dvec_mu, &S.pV, &S.pW, &S.scal, &S.work, &S.energy};
+                     &S.d1, &S.dvec,     &S.dvec_mu, &S.pV, &S.pW, &S.scal, &S.work, &S.energy,
+                     &S.Kfull, &S.Jm};
   for (double** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -598,6 +677,23 @@ void xlbomd_default_params(xlbomd_params* p) {
   p->energy_every = 0;
   p->scf_mode = 0;
   p->kernel_auto = 0;
+  p->kernel_mode = 0;
+  p->kernel_every = 0;
+}
+
+xlbomd_status xlbomd_table_i(xlbomd_params* p, int kmax) {
+  // Table I: kappa, alpha, c_0..c_kmax
+  static const double kappa[3] = {1.82, 1.84, 1.86}, alpha[3] = {0.018, 0.0055, 0.0016};
+  static const double c[3][8] = {{-6, 14, -8, -3, 4, -1, 0, 0},
+                                 {-14, 36, -27, -2, 12, -6, 1, 0},
+                                 {-36, 99, -88, 11, 32, -25, 8, -1}};
+  if (!p || kmax < 5 || kmax > 7) return XLBOMD_ERR_ARG;
+  const int r = kmax - 5;
+  p->kmax = kmax;
+  p->kappa = kappa[r];
+  p->alpha = alpha[r];
+  for (int k = 0; k < 8; ++k) p->c[k] = c[r][k];
+  return XLBOMD_OK;
 }
 
 xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* systems, int nsys, void* cuda_stream,
@@ -606,7 +702,8 @@ xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* syst
   *out = nullptr;
   const xlbomd_params& p = *params;
   if (p.n_sq < 1 || p.n_sq > 40 || p.kmax < 1 || p.kmax > 7 || p.rank_m < 0 || p.rank_m > kMaxRank ||
-      p.kernel_c == 1.0 || !(p.Te > 0) || !(p.dt > 0) || p.mu_max_iter < 1 || p.scf_mode < 0 || p.scf_mode > 1)
+      p.kernel_c == 1.0 || !(p.Te > 0) || !(p.dt > 0) || p.mu_max_iter < 1 || p.scf_mode < 0 || p.scf_mode > 1 ||
+      p.kernel_mode < 0 || p.kernel_mode > 2 || p.kernel_every < 0)
     return XLBOMD_ERR_ARG;
   if (p.prec != XLBOMD_FP64 && p.prec != XLBOMD_FP16x3 && p.prec != XLBOMD_BF16x3) return XLBOMD_ERR_ARG;
   for (int i = 0; i < nsys; ++i) {
@@ -722,6 +819,11 @@ xlbomd_status xlbomd_density(xlbomd_ctx* ctx, int sys) {
   return density(ctx, ctx->sys[sys], true);
 }
 
+xlbomd_status xlbomd_kernel_exact(xlbomd_ctx* ctx, int sys) {
+  CKS(check(ctx, sys));
+  return kernel_exact(ctx, ctx->sys[sys]);
+}
+
 xlbomd_status xlbomd_response(xlbomd_ctx* ctx, int sys, const double* v_dev, double* w_dev) {
   CKS(check(ctx, sys));
   if (!v_dev || !w_dev) return fail(ctx, XLBOMD_ERR_ARG, "null probe pointer");
@@ -800,6 +902,9 @@ xlbomd_status xlbomd_get(xlbomd_ctx* ctx, int sys, int what, double* host_out) {
       return rs;
     }
     case XLBOMD_STATS: std::memcpy(host_out, S.stats, 5 * sizeof(double)); return XLBOMD_OK;
+    case XLBOMD_KMAT:
+      if (!S.have_K) return fail(ctx, XLBOMD_ERR_ARG, "no exact kernel held (xlbomd_kernel_exact)");
+      return cp(S.Kfull, nat * nat);
     case XLBOMD_PROBES: {
       CK(cudaMemcpyAsync(host_out, S.pV, sizeof(double) * ctx->p.rank_m * nat, cudaMemcpyDeviceToHost, ctx->stream));
       CK(cudaMemcpyAsync(host_out + ctx->p.rank_m * nat, S.pW, sizeof(double) * ctx->p.rank_m * nat,

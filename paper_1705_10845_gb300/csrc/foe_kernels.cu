@@ -399,4 +399,234 @@ cudaError_t launch_kernel_vec(cudaStream_t s, int mode, int nat, int m, double c
   return cudaGetLastError();
 }
 
+
+// ---- exact kernel K = (J - I)^-1 (Eq. KK) ----
+
+namespace {
+
+__global__ void unit_vector_kernel(int n, int i, double* __restrict__ v) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a < n) v[a] = (a == i) ? 1.0 : 0.0;
+}
+
+// A[a][col] = w[a] - delta(a, col): column col of J - I (row-major n x n); B = I alongside
+__global__ void jacobian_column_kernel(int n, int col, const double* __restrict__ w, double* __restrict__ A,
+                                       double* __restrict__ B) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  A[(size_t)a * n + col] = w[a] - (a == col ? 1.0 : 0.0);
+  B[(size_t)a * n + col] = (a == col) ? 1.0 : 0.0;
+}
+
+// Gauss-Jordan step k, part 1 (one CTA): partial pivot of column k over rows k..n-1,
+// swap of rows k and p in A and B, scaling of row k by 1 / A_kk, and the elimination
+// factors f_i = A_ik (f_k = 0) copied out so that part 2 reads no column it writes.
+__global__ void gj_pivot_kernel(int n, int k, double* __restrict__ A, double* __restrict__ B,
+                                double* __restrict__ f, double* __restrict__ flag) {
+  __shared__ double sv[32];
+  __shared__ int si[32];
+  __shared__ int s_p;
+  double best = -1.0;
+  int bi = k;
+  for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+    const double v = fabs(A[(size_t)i * n + k]);
+    if (v > best) {
+      best = v;
+      bi = i;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) {
+      best = ov;
+      bi = oi;
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sv[wid] = best;
+    si[wid] = bi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = -1.0;
+    int p = k;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+      if (sv[w] > b || (sv[w] == b && si[w] < p)) {
+        b = sv[w];
+        p = si[w];
+      }
+    s_p = p;
+  }
+  __syncthreads();
+  const int p = s_p;
+  if (p != k)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const double ta = A[(size_t)k * n + j], tb = B[(size_t)k * n + j];
+      A[(size_t)k * n + j] = A[(size_t)p * n + j];
+      B[(size_t)k * n + j] = B[(size_t)p * n + j];
+      A[(size_t)p * n + j] = ta;
+      B[(size_t)p * n + j] = tb;
+    }
+  __syncthreads();
+  const double piv = A[(size_t)k * n + k];
+  const bool bad = !(fabs(piv) > 0.0) || !isfinite(piv);
+  __syncthreads();   // every thread has read the pivot before row k is scaled
+  if (bad) {
+    if (threadIdx.x == 0) *flag = 1.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) f[i] = 0.0;
+    return;
+  }
+  const double inv = 1.0 / piv;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    A[(size_t)k * n + j] *= inv;
+    B[(size_t)k * n + j] *= inv;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) f[i] = (i == k) ? 0.0 : A[(size_t)i * n + k];
+}
+
+// Gauss-Jordan step k, part 2: row_i -= f_i row_k for every i != k, over A's columns >= k
+// (the columns left of k are already those of the identity) and all of B's.
+__global__ void gj_eliminate_kernel(int n, int k, double* __restrict__ A, double* __restrict__ B,
+                                    const double* __restrict__ f) {
+  const int i = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == k || j >= 2 * n) return;
+  const double fi = f[i];
+  if (fi == 0.0) return;
+  if (j < n) {
+    if (j >= k) A[(size_t)i * n + j] -= fi * A[(size_t)k * n + j];
+  } else {
+    const int c = j - n;
+    B[(size_t)i * n + c] -= fi * B[(size_t)k * n + c];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_unit_vector(cudaStream_t s, int n, int i, double* v) {
+  unit_vector_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, i, v);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobian_column(cudaStream_t s, int n, int col, const double* w, double* A, double* B) {
+  jacobian_column_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, col, w, A, B);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_jordan(cudaStream_t s, int n, double* A, double* B, double* f, double* flag) {
+  if (n < 1 || n > 65535) return cudaErrorInvalidValue;
+  const dim3 grid((2 * n + 255) / 256, n);
+  for (int k = 0; k < n; ++k) {
+    gj_pivot_kernel<<<1, 1024, 0, s>>>(n, k, A, B, f, flag);
+    note_launch();
+    gj_eliminate_kernel<<<grid, 256, 0, s>>>(n, k, A, B, f);
+    note_launch();
+  }
+  return cudaGetLastError();
+}
+
+
+// ---- accumulated rank-1 kernel (one Sherman-Morrison update per step) ----
+
+namespace {
+
+__global__ void scaled_identity_kernel(int n, double a, double* __restrict__ M) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * n) return;
+  M[idx] = (idx / n == idx % n) ? a : 0.0;
+}
+
+// y_j = sum_i M_ij x_i (row-major n x n; one thread per column, coalesced over j)
+__global__ void gemv_t_kernel(int n, const double* __restrict__ M, const double* __restrict__ x,
+                              double* __restrict__ y) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double acc = 0.0;
+  for (int i = 0; i < n; ++i) acc += M[(size_t)i * n + j] * x[i];
+  y[j] = acc;
+}
+
+// v <- v / |v|; flag = 1 when |v| is positive and finite, else 0 (v untouched)
+__global__ void normalize_kernel(int n, double* __restrict__ v, double* __restrict__ flag) {
+  __shared__ double sh[32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += v[i] * v[i];
+  a = sqrt(block_sum(a, sh));
+  const bool ok = a > 0.0 && isfinite(a);
+  if (ok)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] /= a;
+  if (threadIdx.x == 0) *flag = ok ? 1.0 : 0.0;
+}
+
+// u = w - t;  out = 1 + v . Ku is formed later by dot1p_kernel
+__global__ void sub_kernel(int n, const double* __restrict__ w, const double* __restrict__ t, double* __restrict__ u) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) u[i] = w[i] - t[i];
+}
+
+__global__ void dot1p_kernel(int n, const double* __restrict__ a, const double* __restrict__ b,
+                             double* __restrict__ out) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += a[i] * b[i];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) *out = 1.0 + acc;
+}
+
+// J += u v^T;  K -= (K u)(v^T K) / (1 + v^T K u)
+__global__ void rank1_update_kernel(int n, const double* __restrict__ u, const double* __restrict__ v,
+                                    const double* __restrict__ Ku, const double* __restrict__ vK,
+                                    const double* __restrict__ denom, double* __restrict__ J, double* __restrict__ K) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * n) return;
+  const int i = (int)(idx / n), j = (int)(idx % n);
+  J[idx] += u[i] * v[j];
+  K[idx] -= Ku[i] * vK[j] / *denom;
+}
+
+inline unsigned blocks_for(size_t count) { return (unsigned)((count + 255) / 256); }
+
+}  // namespace
+
+cudaError_t launch_scaled_identity(cudaStream_t s, int n, double a, double* M) {
+  scaled_identity_kernel<<<blocks_for((size_t)n * n), 256, 0, s>>>(n, a, M);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemv_t(cudaStream_t s, int n, const double* M, const double* x, double* y) {
+  gemv_t_kernel<<<blocks_for(n), 256, 0, s>>>(n, M, x, y);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normalize(cudaStream_t s, int n, double* v, double* flag) {
+  normalize_kernel<<<1, 1024, 0, s>>>(n, v, flag);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub(cudaStream_t s, int n, const double* w, const double* t, double* u) {
+  sub_kernel<<<blocks_for(n), 256, 0, s>>>(n, w, t, u);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot1p(cudaStream_t s, int n, const double* a, const double* b, double* out) {
+  dot1p_kernel<<<1, 1024, 0, s>>>(n, a, b, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rank1_update(cudaStream_t s, int n, const double* u, const double* v, const double* Ku,
+                                const double* vK, const double* denom, double* J, double* K) {
+  rank1_update_kernel<<<blocks_for((size_t)n * n), 256, 0, s>>>(n, u, v, Ku, vK, denom, J, K);
+  note_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace xl

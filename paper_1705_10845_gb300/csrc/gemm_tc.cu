@@ -23,7 +23,9 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <mutex>
+#include <string>
 #include <unordered_map>
 
 #include "precision.h"
@@ -130,6 +132,65 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])),
+      "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])),
+      "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])),
+      "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])),
+      "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])),
+      "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Output tile of tile id: from the symmetric tile list, or the grouped raster (GROUP_M row
+// panels at a time, so that the CTAs in flight share their A and B panels in L2).  False for
+// a tile outside the matrix (a bad tile list), which is reported and never stored.
+__device__ __forceinline__ bool tile_coords(const TcArgs& a, int id, int& tm, int& tn) {
+  if (a.tile_list) {
+    tm = a.tile_list[2 * id];
+    tn = a.tile_list[2 * id + 1];
+  } else {
+    const int tiles_m = a.K / BM;
+    const int per_group = kGroupM * a.tiles_n;
+    const int g = id / per_group, r = id % per_group;
+    const int first = g * kGroupM;
+    const int gm = min(tiles_m - first, kGroupM);
+    tm = first + r % gm;
+    tn = r / gm;
+  }
+  return tm >= 0 && tm < a.K / BM && tn >= 0 && tn < a.tiles_n;
+}
+
+// L2 prefetch of the side inputs of tile (tm, tn) by the 128 epilogue threads (t = 0..127)
+template <int BN>
+__device__ __forceinline__ void prefetch_sides(const TcArgs& a, int tm, int tn, int t) {
+  const int r = tm * BM + t;
+  const float* fsides[2] = {a.E, a.E2};
+  for (int k = 0; k < 2; ++k)
+    if (fsides[k])
+      for (int rr = t; rr < BN; rr += 128)
+        for (int c = 0; c < BM; c += 32) prefetch_l2(fsides[k] + (size_t)(tn * BN + rr) * a.ldc + tm * BM + c);
+  if (a.E64) {
+    if (a.e64_trans) {
+      for (int rr = t; rr < BN; rr += 128)
+        for (int c = 0; c < BM; c += 16) prefetch_l2(a.E64 + (size_t)(tn * BN + rr) * a.ldc + tm * BM + c);
+    } else {
+      for (int c = 0; c < BN; c += 16) prefetch_l2(a.E64 + (size_t)r * a.ldc + tn * BN + c);
+    }
+  }
+}
+
 // a + b for a double-float a and a float b (Knuth two-sum, then renormalise)
 __device__ __forceinline__ float2 df_add(float2 a, float b) {
   const float s = a.x + b;
@@ -137,6 +198,97 @@ __device__ __forceinline__ float2 df_add(float2 a, float b) {
   const float err = (a.x - (s - bb)) + (b - bb) + a.y;
   const float hi = s + err;
   return make_float2(hi, err - (hi - s));
+}
+
+// Epilogue of one 32-column chunk: v holds this lane's row `row`, columns
+// col0 .. col0 + 31 of the raw accumulator sum; scales, adds the side inputs
+// and the diagonal, stores through the per-warp staging tiles tx, ty (32 x 33),
+// and raises vmax.
+__device__ __forceinline__ void epilogue_chunk(const TcArgs& a, float (&v)[32], int row, int row0, int col0,
+                                               int lane, float (*tx)[33], float (*ty)[33], float inv,
+                                               float& vmax) {
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] *= inv;
+  // FP32 side inputs of symmetric value, read transposed: for a fixed
+  // column the 32 lanes read 32 consecutive rows (coalesced)
+  if (a.E) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] += a.beta * a.E[(size_t)(col0 + i) * a.ldc + row];
+  }
+  if (a.E2) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] += a.beta2 * a.E2[(size_t)(col0 + i) * a.ldc + row];
+  }
+  const int dc = row - col0;   // diagonal column of this lane, if in the chunk
+  if (dc >= 0 && dc < 32) {
+    float dd = a.diag;
+    if (a.dvec && row < a.ndvec) dd += a.dvec_scale * (float)a.dvec[row];
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i == dc) v[i] += dd;
+  }
+  if (a.C64) {
+    // double-float value: exact leading term beta64 E64 plus the FP32 part
+    float hi[32], lo[32];
+    if (a.E64 && a.e64_trans) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const float2 e = a.E64[(size_t)(col0 + i) * a.ldc + row];
+        const float2 x = df_add(make_float2(a.beta64 * e.x, a.beta64 * e.y), v[i]);
+        hi[i] = x.x;
+        lo[i] = x.y;
+      }
+    } else if (a.E64) {
+#pragma unroll 8
+      for (int i = 0; i < 32; ++i) {
+        const float2 e = a.E64[(size_t)(row0 + i) * a.ldc + col0 + lane];
+        tx[i][lane] = e.x;
+        ty[i][lane] = e.y;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const float2 x = df_add(make_float2(a.beta64 * tx[lane][i], a.beta64 * ty[lane][i]), v[i]);
+        hi[i] = x.x;
+        lo[i] = x.y;
+      }
+      __syncwarp();
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        hi[i] = v[i];
+        lo[i] = 0.0f;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const int col = col0 + i;
+      if (!a.sym || col >= row) vmax = fmaxf(vmax, fabsf(hi[i]));
+      if (a.sym && col > row) a.C64[(size_t)col * a.ldc + row] = make_float2(hi[i], lo[i]);
+      tx[lane][i] = hi[i];
+      ty[lane][i] = lo[i];
+    }
+    __syncwarp();
+    for (int i = 0; i < 32; ++i) {
+      const int r = row0 + i, c = col0 + lane;
+      if (!a.sym || c >= r) a.C64[(size_t)r * a.ldc + c] = make_float2(tx[i][lane], ty[i][lane]);
+    }
+    __syncwarp();
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int col = col0 + i;
+    if (!a.sym || col >= row) vmax = fmaxf(vmax, fabsf(v[i]));
+    if (a.sym && col > row) a.C[(size_t)col * a.ldc + row] = v[i];
+    tx[lane][i] = v[i];
+  }
+  __syncwarp();
+  for (int i = 0; i < 32; ++i) {
+    const int r = row0 + i, c = col0 + lane;
+    if (!a.sym || c >= r) a.C[(size_t)r * a.ldc + c] = tx[i][lane];
+  }
+  __syncwarp();
 }
 
 template <int BN>
@@ -289,91 +441,207 @@ __global__ void __launch_bounds__(192, 1)
         }
         const int col0 = tn * BN + ch * 32;
         // this lane holds row `row`, columns col0 .. col0 + 31
-#pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] *= inv;
-        // FP32 side inputs of symmetric value, read transposed: for a fixed
-        // column the 32 lanes read 32 consecutive rows (coalesced)
-        if (a.E) {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] += a.beta * a.E[(size_t)(col0 + i) * a.ldc + row];
-        }
-        if (a.E2) {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] += a.beta2 * a.E2[(size_t)(col0 + i) * a.ldc + row];
-        }
-        const int dc = row - col0;   // diagonal column of this lane, if in the chunk
-        if (dc >= 0 && dc < 32) {
-          float dd = a.diag;
-          if (a.dvec && row < a.ndvec) dd += a.dvec_scale * (float)a.dvec[row];
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (i == dc) v[i] += dd;
-        }
-        if (a.C64) {
-          // double-float value: exact leading term beta64 E64 plus the FP32 part
-          float hi[32], lo[32];
-          if (a.E64 && a.e64_trans) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const float2 e = a.E64[(size_t)(col0 + i) * a.ldc + row];
-              const float2 x = df_add(make_float2(a.beta64 * e.x, a.beta64 * e.y), v[i]);
-              hi[i] = x.x;
-              lo[i] = x.y;
-            }
-          } else if (a.E64) {
-#pragma unroll 8
-            for (int i = 0; i < 32; ++i) {
-              const float2 e = a.E64[(size_t)(row0 + i) * a.ldc + col0 + lane];
-              tx[i][lane] = e.x;
-              ty[i][lane] = e.y;
-            }
-            __syncwarp();
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const float2 x = df_add(make_float2(a.beta64 * tx[lane][i], a.beta64 * ty[lane][i]), v[i]);
-              hi[i] = x.x;
-              lo[i] = x.y;
-            }
-            __syncwarp();
-          } else {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              hi[i] = v[i];
-              lo[i] = 0.0f;
-            }
-          }
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const int col = col0 + i;
-            if (!a.sym || col >= row) vmax = fmaxf(vmax, fabsf(hi[i]));
-            if (a.sym && col > row) a.C64[(size_t)col * a.ldc + row] = make_float2(hi[i], lo[i]);
-            tx[lane][i] = hi[i];
-            ty[lane][i] = lo[i];
-          }
-          __syncwarp();
-          for (int i = 0; i < 32; ++i) {
-            const int r = row0 + i, c = col0 + lane;
-            if (!a.sym || c >= r) a.C64[(size_t)r * a.ldc + c] = make_float2(tx[i][lane], ty[i][lane]);
-          }
-          __syncwarp();
-          continue;
-        }
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int col = col0 + i;
-          if (!a.sym || col >= row) vmax = fmaxf(vmax, fabsf(v[i]));
-          if (a.sym && col > row) a.C[(size_t)col * a.ldc + row] = v[i];
-          tx[lane][i] = v[i];
-        }
-        __syncwarp();
-        for (int i = 0; i < 32; ++i) {
-          const int r = row0 + i, c = col0 + lane;
-          if (!a.sym || c >= r) a.C[(size_t)r * a.ldc + c] = tx[i][lane];
-        }
-        __syncwarp();
+        epilogue_chunk(a, v, row, row0, col0, lane, tx, ty, inv, vmax);
       }
       for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
       if (lane == 0 && a.amax) atomicMax(a.amax, __float_as_uint(vmax));
+    }
+  }
+
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// Persistent variant: one CTA per SM walks the tiles id = blockIdx.x, blockIdx.x + gridDim.x, ...
+// The producer and MMA threads run ahead into the next tile while the epilogue drains the
+// previous one.  The three segments run in order (hi*hi over all K into accumulator 0, then
+// the two corrections into accumulator 1), so accumulator 0 is busy for the first third of a
+// tile only: the epilogue first folds accumulator 0 into accumulator 1 in tensor memory
+// (tcgen05.ld + tcgen05.st) and releases it, and the next tile's hi*hi third overlaps the rest
+// of the epilogue (side inputs, stores), which releases accumulator 1 before the next tile's
+// correction segments need it.  Barriers: full/empty (operand ring), acc_full (MMA -> epilogue,
+// one phase per tile), acc0_free and acc1_free (epilogue -> MMA, four warp arrivals per tile).
+// Every wait is bounded; a role that gives up records an error and raises a shared abort flag
+// that ends the other roles' loops.
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+    gemm_tc_persistent_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                              const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
+                              TcArgs a, int ntiles) {
+  constexpr int B_BYTES = BN * BK * 2;
+  constexpr uint32_t TMEM_COLS = 2 * BN;
+  constexpr int STAGE_TILE = 32 * 33 * 4;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  uint8_t* stage = sB + STAGES * B_BYTES;   // 4 warps x 2 staging tiles of the epilogue
+  uint64_t* full = reinterpret_cast<uint64_t*>(stage + 4 * 2 * STAGE_TILE);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc0_free = acc_full + 1;
+  uint64_t* acc1_free = acc_full + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 3);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0 && lane == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc0_free, 4);
+    mbar_init(acc1_free, 4);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  const int nk = a.K / BK;
+  const int total = a.nseg * nk;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (int id = blockIdx.x; id < ntiles && ok && !*abort_flag; id += gridDim.x) {
+        int tm, tn;
+        if (!tile_coords(a, id, tm, tn)) {
+          atomicExch(a.err, 4);
+          *abort_flag = 1;
+          break;
+        }
+        for (int kb = 0; kb < total; ++kb, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (g / STAGES) & 1;
+          if (g >= STAGES && !mbar_wait(&empty[s], ph ^ 1)) {
+            atomicExch(a.err, 1);
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+          const int seg = kb / nk, kk = (kb % nk) * BK;
+          const CUtensorMap* ma = (seg == 2) ? &mAlo : &mAhi;
+          const CUtensorMap* mb = (seg == 1) ? &mBlo : &mBhi;
+          tma_load_2d(sA + s * A_BYTES, ma, kk, tm * BM, &full[s]);
+          tma_load_2d(sB + s * B_BYTES, mb, kk, tn * BN, &full[s]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc_f16 = instr_desc(BN, 0);
+      constexpr uint32_t idesc_bf16 = instr_desc(BN, 1);
+      const uint32_t idesc = a.bf16 ? idesc_bf16 : idesc_f16;
+      uint32_t g = 0;
+      int it = 0;
+      for (int id = blockIdx.x; id < ntiles && !*abort_flag; id += gridDim.x, ++it) {
+        int tm, tn;
+        if (!tile_coords(a, id, tm, tn)) break;
+        bool ok = true;
+        for (int kb = 0; kb < total; ++kb, ++g) {
+          // the previous tile's epilogue must have released the accumulator this segment writes
+          if (it > 0 && (kb == 0 || kb == nk)) {
+            if (!mbar_wait(kb == 0 ? acc0_free : acc1_free, (uint32_t)((it - 1) & 1)) || *abort_flag) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          }
+          const int s = g % STAGES;
+          const uint32_t ph = (g / STAGES) & 1;
+          if (!mbar_wait(&full[s], ph)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const bool corr = kb >= nk;
+          const uint32_t dcol = corr ? (uint32_t)BN : 0u;
+          const bool first = (kb == 0) || (kb == nk);
+#pragma unroll
+          for (int j = 0; j < BK / 16; ++j) {
+            const uint64_t ad = smem_desc(sA + s * A_BYTES + j * 32);
+            const uint64_t bd = smem_desc(sB + s * B_BYTES + j * 32);
+            mma_f16(tmem + dcol, ad, bd, idesc, (first && j == 0) ? 0u : 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (!ok) {
+          atomicExch(a.err, 2);
+          *abort_flag = 1;
+          break;
+        }
+        mma_commit(acc_full);
+      }
+    }
+  } else {
+    // epilogue warps 2..5: TMEM lanes 32 * (warp % 4) ..
+    const int q = warp & 3;
+    float(*tx)[33] = reinterpret_cast<float(*)[33]>(stage + q * 2 * STAGE_TILE);
+    float(*ty)[33] = reinterpret_cast<float(*)[33]>(stage + q * 2 * STAGE_TILE + STAGE_TILE);
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const float inv = a.alpha / (__ldg(a.sa) * __ldg(a.sb));
+    int it = 0;
+    for (int id = blockIdx.x; id < ntiles && !*abort_flag; id += gridDim.x, ++it) {
+      int tm, tn;
+      if (!tile_coords(a, id, tm, tn)) break;
+      prefetch_sides<BN>(a, tm, tn, (warp - 2) * 32 + lane);
+      const bool got = mbar_wait(acc_full, (uint32_t)(it & 1));
+      if (!__all_sync(0xffffffffu, got) || *abort_flag) {
+        if (lane == 0) atomicExch(a.err, 3);
+        *abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // pass 1: accumulator 1 <- accumulator 0 + accumulator 1, then release accumulator 0
+      if (a.nseg > 1) {
+        for (int ch = 0; ch < BN / 32; ++ch) {
+          float v[32], w[32];
+          tmem_ld32(tmem + lane_base + (uint32_t)(ch * 32), v);
+          tmem_ld32(tmem + lane_base + (uint32_t)(BN + ch * 32), w);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] += w[i];
+          tmem_st32(tmem + lane_base + (uint32_t)(BN + ch * 32), v);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc0_free);
+      }
+      // pass 2: the epilogue proper from the summed accumulator
+      const uint32_t src = a.nseg > 1 ? (uint32_t)BN : 0u;
+      const int row0 = tm * BM + q * 32;
+      const int row = row0 + lane;
+      float vmax = 0.0f;
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        float v[32];
+        tmem_ld32(tmem + lane_base + src + (uint32_t)(ch * 32), v);
+        epilogue_chunk(a, v, row, row0, tn * BN + ch * 32, lane, tx, ty, inv, vmax);
+      }
+      for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+      if (lane == 0 && a.amax) atomicMax(a.amax, __float_as_uint(vmax));
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        if (a.nseg == 1) mbar_arrive(acc0_free);
+        mbar_arrive(acc1_free);
+      }
     }
   }
 
@@ -447,6 +715,35 @@ int smem_bytes() {
   return STAGES * (A_BYTES + BN * BK * 2) + (2 * STAGES + 1) * 8 + 16 + 1024;
 }
 
+template <int BN>
+int smem_bytes_persistent() {
+  return STAGES * (A_BYTES + BN * BK * 2) + 4 * 2 * 32 * 33 * 4 + (2 * STAGES + 3) * 8 + 16 + 1024;
+}
+
+// 1: persistent CTAs (default); 0: one CTA per output tile (XLBOMD_GEMM=classic).
+int tc_variant() {
+  static int v = -1;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const char* e = std::getenv("XLBOMD_GEMM");
+    v = (e && std::string(e) == "classic") ? 0 : 1;
+  });
+  return v;
+}
+
+int sm_count() {
+  static int n = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 0;
+  });
+  return n > 0 ? n : 148;
+}
+
+
 }  // namespace
 
 void tc_forget_maps(const void* base) {
@@ -478,6 +775,30 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
   } else {
     args.tile_list = nullptr;
     nblocks = (n / BM) * (n / bn);
+  }
+  if (tc_variant() == 1) {
+    const int grid = std::min(nblocks, sm_count());
+    if (wide) {
+      static std::once_flag once;
+      static cudaError_t attr = cudaSuccess;
+      const int sb = smem_bytes_persistent<256>();
+      std::call_once(once, [&] {
+        attr = cudaFuncSetAttribute(gemm_tc_persistent_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+      });
+      if (attr != cudaSuccess) return attr;
+      gemm_tc_persistent_kernel<256><<<grid, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, args, nblocks);
+    } else {
+      static std::once_flag once;
+      static cudaError_t attr = cudaSuccess;
+      const int sb = smem_bytes_persistent<128>();
+      std::call_once(once, [&] {
+        attr = cudaFuncSetAttribute(gemm_tc_persistent_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+      });
+      if (attr != cudaSuccess) return attr;
+      gemm_tc_persistent_kernel<128><<<grid, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, args, nblocks);
+    }
+    note_launch();
+    return cudaGetLastError();
   }
   if (wide) {
     static std::once_flag once;

@@ -153,6 +153,22 @@ cudaError_t launch_absmax(cudaStream_t s, int n, const double* x, double* out);
 cudaError_t launch_fill_history(cudaStream_t s, int nat, int kmax, double* nh);
 cudaError_t launch_axpy(cudaStream_t s, int n, double a, const double* x, double* y);
 cudaError_t launch_diag_sum(cudaStream_t s, int n, int np, const double* X, double* out);
+// exact kernel (foe_kernels.cu): v = e_i; column col of J - I from w (and of B = I);
+// B <- (A)^-1 B by Gauss-Jordan with partial pivoting (A row-major n x n, destroyed;
+// f: n doubles of work; *flag set to 1 on a zero or non-finite pivot)
+cudaError_t launch_unit_vector(cudaStream_t s, int n, int i, double* v);
+cudaError_t launch_jacobian_column(cudaStream_t s, int n, int col, const double* w, double* A, double* B);
+cudaError_t launch_gauss_jordan(cudaStream_t s, int n, double* A, double* B, double* f, double* flag);
+// accumulated rank-1 kernel (foe_kernels.cu), row-major n x n FP64 matrices:
+// M = a I; y = M^T x; v <- v/|v| (flag 1 if |v| > 0); u = w - t; out = 1 + a.b;
+// J += u v^T and K -= Ku vK^T / denom
+cudaError_t launch_scaled_identity(cudaStream_t s, int n, double a, double* M);
+cudaError_t launch_gemv_t(cudaStream_t s, int n, const double* M, const double* x, double* y);
+cudaError_t launch_normalize(cudaStream_t s, int n, double* v, double* flag);
+cudaError_t launch_sub(cudaStream_t s, int n, const double* w, const double* t, double* u);
+cudaError_t launch_dot1p(cudaStream_t s, int n, const double* a, const double* b, double* out);
+cudaError_t launch_rank1_update(cudaStream_t s, int n, const double* u, const double* v, const double* Ku,
+                                const double* vK, const double* denom, double* J, double* K);
 cudaError_t launch_density_out_f64(cudaStream_t s, int N, int np, const double* Tn, const double* Tmu, double dmu,
                                    double* ddiag, double* D);
 

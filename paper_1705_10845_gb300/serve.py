@@ -36,6 +36,19 @@ def squarings_for(Te: float, width_ev: float = 40.0) -> int:
     return max(10, int(math.ceil(math.log2(beta * width_ev / 0.1))) - 1)
 
 
+def work_estimate(natoms: int, n_sq: int, steps: int) -> float:
+    """Relative device work of a job: the expansion and response products cost n_sq np^3 per
+    step; small systems are bound by launch latency (a floor of about a 512-orbital step)."""
+    np_ = (4 * natoms + 127) // 128 * 128
+    return float(steps) * n_sq * max(np_, 512) ** 3
+
+
+def stream_priority(natoms: int) -> int:
+    """CUDA stream priority by size class (lower is served first): the short kernels of small
+    systems are dispatched ahead of the long products of large ones."""
+    return -2 if natoms <= 256 else (-1 if natoms <= 1024 else 0)
+
+
 def bytes_estimate(natoms: int, n_sq: int, prec: str = "fp16x3") -> int:
     """Device memory of one context (expansion matrices dominate)."""
     np_ = (4 * natoms + 127) // 128 * 128
@@ -81,10 +94,18 @@ def make_context(X, job: Job, stream_ptr: int):
 
 
 class Scheduler:
-    """Admission by device memory plus a worker pool that steps the admitted jobs."""
+    """Admission by device memory plus a worker pool that steps the admitted jobs.
+
+    policy "sjf": among the jobs that have arrived, the one with the least estimated work is
+    admitted first (shortest job first, which minimises the mean time in the system of an
+    overloaded server); "fifo": in arrival order.
+    """
 
     def __init__(self, X, budget_bytes: int, workers: int, make_ctx=make_context, clock=time.perf_counter,
-                 keep_results: bool = False):
+                 keep_results: bool = False, policy: str = "fifo"):
+        if policy not in ("fifo", "sjf"):
+            raise ValueError(f"unknown admission policy {policy!r}")
+        self.policy = policy
         self.X = X
         self.keep_results = keep_results
         self.budget = budget_bytes
@@ -93,7 +114,8 @@ class Scheduler:
         self.make_ctx = make_ctx
         self.clock = clock
         self.lock = threading.Lock()
-        self.pending: list[tuple] = []        # heap of (arrival, jid, job)
+        self.pending: list[tuple] = []        # heap of (arrival, jid, job): not yet arrived
+        self.ready: list[tuple] = []          # heap of (key, jid, job): arrived, waiting for memory
         self.active: list[list[Job]] = [[] for _ in range(workers)]
         self.finished: list[Job] = []
         self.rejected: list[Job] = []
@@ -107,17 +129,26 @@ class Scheduler:
                 return
             heapq.heappush(self.pending, (job.arrival, job.jid, job))
 
-    def _admit(self, w: int, now: float):
-        """Admit arrived jobs that fit, into worker w's slice (least loaded first)."""
+    def _key(self, job: Job):
+        if self.policy == "sjf":
+            return (work_estimate(job.natoms, squarings_for(job.Te), job.steps), job.arrival)
+        return (job.arrival,)
+
+    def _admit(self, now: float):
+        """Reserve memory for the first ready job if it fits the budget."""
         with self.lock:
-            if not self.pending or self.pending[0][0] > now:
+            while self.pending and self.pending[0][0] <= now:
+                _, jid, job = heapq.heappop(self.pending)
+                heapq.heappush(self.ready, (self._key(job), jid, job))
+            if not self.ready:
                 return None
-            job = self.pending[0][2]
+            job = self.ready[0][2]
             if self.used + job.mem > self.budget:
                 return None
-            heapq.heappop(self.pending)
+            heapq.heappop(self.ready)
             self.used += job.mem
             self.peak_used = max(getattr(self, "peak_used", 0), self.used)
+            job.admitted = now
         return job
 
     def _release(self, job: Job):
@@ -125,37 +156,73 @@ class Scheduler:
             self.used -= job.mem
             self.finished.append(job)
 
-    def run(self, until: float | None = None, stream_factory=None):
-        """Run until every submitted job finished (or the clock passes `until`)."""
-        t0 = self.clock()
-        stop = threading.Event()
+    def run(self, until: float | None = None, stream_factory=None, admitters: int = 4):
+        """Run until every submitted job finished (or the clock passes `until`).
 
-        def worker(w: int):
-            stream = stream_factory() if stream_factory else None
-            mine = self.active[w]
-            while not stop.is_set():
-                now = self.clock() - t0
-                if until is not None and now > until:
-                    break
-                # only the least-loaded workers admit, so that the jobs spread out
-                job = None
-                if len(mine) <= min(len(a) for a in self.active):
-                    job = self._admit(w, now)
-                if job is not None:
+        Admission threads build each job's context (upload and t0 SCF) on the job's own stream
+        and hand it to the stepping worker with the least per-step work; stepping workers only
+        advance their jobs, so a long SCF never stalls running trajectories.
+        """
+        t0 = self.clock()
+        inbox: list[list[Job]] = [[] for _ in range(self.workers)]
+        load = [0.0] * self.workers
+        alive = [admitters]
+
+        def timed_out():
+            return until is not None and self.clock() - t0 > until
+
+        def step_work(job):
+            return work_estimate(job.natoms, squarings_for(job.Te), 1)
+
+        def admitter():
+            try:
+                while not timed_out():
+                    job = self._admit(self.clock() - t0)
+                    if job is None:
+                        with self.lock:
+                            if not self.pending and not self.ready:
+                                return
+                        time.sleep(0.001)
+                        continue
                     try:
-                        job.stream = stream
-                        job.ctx = self.make_ctx(self.X, job, stream.cuda_stream if stream is not None else 0)
-                        job.admitted = self.clock() - t0
-                        mine.append(job)
+                        job.stream = stream_factory(job) if stream_factory else None
+                        job.ctx = self.make_ctx(self.X, job, job.stream.cuda_stream if job.stream is not None else 0)
                     except Exception as e:   # admission failure: report and free the reservation
                         job.error = f"job {job.jid} ({job.natoms} atoms, Te {job.Te:.0f} K): {e}"
                         self._release(job)
-                    continue
-                if not mine:
+                        continue
                     with self.lock:
-                        empty = not self.pending
-                    if empty and all(not a for a in self.active):
-                        break
+                        w = min(range(self.workers), key=lambda i: load[i])
+                        load[w] += step_work(job)
+                        inbox[w].append(job)
+            finally:
+                with self.lock:
+                    alive[0] -= 1
+
+        def finish(w, job, mine):
+            job.finished = self.clock() - t0
+            if self.keep_results and not job.error:
+                job.result = {"q": job.ctx.get(0, self.X.Q), "R": job.ctx.get(0, self.X.R)}
+            try:
+                job.ctx.close()
+            except Exception:
+                pass
+            job.ctx = None
+            mine[:] = [j for j in mine if j is not job]
+            with self.lock:
+                load[w] -= step_work(job)
+            self._release(job)
+
+        def worker(w: int):
+            mine = self.active[w]
+            while not timed_out():
+                with self.lock:
+                    mine.extend(inbox[w])
+                    inbox[w].clear()
+                    idle_done = alive[0] == 0
+                if not mine:
+                    if idle_done:
+                        return
                     time.sleep(0.001)
                     continue
                 for job in list(mine):
@@ -167,25 +234,19 @@ class Scheduler:
                     job.lat.append(self.clock() - t)
                     job.done_steps += 1
                     if job.error or job.done_steps >= job.steps:
-                        job.finished = self.clock() - t0
-                        if self.keep_results and not job.error:
-                            job.result = {"q": job.ctx.get(0, self.X.Q), "R": job.ctx.get(0, self.X.R)}
-                        try:
-                            job.ctx.close()
-                        except Exception:
-                            pass
-                        job.ctx = None
-                        mine.remove(job)
-                        self._release(job)
+                        finish(w, job, mine)
 
-        threads = [threading.Thread(target=worker, args=(w,), daemon=True) for w in range(self.workers)]
+        threads = [threading.Thread(target=admitter, daemon=True) for _ in range(admitters)]
+        threads += [threading.Thread(target=worker, args=(w,), daemon=True) for w in range(self.workers)]
         for t in threads:
             t.start()
         for t in threads:
             t.join()
-        stop.set()
         wall = self.clock() - t0
-        for a in self.active:          # jobs still running when the window closed
+        for w in range(self.workers):      # contexts built but never stepped count as admitted
+            self.active[w].extend(inbox[w])
+            inbox[w].clear()
+        for a in self.active:              # jobs still running when the window closed
             for job in a:
                 if job.ctx is not None:
                     try:
@@ -197,12 +258,16 @@ class Scheduler:
 
 
 def summarize(sched: Scheduler, wall: float):
-    lat = [x for j in sched.finished for x in j.lat]
-    steps = sum(j.done_steps for j in sched.finished) + sum(j.done_steps for a in sched.active for j in a)
+    """Throughput and per-step latency over every admitted job (finished or still running)."""
+    admitted = list(sched.finished) + [j for a in sched.active for j in a]
+    lat = [x for j in admitted for x in j.lat]
+    steps = sum(j.done_steps for j in admitted)
     out = {"steps_per_s": steps / wall if wall > 0 else None, "total_steps": steps, "wall_s": wall,
+           "atom_steps_per_s": sum(j.done_steps * j.natoms for j in admitted) / wall if wall > 0 else None,
+           "jobs_admitted": len(admitted),
            "jobs_finished": sum(1 for j in sched.finished if not j.error and j.done_steps >= j.steps),
            "jobs_failed": [j.error for j in sched.finished if j.error][:5],
-           "jobs_pending": len(sched.pending), "jobs_rejected": len(sched.rejected)}
+           "jobs_pending": len(sched.pending) + len(sched.ready), "jobs_rejected": len(sched.rejected)}
     if lat:
         a = np.array(lat) * 1000.0
         out.update({"step_latency_ms_p50": float(np.percentile(a, 50)),
@@ -223,6 +288,8 @@ def main(argv=None):
     ap.add_argument("--budget-gb", type=float, default=None)
     ap.add_argument("--prec", default="fp16x3")
     ap.add_argument("--seed", type=int, default=1705)
+    ap.add_argument("--policy", choices=["sjf", "fifo"], default="sjf", help="admission order of arrived jobs")
+    ap.add_argument("--no-priority", action="store_true", help="all streams at the default priority")
     a = ap.parse_args(argv)
 
     sys.path.insert(0, ROOT)
@@ -234,7 +301,7 @@ def main(argv=None):
     free, _ = torch.cuda.mem_get_info()
     budget = int(a.budget_gb * 2**30) if a.budget_gb else int(free * 0.85)
     rng = np.random.default_rng(a.seed)
-    sched = Scheduler(X, budget, a.workers)
+    sched = Scheduler(X, budget, a.workers, policy=a.policy)
     t = 0.0
     for i in range(a.jobs):
         nat = int(round(math.exp(rng.uniform(math.log(a.min_atoms), math.log(a.max_atoms)))))
@@ -249,7 +316,8 @@ def main(argv=None):
                          seed=a.seed + i, prec=a.prec))
     l0 = X.binding.launch_count()
     wall = sched.run(until=(a.duration + 60.0) if a.mode == "serve" else None,
-                     stream_factory=lambda: torch.cuda.Stream())
+                     stream_factory=lambda job: torch.cuda.Stream(
+                         priority=0 if a.no_priority else stream_priority(job.natoms)))
     sync_error = ""
     try:
         torch.cuda.synchronize()
@@ -258,7 +326,8 @@ def main(argv=None):
     res = summarize(sched, wall)
     if sync_error:
         res["sync_error"] = sync_error
-    res.update({"mode": a.mode, "workers": a.workers, "prec": a.prec, "budget_gb": budget / 2**30,
+    res.update({"mode": a.mode, "policy": a.policy, "stream_priority": not a.no_priority, "workers": a.workers,
+                "prec": a.prec, "budget_gb": budget / 2**30,
                 "atoms_range": [a.min_atoms, a.max_atoms], "steps_per_job": a.steps,
                 "gpu_launches": X.binding.launch_count() - l0})
     print(json.dumps(res), flush=True)

@@ -247,15 +247,18 @@ def test_exact_kernel_matches_oracle(X, name, make):
     assert np.max(np.abs(Kr - Kref @ ev.r)) < 1e-10
 
 
-@pytest.mark.parametrize("variant", ["exact_every5", "delta", "kmax6", "kmax7"])
+@pytest.mark.parametrize("variant", ["exact_every5", "accumulated", "delta", "kmax6", "kmax7"])
 def test_kernel_and_dissipation_variants_follow_oracle(X, variant):
-    # the exact kernel held and recomputed every 5 steps (Section VI.A), K = K_0
-    # only (rank 0), and the K_max = 6, 7 rows of Table I (the library's table
-    # against the oracle's, typed independently)
+    # the exact kernel held and recomputed every 5 steps (Section VI.A), the
+    # accumulated rank-1 kernel (end of Section V.F), K = K_0 only (rank 0), and
+    # the K_max = 6, 7 rows of Table I (the library's table against the
+    # oracle's, typed independently)
     s = synth.make_system(24, 1705, L=7.0)
     kw, xlkw = {}, {}
     if variant == "exact_every5":
         kw, xlkw = dict(kernel_mode=1, kernel_every=5), dict(kernel_mode="exact", kernel_every=5)
+    elif variant == "accumulated":
+        kw, xlkw = dict(kernel_mode=2), dict(kernel_mode="accumulated")
     elif variant == "delta":
         kw, xlkw = dict(rank_m=0), dict(rank_m=0)
     else:
