@@ -74,6 +74,8 @@ class Model:
     r_taper: float = 4.5                    # taper starts here (A)
     hubbard_U: float = 6.0                  # eV
     coulomb_k: float = 14.399645            # eV A
+    rep_A: float = 0.0                      # pair repulsion A exp(-r/rho) S(r) (eV); 0 = off
+    rep_rho: float = 0.3                    # A
     Te: float = 1000.0                      # K
     n_sq: int = 10                          # squarings of the recursive expansion
 
@@ -589,11 +591,29 @@ def kernel_exact(dens: Density, gamma):
 # Energy and forces (Section IV.B-IV.C, Eq. EqMotFT)
 # --------------------------------------------------------------------------
 
-def free_energy(H0, gamma, dens: Density, q, n):
+def repulsion(R, L, model: Model):
+    """Pair repulsion E_rep = 1/2 sum over ordered image pairs of A exp(-r/rho) S(r), with the
+    hoppings' taper S; returns (E_rep, dE_rep/dR (N_at x 3)).  Zero when rep_A = 0."""
+    R = np.asarray(R, dtype=float)
+    g = np.zeros_like(R)
+    if model.rep_A == 0.0:
+        return 0.0, g
+    I, J, d = image_pairs(R, L, model.r_cut)
+    r = np.sqrt(np.sum(d * d, axis=1))
+    S, dS = taper(r, model.r_taper, model.r_cut)
+    e = model.rep_A * np.exp(-r / model.rep_rho)
+    de = e * (dS - S / model.rep_rho)                # d(e S)/dr
+    u = (0.5 * de / r)[:, None] * d                  # d/d(R_J) of half the pair term
+    np.add.at(g, J, u)
+    np.add.at(g, I, -u)
+    return 0.5 * float(np.sum(e * S)), g
+
+
+def free_energy(H0, gamma, dens: Density, q, n, e_rep=0.0):
     """Shadow free energy Omega[n](R) of the SCC-TB model.
 
     Omega = 2 Tr[D H0] + 1/2 sum_IJ (2 q_I - n_I) gamma_IJ n_J
-            - 2 kB Te sum_i s(f_i).
+            - 2 kB Te sum_i s(f_i) + E_rep.
     Returns (Omega, parts dict).
     """
     n = np.asarray(n, dtype=float)
@@ -601,7 +621,7 @@ def free_energy(H0, gamma, dens: Density, q, n):
     coul = 0.5 * np.dot(2.0 * q - n, gamma @ n)
     S = float(np.sum(entropy_terms(dens)))
     ent = -2.0 * S / dens.beta
-    return band + coul + ent, dict(band=band, coulomb=coul, entropy=ent, S=S)
+    return band + coul + ent + e_rep, dict(band=band, coulomb=coul, entropy=ent, S=S, repulsion=e_rep)
 
 
 def forces(R, L, model: Model, D, q, n, gamma_grad=None):
@@ -631,6 +651,7 @@ def forces(R, L, model: Model, D, q, n, gamma_grad=None):
     t = w[..., None] * gamma_grad                   # contributes +t to R_J, -t to R_I
     dO += t.sum(axis=0)
     dO -= t.sum(axis=1)
+    dO += repulsion(R, L, model)[1]
     return -dO
 
 
@@ -668,7 +689,7 @@ def evaluate(R, L, Z, n, model: Model, xl: XLParams | None = None, with_kernel=T
     q = mulliken(dens.D, Z)
     r = q - n
     F = forces(R, L, model, dens.D, q, n) if with_forces else None
-    Om, parts = free_energy(H0, gam, dens, q, n)
+    Om, parts = free_energy(H0, gam, dens, q, n, repulsion(R, L, model)[0])
     ev = Evaluation(H0=H0, gamma=gam, H=H, dens=dens, q=q, r=r, F=F, Omega=Om, parts=parts)
     if with_kernel and xl is not None:
         P, gmu = divided_differences(dens)

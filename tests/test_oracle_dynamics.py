@@ -157,3 +157,36 @@ def test_residual_and_energy_fluctuations_scale_as_dt_squared():
         fluct.append(np.std(E))
     for a, b in ((res[0], res[1]), (res[1], res[2]), (fluct[0], fluct[1]), (fluct[1], fluct[2])):
         assert 3.0 < a / b < 5.5, (res, fluct)
+
+
+def test_pair_repulsion_forces_and_energy():
+    # the optional pair term: its forces are minus the finite-difference gradient
+    # of Omega, pairwise (sum F = 0), zero at rep_A = 0, and the dimer value is
+    # A exp(-r/rho) inside the taper
+    s = synth.make_system(8, 42, L=7.0)
+    mr = O.Model(n_sq=20, rep_A=40.0, rep_rho=0.3)
+    e0, g0 = O.repulsion(s.R, s.L, O.Model())
+    assert e0 == 0.0 and not np.any(g0)
+    e, g = O.repulsion(s.R, s.L, mr)
+    assert np.max(np.abs(g.sum(axis=0))) < 1e-12
+    h = 1e-6
+    for I in (0, 5):
+        for c in range(3):
+            Rp, Rm = s.R.copy(), s.R.copy()
+            Rp[I, c] += h
+            Rm[I, c] -= h
+            fd = (O.repulsion(Rp, s.L, mr)[0] - O.repulsion(Rm, s.L, mr)[0]) / (2 * h)
+            assert abs(fd - g[I, c]) < 1e-7
+    R2 = np.array([[1.0, 1.0, 1.0], [2.5, 1.0, 1.0]])
+    assert abs(O.repulsion(R2, 12.0, mr)[0] - 40.0 * np.exp(-1.5 / 0.3)) < 1e-14
+    # the full force with the pair term against finite differences of Omega at fixed n
+    rng = np.random.default_rng(4)
+    n = rng.normal(scale=0.05, size=8)
+    n -= n.mean()
+    ev = O.evaluate(s.R, s.L, s.Z, n, mr, None, with_kernel=False)
+    for I, c in ((1, 0), (6, 2)):
+        Rp, Rm = s.R.copy(), s.R.copy()
+        Rp[I, c] += 1e-5
+        Rm[I, c] -= 1e-5
+        fd = (omega_at(Rp, s.L, s.Z, n, mr) - omega_at(Rm, s.L, s.Z, n, mr)) / 2e-5
+        assert abs(ev.F[I, c] + fd) < 1e-6
