@@ -30,9 +30,13 @@ if ROOT not in sys.path:
 
 METRIC = "XL-BOMD steps/s and FOE TFLOP/s vs peak, mixed vs FP64 GPU at |dq|<=1e-5 e"
 ALPHA_MIX = 0.06
-# DRAM bytes (read + write) of one dense n = 6144 launch of the product kernel,
-# from the ncu capture summarised in profiles/gemm_tc_fp16x3_n6144.md
-GEMM_TRAFFIC_N6144 = 1.211e9 + 0.142e9
+# DRAM bytes (read + write) of one dense n = 6144 launch of each product-kernel variant, from
+# the ncu captures summarised in profiles/ (None: not captured since the kernel last changed)
+GEMM_TRAFFIC_N6144 = {"classic": 1.211e9 + 0.142e9, "persistent": None}
+
+
+def gemm_variant():
+    return "classic" if os.environ.get("XLBOMD_GEMM") == "classic" else "persistent"
 
 
 def parse():
@@ -46,6 +50,10 @@ def parse():
     ap.add_argument("--Te", type=float, default=1500.0)
     ap.add_argument("--nsq", type=int, default=14)
     ap.add_argument("--rank", type=int, default=4)
+    ap.add_argument("--kernel-prec", type=int, default=0, choices=[0, 1],
+                    help="1: the kernel's probe chains take one 16-bit product instead of three")
+    ap.add_argument("--rep-A", type=float, default=40.0,
+                    help="pair repulsion A exp(-r/0.3 A) (eV): the model's atoms collapse without it in long runs")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=0,
@@ -70,6 +78,8 @@ def workload_config(a, parallel):
         "workload": f"XL-BOMD, {a.natoms} carbon-like atoms (N = {4 * a.natoms} orbitals), orthogonal SCC-TB, "
                     f"Te = {a.Te:g} K, {a.nsq} squarings, rank-{a.rank} kernel, dt = 0.25 fs",
         "natoms": a.natoms, "n_orb": 4 * a.natoms, "Te_K": a.Te, "n_squarings": a.nsq, "rank_m": a.rank,
+        "pair_repulsion": f"{a.rep_A:g} exp(-r/0.3 A) eV" if a.rep_A else "off",
+        "kernel_probe_products": "one 16-bit product" if a.kernel_prec else "three (full split)",
         "prec": a.prec, "parallelism": parallel,
         "l2": "inputs larger than L2: about 11 GB of expansion matrices are rewritten every step",
     }
@@ -139,6 +149,7 @@ def peaks():
 
 def make_params(X, a, prec):
     return X.default_params(Te=a.Te, n_sq=a.nsq, rank_m=a.rank, dt=0.25, mix_alpha=ALPHA_MIX,
+                            rep_A=a.rep_A, rep_rho=0.3, kernel_prec=a.kernel_prec,
                             kernel_c=1.0 - 1.0 / ALPHA_MIX, prec=prec,
                             scf_tol=1e-10 if prec == "fp64" else 1e-5, scf_mode=1, kernel_auto=1,
                             mu_tol=1e-9 if prec == "fp64" else 1e-3, scf_max_iter=200)
@@ -194,7 +205,7 @@ def run_trajectory_study(a, X, ctx, s):
     run, so at every K-th step the oracle evaluates the GPU's own (R, n) state."""
     import numpy as np
     import oracle as O
-    m = O.Model(Te=a.Te, n_sq=a.nsq)
+    m = O.Model(Te=a.Te, n_sq=a.nsq, rep_A=a.rep_A, rep_rho=0.3)
     t = time.perf_counter()
     ctx.scf(0)
     t_scf = time.perf_counter() - t
@@ -268,7 +279,8 @@ def run_precision_study(a, X, ctx, s, sysd, stream):
         c.close()
         rows.append(row)
     t = time.perf_counter()
-    ev = O.evaluate(R, s.L, s.Z, n, O.Model(Te=a.Te, n_sq=a.nsq), None, with_kernel=False)
+    ev = O.evaluate(R, s.L, s.Z, n, O.Model(Te=a.Te, n_sq=a.nsq, rep_A=a.rep_A, rep_rho=0.3), None,
+                    with_kernel=False)
     t_or = time.perf_counter() - t
     out = {"study": "precision", "natoms": s.natoms, "n_orbitals": 4 * s.natoms, "Te": a.Te, "n_sq": a.nsq,
            "rank_m": a.rank, "scf_s": t_scf, "oracle_eval_s": t_or, "md_steps_timed": a.steps, "results": []}
@@ -447,13 +459,14 @@ def main():
         "dtype": a.prec, "data": "synthetic", "config": workload_config(a, f"replicas x{ws}"),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None,
-                     "traffic": GEMM_TRAFFIC_N6144 if (a.natoms == 1536 and a.prec == "fp16x3") else None,
+                     "traffic": GEMM_TRAFFIC_N6144[gemm_variant()] if (a.natoms == 1536 and a.prec == "fp16x3")
+                     else None,
                      "traffic_note": "bytes per dense n = 6144 launch (ncu); algorithmic 0.453 GB",
-                     "kernel": "gemm_tc_kernel (split-precision tcgen05 product)",
+                     "kernel": f"gemm_tc {gemm_variant()} kernel (split-precision tcgen05 product)",
                      "note": f"algorithmic 2n^3 per product (n^3 when symmetric-output) over CUDA-event time of "
                              f"{int(gemm_launches)} launches; each split product runs 3 half-precision "
-                             f"tensor products, so tensor-pipe work is 3x the algorithmic flops; peak = "
-                             f"{src} sustained bf16"},
+                             f"tensor products ({'1 in the probe chains' if a.kernel_prec else 'also in the probe chains'}), "
+                             f"so tensor-pipe work is up to 3x the algorithmic flops; peak = {src} sustained bf16"},
         "foe_tflops": (gemm_flops / sec / 1e12) if sec > 0 else None,
         "gemm_time_share": (gemm_ms / ms) if ms > 0 else None,
         "per_step": {"mu_passes": units[0] / a.steps, "products": units[3] / a.steps,

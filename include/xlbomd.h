@@ -103,6 +103,17 @@ typedef struct {
                               J_0 = c I without an update (end of Section V.F) */
   int kernel_every;        /* kernel_mode 1: recompute K every this many MD steps
                               (0: keep the kernel of the t0 state) */
+  double rep_A;            /* optional pair repulsion rep_A exp(-r/rep_rho) S(r) over the image
+                              pairs within r_cut, S the hoppings' taper (eV; 0 = off, the
+                              default).  The model has no repulsive term otherwise, and its
+                              atoms fall into each other within a few hundred steps */
+  double rep_rho;          /* its decay length (A) */
+  int kernel_prec;         /* split precisions: 0 = the kernel's response chains (probes, the
+                              stiffest-mode search, exact-kernel columns) take the three products
+                              of the split; 1 = one 16-bit product (hi operands only, FP32
+                              accumulation).  The kernel only preconditions the n dynamics and
+                              the forces do not contain it; the expansion and the chemical-
+                              potential chain always take three.  Ignored by FP64. */
 } xlbomd_params;
 
 /* One trajectory.  R and V are natoms x 3 row-major (A, A/fs), Z natoms
@@ -126,7 +137,8 @@ typedef enum {
   XLBOMD_V = 5,        /* get/set: velocities (natoms x 3) */
   XLBOMD_KR = 6,       /* get: K (q - n) (natoms) */
   XLBOMD_RES = 7,      /* get: residual q - n (natoms) */
-  XLBOMD_ENERGY = 8,   /* get: [Omega, band, coulomb, entropy, kinetic, total] (6) */
+  XLBOMD_ENERGY = 8,   /* get: [Omega, band, coulomb, entropy, kinetic, total, repulsion] (7);
+                          Omega includes the repulsion */
   XLBOMD_MU = 9,       /* get/set: chemical potential (1); set is the Newton start */
   XLBOMD_D = 10,       /* get: density matrix (N x N) */
   XLBOMD_H = 11,       /* get: H[n] (N x N) */

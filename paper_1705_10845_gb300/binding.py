@@ -38,6 +38,7 @@ class Params(C.Structure):
         ("mu_max_iter", C.c_int), ("diverge_tol", C.c_double), ("prec", C.c_int),
         ("energy_every", C.c_int), ("scf_mode", C.c_int),
         ("kernel_auto", C.c_int), ("kernel_mode", C.c_int), ("kernel_every", C.c_int),
+        ("rep_A", C.c_double), ("rep_rho", C.c_double), ("kernel_prec", C.c_int),
     ]
 
 
@@ -201,7 +202,7 @@ class Context:
         k1 = self.params.kmax + 1
         m = self.params.rank_m
         return {Q: nat, N: nat, NHIST: k1 * nat, F: 3 * nat, R: 3 * nat, V: 3 * nat, KR: nat, RES: nat,
-                ENERGY: 6, MU: 1, D: (4 * nat) ** 2, H: (4 * nat) ** 2, GAMMA: nat * nat, STATS: 5,
+                ENERGY: 7, MU: 1, D: (4 * nat) ** 2, H: (4 * nat) ** 2, GAMMA: nat * nat, STATS: 5,
                 PROBES: 2 * m * nat, KMAT: nat * nat}[what]
 
     def get(self, sys, what) -> np.ndarray:

@@ -122,6 +122,8 @@ ModelConst model_of(const xlbomd_params& p) {
   m.r_taper = p.r_taper;
   m.U = p.hubbard_U;
   m.k = p.coulomb_k;
+  m.rep_A = p.rep_A;
+  m.rep_rho = p.rep_rho;
   return m;
 }
 
@@ -421,15 +423,20 @@ xlbomd_status kernel_update(xlbomd_ctx* ctx, Sys& S) {
 // a10
 xlbomd_status energy(xlbomd_ctx* ctx, Sys& S) {
   cudaStream_t st = ctx->stream;
+  CK(cudaMemsetAsync(S.energy + 4, 0, sizeof(double), st));
+  if (ctx->p.rep_A != 0.0) {
+    CK(launch_repulsion(st, model_of(ctx->p), S.nat, S.L, S.R, nullptr, S.work));
+    CK(launch_sum(st, S.nat, S.work, S.energy + 4));
+  }
   CK(launch_frob_dot(st, S.N, S.np, S.Dm, S.H0, S.work, S.energy + 0));
   CK(launch_energy_vec(st, S.nat, S.q, S.nh, S.pot, S.V, S.mass, S.energy + 1));
   CK(ctx->eng->entropy(st, S.mats, S.N, beta_of(ctx->p), ctx->p.n_sq, S.mu, S.dmu_last, S.Dm, S.H, S.work,
                        S.energy + 3));
-  CKS(sync_read(ctx, S.energy, 4));
+  CKS(sync_read(ctx, S.energy, 5));
   const double band = 2.0 * ctx->pinned[0], coul = ctx->pinned[1], ke = ctx->pinned[2];
-  const double ent = -2.0 * kKB * ctx->p.Te * ctx->pinned[3];
-  const double om = band + coul + ent;
-  const double out[6] = {om, band, coul, ent, ke, om + ke};
+  const double ent = -2.0 * kKB * ctx->p.Te * ctx->pinned[3], rep = ctx->pinned[4];
+  const double om = band + coul + ent + rep;
+  const double out[7] = {om, band, coul, ent, ke, om + ke, rep};
   std::memcpy(S.eh, out, sizeof(out));
   return XLBOMD_OK;
 }
@@ -679,6 +686,9 @@ void xlbomd_default_params(xlbomd_params* p) {
   p->kernel_auto = 0;
   p->kernel_mode = 0;
   p->kernel_every = 0;
+  p->rep_A = 0.0;
+  p->rep_rho = 0.3;
+  p->kernel_prec = 0;
 }
 
 xlbomd_status xlbomd_table_i(xlbomd_params* p, int kmax) {
@@ -703,7 +713,8 @@ xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* syst
   const xlbomd_params& p = *params;
   if (p.n_sq < 1 || p.n_sq > 40 || p.kmax < 1 || p.kmax > 7 || p.rank_m < 0 || p.rank_m > kMaxRank ||
       p.kernel_c == 1.0 || !(p.Te > 0) || !(p.dt > 0) || p.mu_max_iter < 1 || p.scf_mode < 0 || p.scf_mode > 1 ||
-      p.kernel_mode < 0 || p.kernel_mode > 2 || p.kernel_every < 0)
+      p.kernel_mode < 0 || p.kernel_mode > 2 || p.kernel_every < 0 || p.rep_A < 0.0 || !(p.rep_rho > 0.0) ||
+      p.kernel_prec < 0 || p.kernel_prec > 1)
     return XLBOMD_ERR_ARG;
   if (p.prec != XLBOMD_FP64 && p.prec != XLBOMD_FP16x3 && p.prec != XLBOMD_BF16x3) return XLBOMD_ERR_ARG;
   for (int i = 0; i < nsys; ++i) {
@@ -718,6 +729,7 @@ xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* syst
     delete ctx;
     return XLBOMD_ERR_UNSUPPORTED;
   }
+  ctx->eng->set_probe_segments(p.kernel_prec == 1 ? 1 : 3);
   auto bail = [&](xlbomd_status st) {
     xlbomd_free(ctx);
     return st;
@@ -880,7 +892,7 @@ xlbomd_status xlbomd_get(xlbomd_ctx* ctx, int sys, int what, double* host_out) {
     case XLBOMD_V: return cp(S.V, 3 * nat);
     case XLBOMD_KR: return cp(S.Kr, nat);
     case XLBOMD_RES: return cp(S.r, nat);
-    case XLBOMD_ENERGY: std::memcpy(host_out, S.eh, 6 * sizeof(double)); return XLBOMD_OK;
+    case XLBOMD_ENERGY: std::memcpy(host_out, S.eh, 7 * sizeof(double)); return XLBOMD_OK;
     case XLBOMD_MU: host_out[0] = S.mu; return XLBOMD_OK;
     case XLBOMD_D: return cp2d(S.Dm, S.N, S.np);
     case XLBOMD_H: return cp2d(S.H, S.N, S.np);
@@ -1004,7 +1016,7 @@ xlbomd_status xlbomd_selftest_gemm(int n, int prec, int sym, double* result) {
 
 xlbomd_status xlbomd_free(xlbomd_ctx* ctx) {
   if (!ctx) return XLBOMD_ERR_ARG;
-  if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  cudaStreamSynchronize(ctx->stream);   // no work of this context may still use its memory
   for (Sys& S : ctx->sys) free_sys(S);
   if (ctx->cdev) cudaFree(ctx->cdev);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);

@@ -295,6 +295,7 @@ struct Epi {
   float dvec_scale = 1.0f;
   bool out64 = false;       // write C.d (and convert from it) instead of C.f
   bool convert = true;      // produce the split operand pair of C
+  int nseg = 3;             // 3: hi*hi + hi*lo + lo*hi; 1: hi*hi only
 };
 
 // The recursion is carried in correction form so that its exact leading
@@ -360,7 +361,7 @@ class EngineSplit : public Engine {
     auto& tl = tiles_[np];
     RET(cudaMemsetAsync(C.amax, 0, sizeof(unsigned), s));
     TcArgs a;
-    a.nseg = 3;
+    a.nseg = e.nseg;
     a.sym = sym ? 1 : 0;
     a.bf16 = bf16_;
     a.alpha = e.alpha;
@@ -449,6 +450,8 @@ class EngineSplit : public Engine {
                     double* stats) override {
     const int np = m.np, n = m.n;
     const size_t cnt = (size_t)np * np;
+    // probe chains may run on the hi operands alone; the mu chain always takes all three products
+    const int nseg = full_last ? 3 : probe_nseg_;
     SplitMat* T1 = &m.sT1a;
     SplitMat* T1n = &m.sT1b;
     for (int k = 0; k < n; ++k) {
@@ -457,6 +460,7 @@ class EngineSplit : public Engine {
       Epi em;                                                                    // Mt = 2 T1 - T_{k+1} A1
       em.alpha = -1.f;
       em.out64 = true;
+      em.nseg = nseg;
       if (k == 0) {
         level0_A1_d_kernel<<<nblk(cnt), 256, 0, s>>>(np, m.sT[0].d, dvec, m.sA1.f, m.sA1.amax);
         note_launch();
@@ -466,6 +470,7 @@ class EngineSplit : public Engine {
       } else {
         Epi eg;
         eg.convert = false;
+        eg.nseg = nseg;
         RET(gemm(s, np, m.sT[k], *T1, m.sG, eg, false, stats));                  // G = T T1
         dim3 grid(np / 32, np / 32), block(32, 8);
         transpose_add_f32_kernel<<<grid, block, 0, s>>>(np, m.sG.f, m.sA1.f, m.sA1.amax);
@@ -490,6 +495,7 @@ class EngineSplit : public Engine {
       ey.e64_trans = 1;
       ey.out64 = true;
       ey.convert = !last;
+      ey.nseg = nseg;
       RET(gemm(s, np, m.sY[k], m.sMt, *dst, ey, true, stats));
       if (last) {
         get_diag_d_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, np, dst->d, out_diag);
@@ -503,6 +509,7 @@ class EngineSplit : public Engine {
   }
 
   const int* device_error() const override { return err_; }
+  void set_probe_segments(int nseg) override { probe_nseg_ = (nseg == 1) ? 1 : 3; }
 
   cudaError_t trace_tn(cudaStream_t s, MatSet& m, int N, double* out) override {
     diag_sum_d_kernel<<<1, 1024, 0, s>>>(N, m.np, m.sT[m.n].d, out);
@@ -545,6 +552,7 @@ class EngineSplit : public Engine {
 
  private:
   int bf16_;
+  int probe_nseg_ = 3;
   std::unordered_map<int, std::pair<int*, std::pair<int, int>>> tiles_;
 };
 

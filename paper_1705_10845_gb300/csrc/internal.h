@@ -28,6 +28,7 @@ cudaError_t gemm_f64_nt(cudaStream_t s, int M, int N, int K, const double* A, in
 // ---- model (model_kernels.cu) ----
 struct ModelConst {
   double eps_s, eps_p, t0[4], r_decay, r_cut, r_taper, U, k;
+  double rep_A, rep_rho;   // pair repulsion rep_A exp(-r/rep_rho) S(r); rep_A = 0: off
 };
 
 // H0 (np x np, zeroed padding) from positions R (natoms x 3) in a box L.
@@ -55,6 +56,10 @@ cudaError_t launch_gershgorin(cudaStream_t s, int n, int np, const double* H, do
 cudaError_t launch_forces(cudaStream_t s, const ModelConst& m, int nat, double L, double eta, int ng,
                           const double* G4, const double* R, const double* D, int np, const double* q,
                           const double* n, double* F, double* work /* >= 4*ng */, bool fp32);
+// Pair repulsion: F_I += -dE_rep/dR_I when F is not null; e_I = half the pair energy of atom I
+// when e is not null (E_rep = sum_I e_I).  No launch when rep_A = 0.
+cudaError_t launch_repulsion(cudaStream_t s, const ModelConst& m, int nat, double L, const double* R, double* F,
+                             double* e);
 // q_I = sum_{a in I} (1 + Tn_aa) + 2 dmu dmu_diag_a - Z_I, r = q - n
 cudaError_t launch_charges(cudaStream_t s, int nat, const double* ddiag, const double* Z,
                            const double* n, double* q, double* r);

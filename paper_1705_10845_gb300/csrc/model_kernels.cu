@@ -437,6 +437,51 @@ __global__ void verlet_second_kernel(int nat, double dt, double minv, double* __
 }
 
 // out[0] = 1/2 sum (2q - n) pot (Coulomb), out[1] = kinetic energy (eV)
+// Pair repulsion A exp(-r/rho) S(r) over the 27 images of the minimum image (one warp per
+// atom I, lanes over J): F_I += sum_{J,T} d(e S)/dr (R_J + T L - R_I)/r, e_I = 1/2 sum e S.
+__global__ void repulsion_kernel(ModelConst m, int nat, double L, const double* __restrict__ R,
+                                 double* __restrict__ F, double* __restrict__ e) {
+  const int I = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (I >= nat) return;
+  const double xi = R[3 * I], yi = R[3 * I + 1], zi = R[3 * I + 2];
+  const double rc2 = m.r_cut * m.r_cut, w = m.r_cut - m.r_taper;
+  double fx = 0.0, fy = 0.0, fz = 0.0, en = 0.0;
+  for (int J = lane; J < nat; J += 32) {
+    const double x0 = R[3 * J] - xi, y0 = R[3 * J + 1] - yi, z0 = R[3 * J + 2] - zi;
+    for (int tx = -1; tx <= 1; ++tx)
+      for (int ty = -1; ty <= 1; ++ty)
+        for (int tz = -1; tz <= 1; ++tz) {
+          if (J == I && tx == 0 && ty == 0 && tz == 0) continue;
+          const double dx = x0 + tx * L, dy = y0 + ty * L, dz = z0 + tz * L;
+          const double r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 >= rc2) continue;
+          const double r = sqrt(r2);
+          const double u = fmin(fmax((r - m.r_taper) / w, 0.0), 1.0);
+          const double S = 1.0 - u * u * u * (10.0 - u * (15.0 - 6.0 * u));
+          const double dS = -30.0 * u * u * (1.0 - u) * (1.0 - u) / w;
+          const double ex = m.rep_A * exp(-r / m.rep_rho);
+          const double de = ex * (dS - S / m.rep_rho);
+          fx += de * dx / r;
+          fy += de * dy / r;
+          fz += de * dz / r;
+          en += 0.5 * ex * S;
+        }
+  }
+  fx = warp_sum(fx);
+  fy = warp_sum(fy);
+  fz = warp_sum(fz);
+  en = warp_sum(en);
+  if (lane == 0) {
+    if (F) {
+      F[3 * I] += fx;
+      F[3 * I + 1] += fy;
+      F[3 * I + 2] += fz;
+    }
+    if (e) e[I] = en;
+  }
+}
+
 __global__ void energy_vec_kernel(int nat, const double* __restrict__ q, const double* __restrict__ n,
                                   const double* __restrict__ pot, const double* __restrict__ V, double mass,
                                   double* __restrict__ out) {
@@ -523,6 +568,15 @@ cudaError_t launch_gershgorin(cudaStream_t s, int n, int np, const double* H, do
   return cudaGetLastError();
 }
 
+cudaError_t launch_repulsion(cudaStream_t s, const ModelConst& m, int nat, double L, const double* R, double* F,
+                             double* e) {
+  if (m.rep_A == 0.0) return cudaSuccess;
+  const int wpb = 8;
+  repulsion_kernel<<<(nat + wpb - 1) / wpb, 32 * wpb, 0, s>>>(m, nat, L, R, F, e);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_forces(cudaStream_t s, const ModelConst& m, int nat, double L, double eta, int ng,
                           const double* G4, const double* R, const double* D, int np, const double* q,
                           const double* n, double* F, double* work, bool fp32) {
@@ -541,6 +595,7 @@ cudaError_t launch_forces(cudaStream_t s, const ModelConst& m, int nat, double L
     forces_coul_recip_kernel<<<nb, 32 * wpb, 0, s>>>(m.k, nat, ng, G4, R, q, n, work, F);
     note_launch();
   }
+  if (cudaError_t e = launch_repulsion(s, m, nat, L, R, F, nullptr)) return e;
   return cudaGetLastError();
 }
 

@@ -33,7 +33,7 @@ def model_params(X, **kw):
 
 
 def oracle_model(p):
-    return O.Model(Te=p.Te, n_sq=p.n_sq)
+    return O.Model(Te=p.Te, n_sq=p.n_sq, rep_A=p.rep_A, rep_rho=p.rep_rho)
 
 
 CASES = [
@@ -195,6 +195,25 @@ def test_mu_search_through_flat_occupation(X, prec, tol_q):
     assert np.max(np.abs(q - ref.q)) < tol_q
 
 
+def test_pair_repulsion_matches_oracle(X):
+    s = synth.make_system(24, 1705, L=7.0)
+    p = model_params(X, rep_A=40.0, rep_rho=0.3)
+    m = oracle_model(p)
+    n = random_n(s.natoms, 12)
+    ref = O.evaluate(s.R, s.L, s.Z, n, m, None, with_kernel=False)
+    with X.Context(p, [sysdict(s)]) as ctx:
+        ctx.set(0, X.N, n)
+        ctx.set(0, X.MU, [ref.dens.mu])
+        ctx.build_H(0)
+        ctx.density(0)
+        ctx.energy(0)
+        F, E = ctx.get(0, X.F), ctx.get(0, X.ENERGY)
+    assert ref.parts["repulsion"] > 0.0
+    assert E[6] == pytest.approx(ref.parts["repulsion"], rel=1e-12, abs=1e-12)
+    assert E[0] == pytest.approx(ref.Omega, rel=1e-8)
+    assert np.max(np.abs(F - ref.F)) < 1e-8
+
+
 def test_single_atom_edge_case(X):
     p = model_params(X)
     s = dict(natoms=1, L=7.0, R=np.array([[1.0, 2.0, 3.0]]), V=np.zeros((1, 3)), Z=np.array([4.0]), mass=12.0)
@@ -247,7 +266,7 @@ def test_exact_kernel_matches_oracle(X, name, make):
     assert np.max(np.abs(Kr - Kref @ ev.r)) < 1e-10
 
 
-@pytest.mark.parametrize("variant", ["exact_every5", "accumulated", "delta", "kmax6", "kmax7"])
+@pytest.mark.parametrize("variant", ["exact_every5", "accumulated", "delta", "kmax6", "kmax7", "repulsion"])
 def test_kernel_and_dissipation_variants_follow_oracle(X, variant):
     # the exact kernel held and recomputed every 5 steps (Section VI.A), the
     # accumulated rank-1 kernel (end of Section V.F), K = K_0 only (rank 0), and
@@ -259,6 +278,8 @@ def test_kernel_and_dissipation_variants_follow_oracle(X, variant):
         kw, xlkw = dict(kernel_mode=1, kernel_every=5), dict(kernel_mode="exact", kernel_every=5)
     elif variant == "accumulated":
         kw, xlkw = dict(kernel_mode=2), dict(kernel_mode="accumulated")
+    elif variant == "repulsion":
+        kw = dict(rep_A=40.0, rep_rho=0.3)
     elif variant == "delta":
         kw, xlkw = dict(rank_m=0), dict(rank_m=0)
     else:

@@ -138,3 +138,35 @@ def test_one_cta_per_tile_variant_matches_fp64(X):
                 err, flag, ms = res[k]
                 k += 1
                 assert flag == 0 and err < bound * n, (n, err)
+
+
+@pytest.mark.parametrize("prec", ["fp16x3", "bf16x3"])
+def test_single_product_probe_chains(X, prec):
+    # kernel_prec = 1: the kernel's response chains run one 16-bit product per
+    # step; charges and forces (expansion and mu chain at three products) do not
+    # change, and K r is checked against the oracle's exact-response kernel
+    s = synth.make_system(37, 11)
+    out = {}
+    ref = None
+    for kp in (0, 1):
+        p = X.default_params(mix_alpha=ALPHA_MIX, kernel_c=1 - 1 / ALPHA_MIX, prec=prec, mu_tol=1e-3,
+                             kernel_prec=kp)
+        m = O.Model(Te=p.Te, n_sq=p.n_sq)
+        rng = np.random.default_rng(2)
+        n = rng.normal(scale=0.02, size=s.natoms)
+        n -= n.mean()
+        ref = O.evaluate(s.R, s.L, s.Z, n, m, O.XLParams(rank_m=p.rank_m, kernel_c=p.kernel_c))
+        with X.Context(p, [sysdict(s)]) as ctx:
+            ctx.set(0, X.N, n)
+            ctx.set(0, X.MU, [ref.dens.mu + 0.01])
+            ctx.build_H(0)
+            ctx.density(0)
+            ctx.kernel_update(0)
+            out[kp] = (ctx.get(0, X.Q), ctx.get(0, X.F), ctx.get(0, X.KR))
+    q0, F0, K0 = out[0]
+    q1, F1, K1 = out[1]
+    assert np.array_equal(q0, q1) and np.array_equal(F0, F1)
+    rel = np.abs(K1 - ref.Kr).max() / np.abs(ref.Kr).max()
+    print(prec, "single-product probes: K r rel err", rel, "three products:",
+          np.abs(K0 - ref.Kr).max() / np.abs(ref.Kr).max())
+    assert rel < (2e-3 if prec == "fp16x3" else 2e-2)
