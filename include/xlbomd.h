@@ -114,6 +114,11 @@ typedef struct {
                               accumulation).  The kernel only preconditions the n dynamics and
                               the forces do not contain it; the expansion and the chemical-
                               potential chain always take three.  Ignored by FP64. */
+  int graphs;              /* 1: split precisions with at most 2048 padded orbitals capture each
+                              chemical-potential pass (per Newton-Schulz plan) and each probe's
+                              response in CUDA graphs and replay them (the second run of a plan
+                              is captured; results are bitwise those of direct launches).  For
+                              many small systems, where launch overhead dominates.  0: off. */
 } xlbomd_params;
 
 /* One trajectory.  R and V are natoms x 3 row-major (A, A/fs), Z natoms

@@ -38,7 +38,7 @@ class Params(C.Structure):
         ("mu_max_iter", C.c_int), ("diverge_tol", C.c_double), ("prec", C.c_int),
         ("energy_every", C.c_int), ("scf_mode", C.c_int),
         ("kernel_auto", C.c_int), ("kernel_mode", C.c_int), ("kernel_every", C.c_int),
-        ("rep_A", C.c_double), ("rep_rho", C.c_double), ("kernel_prec", C.c_int),
+        ("rep_A", C.c_double), ("rep_rho", C.c_double), ("kernel_prec", C.c_int), ("graphs", C.c_int),
     ]
 
 

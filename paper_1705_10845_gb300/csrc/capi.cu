@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -20,6 +21,7 @@
 using namespace xl;
 
 std::atomic<long long> xl::g_launch_count{0};
+thread_local long long xl::t_launch_count = 0;
 
 namespace {
 
@@ -51,6 +53,17 @@ struct Sys {
   double stats[5] = {0, 0, 0, 0, 0};
   double eh[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   std::vector<double> G4h;
+  // captured work (params.graphs): one graph per Newton-Schulz plan of a chemical-potential pass,
+  // one per probe slot of the kernel update; dpar holds mu and the start scales c_k
+  struct Captured {
+    std::vector<int> key;
+    int seen = 0;                      // eager runs before the capture
+    cudaGraphExec_t exec = nullptr;
+    double stats[5] = {0, 0, 0, 0, 0};  // host counters one run adds
+    long long launches = 0;            // kernels one run launches
+  };
+  std::vector<Captured> graphs;
+  double* dpar = nullptr;
 };
 
 }  // namespace
@@ -60,6 +73,7 @@ struct xlbomd_ctx {
   cudaStream_t stream = nullptr;
   std::vector<Sys> sys;
   double* pinned = nullptr;
+  double* ppar = nullptr;   // pinned staging of the device parameters of a captured pass
   double* cdev = nullptr;
   int status = XLBOMD_OK;
   std::string msg;
@@ -156,6 +170,62 @@ xlbomd_status check(xlbomd_ctx* ctx, int sys) {
   if (!ctx) return XLBOMD_ERR_ARG;
   if (ctx->status != XLBOMD_OK) return (xlbomd_status)ctx->status;
   if (sys < 0 || sys >= (int)ctx->sys.size()) return fail(ctx, XLBOMD_ERR_ARG, "system index out of range");
+  return XLBOMD_OK;
+}
+
+// Work that params.graphs may capture: split precisions, up to 2048 padded orbitals (where
+// launch overhead matters), no per-product event timing.
+bool use_graphs(const xlbomd_ctx* ctx, const Sys& S) {
+  return ctx->p.graphs == 1 && ctx->p.prec != XLBOMD_FP64 && S.np <= 2048 && !ctx->eng->prof;
+}
+
+// Enqueue fn's work on the context stream: eagerly the first time `key` is seen (this also
+// makes every lazy set-up happen outside a capture), captured into a CUDA graph the second
+// time, replayed from the graph afterwards.  fn must enqueue the same work for the same key;
+// what may differ between runs lives in device memory (for the chemical-potential pass, mu
+// and the Newton-Schulz start scales in S.dpar).
+xlbomd_status run_captured(xlbomd_ctx* ctx, Sys& S, const std::vector<int>& key,
+                           const std::function<xlbomd_status()>& fn) {
+  cudaStream_t st = ctx->stream;
+  Sys::Captured* g = nullptr;
+  for (auto& x : S.graphs)
+    if (x.key == key) g = &x;
+  if (!g) {
+    S.graphs.emplace_back();
+    g = &S.graphs.back();
+    g->key = key;
+  }
+  if (g->exec) {
+    CK(cudaGraphLaunch(g->exec, st));
+    for (int k = 0; k < 5; ++k) S.stats[k] += g->stats[k];
+    g_launch_count.fetch_add(g->launches, std::memory_order_relaxed);
+    return XLBOMD_OK;
+  }
+  if (g->seen == 0) {
+    g->seen = 1;
+    return fn();
+  }
+  double before[5];
+  std::memcpy(before, S.stats, sizeof(before));
+  const long long l0 = t_launch_count;
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  const xlbomd_status rs = fn();
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+  if (rs != XLBOMD_OK || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rs != XLBOMD_OK ? rs : fail(ctx, XLBOMD_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&g->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    g->exec = nullptr;
+    return fail(ctx, XLBOMD_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+  }
+  for (int k = 0; k < 5; ++k) g->stats[k] = S.stats[k] - before[k];
+  g->launches = t_launch_count - l0;
+  CK(cudaGraphLaunch(g->exec, st));   // the captured work has not run yet
   return XLBOMD_OK;
 }
 
@@ -260,11 +330,25 @@ xlbomd_status density(xlbomd_ctx* ctx, Sys& S, bool with_forces) {
     if (!(t0max < 1.0)) return fail(ctx, XLBOMD_ERR_SPECTRUM, "|beta (e - mu)| / 2^(n+1) >= 1");
     ns_plan(t0max, n, tol_ns, plan_s, plan_c);
     S.mats.t0max = t0max;
-    CK(E.foe(st, S.mats, S.H, S.N, mu, sc, plan_s, plan_c, S.stats));
-    // mu chain: T1_0 = +sc I, full last level
-    CK(E.chain(st, S.mats, S.dvec_mu, S.N, true, S.dmu_diag, S.stats));
-    CK(E.trace_tn(st, S.mats, S.N, S.scal));          // scal[0] = sum_i T_n,ii
-    CK(launch_sum(st, S.N, S.dmu_diag, S.scal + 1));    // scal[1] = sum_i dT_n,ii/dmu
+    auto mu_pass = [&](const double* dp) -> xlbomd_status {
+      CK(E.foe(st, S.mats, S.H, S.N, mu, sc, plan_s, plan_c, S.stats, dp));
+      // mu chain: T1_0 = +sc I, full last level
+      CK(E.chain(st, S.mats, S.dvec_mu, S.N, true, S.dmu_diag, S.stats));
+      CK(E.trace_tn(st, S.mats, S.N, S.scal));          // scal[0] = sum_i T_n,ii
+      CK(launch_sum(st, S.N, S.dmu_diag, S.scal + 1));    // scal[1] = sum_i dT_n,ii/dmu
+      return XLBOMD_OK;
+    };
+    if (use_graphs(ctx, S)) {
+      if (!S.dpar) CKS(dalloc(ctx, &S.dpar, 64));
+      ctx->ppar[0] = mu;
+      for (int k = 0; k < n && k < 63; ++k) ctx->ppar[1 + k] = plan_c[k];
+      CK(cudaMemcpyAsync(S.dpar, ctx->ppar, sizeof(double) * 64, cudaMemcpyHostToDevice, st));
+      std::vector<int> key{0};
+      key.insert(key.end(), plan_s.begin(), plan_s.end());
+      CKS(run_captured(ctx, S, key, [&] { return mu_pass(S.dpar); }));
+    } else {
+      CKS(mu_pass(nullptr));
+    }
     int* herr = reinterpret_cast<int*>(ctx->pinned + 63);
     *herr = 0;
     if (const int* derr = E.device_error())
@@ -411,7 +495,12 @@ xlbomd_status kernel_update(xlbomd_ctx* ctx, Sys& S) {
     CK(launch_kernel_vec(st, 0, S.nat, i, S.kc, S.r, S.pV, S.pW, nullptr, S.scal + 8));
     CKS(sync_read(ctx, S.scal + 8, 1));
     if (ctx->pinned[0] != 1.0) break;
-    CKS(response(ctx, S, S.pV + (size_t)i * S.nat, S.pW + (size_t)i * S.nat));
+    double* vi = S.pV + (size_t)i * S.nat;
+    double* wi = S.pW + (size_t)i * S.nat;
+    if (use_graphs(ctx, S))
+      CKS(run_captured(ctx, S, {1, i}, [&] { return response(ctx, S, vi, wi); }));
+    else
+      CKS(response(ctx, S, vi, wi));
     m = i + 1;
   }
   CK(launch_kernel_vec(st, 1, S.nat, m, S.kc, S.r, S.pV, S.pW, S.Kr, S.scal + 8));
@@ -554,11 +643,14 @@ void free_sys(Sys& S) {
   double** ptrs[] = {&S.R,  &S.V,        &S.F,    &S.Z,  &S.nh,  &S.q,    &S.r,     &S.Kr,    &S.pot,
                      &S.potv, &S.gam,    &S.SF,   &S.G4, &S.H0,  &S.H,    &S.Dm,    &S.ddiag, &S.dmu_diag,
                      &S.d1, &S.dvec,     &S.dvec_mu, &S.pV, &S.pW, &S.scal, &S.work, &S.energy,
-                     &S.Kfull, &S.Jm};
+                     &S.Kfull, &S.Jm, &S.dpar};
   for (double** p : ptrs) {
     if (*p) cudaFree(*p);
     *p = nullptr;
   }
+  for (auto& g : S.graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  S.graphs.clear();
   free_matset(S.mats);
 }
 
@@ -689,6 +781,7 @@ void xlbomd_default_params(xlbomd_params* p) {
   p->rep_A = 0.0;
   p->rep_rho = 0.3;
   p->kernel_prec = 0;
+  p->graphs = 0;
 }
 
 xlbomd_status xlbomd_table_i(xlbomd_params* p, int kmax) {
@@ -714,7 +807,7 @@ xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* syst
   if (p.n_sq < 1 || p.n_sq > 40 || p.kmax < 1 || p.kmax > 7 || p.rank_m < 0 || p.rank_m > kMaxRank ||
       p.kernel_c == 1.0 || !(p.Te > 0) || !(p.dt > 0) || p.mu_max_iter < 1 || p.scf_mode < 0 || p.scf_mode > 1 ||
       p.kernel_mode < 0 || p.kernel_mode > 2 || p.kernel_every < 0 || p.rep_A < 0.0 || !(p.rep_rho > 0.0) ||
-      p.kernel_prec < 0 || p.kernel_prec > 1)
+      p.kernel_prec < 0 || p.kernel_prec > 1 || p.graphs < 0 || p.graphs > 1)
     return XLBOMD_ERR_ARG;
   if (p.prec != XLBOMD_FP64 && p.prec != XLBOMD_FP16x3 && p.prec != XLBOMD_BF16x3) return XLBOMD_ERR_ARG;
   for (int i = 0; i < nsys; ++i) {
@@ -734,7 +827,9 @@ xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* syst
     xlbomd_free(ctx);
     return st;
   };
-  if (cudaMallocHost((void**)&ctx->pinned, 64 * sizeof(double)) != cudaSuccess) return bail(XLBOMD_ERR_OOM);
+  if (cudaMallocHost((void**)&ctx->pinned, 64 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&ctx->ppar, 64 * sizeof(double)) != cudaSuccess)
+    return bail(XLBOMD_ERR_OOM);
   if (dalloc(ctx, &ctx->cdev, 8) != XLBOMD_OK) return bail(XLBOMD_ERR_OOM);
   // every upload and memset below runs on the context's stream, which may be non-blocking
   if (cudaMemcpyAsync(ctx->cdev, p.c, sizeof(double) * 8, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
@@ -1020,6 +1115,7 @@ xlbomd_status xlbomd_free(xlbomd_ctx* ctx) {
   for (Sys& S : ctx->sys) free_sys(S);
   if (ctx->cdev) cudaFree(ctx->cdev);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->ppar) cudaFreeHost(ctx->ppar);
   delete ctx->eng;
   delete ctx;
   return XLBOMD_OK;

@@ -10,7 +10,11 @@ namespace xl {
 
 // Number of kernels this library has launched (all contexts, all streams).
 extern std::atomic<long long> g_launch_count;
-inline void note_launch() { g_launch_count.fetch_add(1, std::memory_order_relaxed); }
+extern thread_local long long t_launch_count;   // launches by the calling host thread
+inline void note_launch() {
+  g_launch_count.fetch_add(1, std::memory_order_relaxed);
+  ++t_launch_count;
+}
 
 constexpr int kMaxRank = 8;
 constexpr double kPi = 3.14159265358979323846;

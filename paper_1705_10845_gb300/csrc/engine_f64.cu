@@ -31,7 +31,7 @@ class EngineF64 : public Engine {
   }
 
   cudaError_t foe(cudaStream_t s, MatSet& m, const double* H, int N, double mu, double sc,
-                  const std::vector<int>& ns, const std::vector<double>& nc, double* stats) override {
+                  const std::vector<int>& ns, const std::vector<double>& nc, double* stats, const double*) override {
     const int np = m.np, n = m.n;
     RET(launch_t0_init(s, N, np, H, mu, sc, m.T[0]));
     for (int k = 0; k < n; ++k) {

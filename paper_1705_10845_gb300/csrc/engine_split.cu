@@ -84,8 +84,12 @@ __global__ void t0_init_f32_kernel(int n, int np, const double* __restrict__ H, 
 
 // Y = a I + b X
 __global__ void axpi_f32_kernel(int np, float a, float b, const float* __restrict__ X, float* __restrict__ Y,
-                                unsigned* amax) {
+                                unsigned* amax, const double* __restrict__ dc = nullptr) {
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (dc) {   // a = 1 - c, b = c from the device copy of c
+    a = (float)(1.0 - dc[0]);
+    b = (float)dc[0];
+  }
   float v = 0.0f;
   if (idx < (size_t)np * np) {
     const int i = (int)(idx / np), j = (int)(idx % np);
@@ -202,8 +206,9 @@ __global__ void convert_split_d_kernel(size_t count, const float2* __restrict__ 
 
 // T0 = -sc (H - mu I) as a double-float (hi = rn32(v), lo = rn32(v - hi))
 __global__ void t0_init_d_kernel(int n, int np, const double* __restrict__ H, double mu, double sc,
-                                 float2* __restrict__ T0, unsigned* amax) {
+                                 float2* __restrict__ T0, unsigned* amax, const double* __restrict__ dmu = nullptr) {
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (dmu) mu = dmu[0];
   float vh = 0.0f;
   if (idx < (size_t)np * np) {
     const int i = (int)(idx / np), j = (int)(idx % np);
@@ -396,43 +401,48 @@ class EngineSplit : public Engine {
   }
 
   cudaError_t foe(cudaStream_t s, MatSet& m, const double* H, int N, double mu, double sc,
-                  const std::vector<int>& ns, const std::vector<double>& nc, double* stats) override {
+                  const std::vector<int>& ns, const std::vector<double>& nc, double* stats,
+                  const double* dpar) override {
     const int np = m.np, n = m.n;
     const size_t cnt = (size_t)np * np;
     RET(cudaMemsetAsync(m.sT[0].amax, 0, sizeof(unsigned), s));
-    t0_init_d_kernel<<<nblk(cnt), 256, 0, s>>>(N, np, H, mu, sc, m.sT[0].d, m.sT[0].amax);
+    t0_init_d_kernel<<<nblk(cnt), 256, 0, s>>>(N, np, H, mu, sc, m.sT[0].d, m.sT[0].amax, dpar);
     note_launch();
     RET(cudaGetLastError());
     RET(convert_d(s, m.sT[0], np));
     for (int k = 0; k < n; ++k) {
       Epi es;
       RET(gemm(s, np, m.sT[k], m.sT[k], m.sS, es, true, stats));                 // S = T^2
-      SplitMat& W = m.sY[k];
-      RET(cudaMemsetAsync(W.amax, 0, sizeof(unsigned), s));
+      // the Newton-Schulz iterates alternate between sY[k] and the work matrix; the start is
+      // chosen by the parity of the iteration count so that W_k always ends in sY[k] (the
+      // buffers every later use, and a captured graph of this pass, refer to)
+      SplitMat* W = (ns[k] % 2 == 1) ? &m.sYw : &m.sY[k];
+      SplitMat* Wn = (W == &m.sY[k]) ? &m.sYw : &m.sY[k];
+      RET(cudaMemsetAsync(W->amax, 0, sizeof(unsigned), s));
       if (k == 0)
-        axpi_f32_kernel<<<nblk(cnt), 256, 0, s>>>(np, 0.f, 1.f, m.sS.f, W.f, W.amax);          // W = S
+        axpi_f32_kernel<<<nblk(cnt), 256, 0, s>>>(np, 0.f, 1.f, m.sS.f, W->f, W->amax);        // W = S
       else
-        axpi_f32_kernel<<<nblk(cnt), 256, 0, s>>>(np, (float)(1.0 - nc[k]), (float)nc[k], m.sY[k - 1].f, W.f,
-                                                 W.amax);                                  // W = (1-c) I + c W_{k-1}
+        axpi_f32_kernel<<<nblk(cnt), 256, 0, s>>>(np, (float)(1.0 - nc[k]), (float)nc[k], m.sY[k - 1].f, W->f,
+                                                 W->amax, dpar ? dpar + 1 + k : nullptr);  // W = (1-c) I + c W_{k-1}
       note_launch();
       RET(cudaGetLastError());
-      RET(convert(s, W, np));
+      RET(convert(s, *W, np));
       for (int it = 0; it < ns[k]; ++it) {
         Epi eq;                                                                   // Q = S - W - W S
         eq.alpha = -1.f;
         eq.E = &m.sS;
         eq.beta = 1.f;
-        eq.E2 = &m.sY[k];
+        eq.E2 = W;
         eq.beta2 = -1.f;
-        RET(gemm(s, np, m.sY[k], m.sS, m.sQ, eq, false, stats));
+        RET(gemm(s, np, *W, m.sS, m.sQ, eq, false, stats));
         Epi ew;                                                                   // W <- W + Q - Q W
         ew.alpha = -1.f;
-        ew.E = &m.sY[k];
+        ew.E = W;
         ew.beta = 1.f;
         ew.E2 = &m.sQ;
         ew.beta2 = 1.f;
-        RET(gemm(s, np, m.sQ, m.sY[k], m.sYw, ew, true, stats));
-        std::swap(m.sY[k], m.sYw);
+        RET(gemm(s, np, m.sQ, *W, *Wn, ew, true, stats));
+        std::swap(W, Wn);
         if (stats) stats[1] += 1;
       }
       Epi et;                                                                     // T' = 2T - 2 T W

@@ -108,8 +108,12 @@ class Engine {
   int kind_n_[64] = {0};
   // T_0 = -sc (H - mu I); n levels T_{k+1} = 2 T_k Y_k, Y_k = (I + T_k^2)^-1 by
   // plan.s[k] Newton-Schulz steps (2I - Y B) Y from Y = I - S (k = 0) or c_k Y_{k-1}.
+  // dpar (device, may be null): when set, mu = dpar[0] and the Newton-Schulz start scales
+  // c_k = dpar[1 + k] are read on the device instead of the host values mu, nc (so that a
+  // captured graph of the expansion can be replayed with new values; split engines only).
   virtual cudaError_t foe(cudaStream_t s, MatSet& m, const double* H, int N, double mu, double sc,
-                          const std::vector<int>& ns, const std::vector<double>& nc, double* stats) = 0;
+                          const std::vector<int>& ns, const std::vector<double>& nc, double* stats,
+                          const double* dpar) = 0;
   // Response chain with diagonal T1_0 = diag(dvec): T1_{k+1} = Y_k (2 T1_k - A1 T_{k+1}),
   // A1 = T_k T1_k + T1_k T_k.  out_diag = diag(T1_n); full_last keeps T1_n in Tmu.
   virtual cudaError_t chain(cudaStream_t s, MatSet& m, const double* dvec, int N, bool full_last,
