@@ -50,8 +50,9 @@ def parse():
     ap.add_argument("--Te", type=float, default=1500.0)
     ap.add_argument("--nsq", type=int, default=14)
     ap.add_argument("--rank", type=int, default=4)
-    ap.add_argument("--kernel-prec", type=int, default=0, choices=[0, 1],
-                    help="1: the kernel's probe chains take one 16-bit product instead of three")
+    ap.add_argument("--kernel-prec", type=int, default=1, choices=[0, 1],
+                    help="1 (default): the kernel's probe chains take one 16-bit product instead of three; "
+                         "0: three, as the expansion")
     ap.add_argument("--rep-A", type=float, default=40.0,
                     help="pair repulsion A exp(-r/0.3 A) (eV): the model's atoms collapse without it in long runs")
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -269,7 +270,7 @@ def run_precision_study(a, X, ctx, s, sysd, stream):
         c.energy(0)
         row = {"prec": prec, "q": c.get(0, X.Q), "F": c.get(0, X.F), "Omega": float(c.get(0, X.ENERGY)[0]),
                "density_s": t_dens}
-        c.kernel_update(0)
+        c.scf(0)                        # own t0 state and automatic c before the timed MD steps
         c.step(1)                       # warm-up
         torch.cuda.synchronize()
         t = time.perf_counter()
