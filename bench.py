@@ -86,6 +86,27 @@ def workload_config(a, parallel):
     }
 
 
+def replica_seed(rank: int) -> int:
+    """Each rank runs its own replica trajectory (weak scaling)."""
+    return 1705 + rank
+
+
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """Largest x over the ranks (the slowest replica sets the job's time); x itself without a
+    process group.  The only collective of a run: timing, never data."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -318,7 +339,7 @@ def main():
         dist.barrier()
     X.load()
 
-    s = synth.make_system(a.natoms, 1705 + rank)
+    s = synth.make_system(a.natoms, replica_seed(rank))
     sysd = dict(natoms=s.natoms, L=s.L, R=s.R, V=s.V, Z=s.Z, mass=s.mass)
     p = make_params(X, a, a.prec)
     stream = torch.cuda.current_stream()
@@ -372,12 +393,9 @@ def main():
     prof = ctx.gemm_profile(2)
     ctx.gemm_profile(0)
     st1 = ctx.get(0, X.STATS)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     sec = ms / 1000.0
-    value = ws * a.steps / sec
+    value = job_rate(a.steps, ws, sec)
 
     # ---- end to end: host state in, results out, every step ----
     ke = a.e2e_steps if a.e2e_steps is not None else max(1, a.steps // 2)
@@ -404,11 +422,8 @@ def main():
         f_host = ctx.get(0, X.F)
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([te], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        te = float(t.item())
-    e2e_value = ws * ke / te
+    te = max_over_ranks(te, dist, "cuda")
+    e2e_value = job_rate(ke, ws, te)
     h2d = 8 * (3 * nat + 3 * nat + k1 * nat)
     d2h = 8 * (3 * nat + 3 * nat + k1 * nat + nat + 3 * nat)
 

@@ -118,7 +118,9 @@ typedef struct {
                               chemical-potential pass (per Newton-Schulz plan) and each probe's
                               response in CUDA graphs and replay them (the second run of a plan
                               is captured; results are bitwise those of direct launches).  For
-                              many small systems, where launch overhead dominates.  0: off. */
+                              many small systems, where launch overhead dominates; needs a
+                              caller stream (xlbomd_init's cuda_stream, not the legacy default
+                              stream, which cannot be captured).  0: off. */
 } xlbomd_params;
 
 /* One trajectory.  R and V are natoms x 3 row-major (A, A/fs), Z natoms

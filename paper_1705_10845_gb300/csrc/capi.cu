@@ -174,9 +174,11 @@ xlbomd_status check(xlbomd_ctx* ctx, int sys) {
 }
 
 // Work that params.graphs may capture: split precisions, up to 2048 padded orbitals (where
-// launch overhead matters), no per-product event timing.
+// launch overhead matters), no per-product event timing, and a caller stream (the legacy
+// default stream cannot be captured).
 bool use_graphs(const xlbomd_ctx* ctx, const Sys& S) {
-  return ctx->p.graphs == 1 && ctx->p.prec != XLBOMD_FP64 && S.np <= 2048 && !ctx->eng->prof;
+  return ctx->p.graphs == 1 && ctx->p.prec != XLBOMD_FP64 && S.np <= 2048 && !ctx->eng->prof &&
+         ctx->stream != nullptr && ctx->stream != cudaStreamLegacy && ctx->stream != cudaStreamPerThread;
 }
 
 // Enqueue fn's work on the context stream: eagerly the first time `key` is seen (this also

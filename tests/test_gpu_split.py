@@ -176,13 +176,15 @@ def test_graph_replay_matches_direct_launches(X):
     # params.graphs = 1: chemical-potential passes and probe responses are
     # captured on their second run and replayed afterwards; a run through the
     # kernel SCF and 15 MD steps must equal the run with direct launches bitwise
+    import torch
     s = synth.make_system(64, 3)
     res = {}
+    stream = torch.cuda.Stream()      # the legacy default stream cannot be captured
     for g in (0, 1):
         p = X.default_params(mix_alpha=ALPHA_MIX, kernel_c=1 - 1 / ALPHA_MIX, prec="fp16x3", Te=1000.0,
                              n_sq=12, rank_m=2, scf_mode=1, kernel_auto=1, scf_tol=1e-5, mu_tol=1e-3,
                              rep_A=40.0, graphs=g)
-        with X.Context(p, [sysdict(s)]) as ctx:
+        with X.Context(p, [sysdict(s)], stream=stream.cuda_stream) as ctx:
             ctx.scf(0)
             ctx.step(15)
             res[g] = [ctx.get(0, w) for w in (X.Q, X.R, X.NHIST, X.KR, X.F, X.STATS)]
