@@ -117,10 +117,11 @@ typedef struct {
   int graphs;              /* 1: split precisions with at most 2048 padded orbitals capture each
                               chemical-potential pass (per Newton-Schulz plan) and each probe's
                               response in CUDA graphs and replay them (the second run of a plan
-                              is captured; results are bitwise those of direct launches).  For
-                              many small systems, where launch overhead dominates; needs a
-                              caller stream (xlbomd_init's cuda_stream, not the legacy default
-                              stream, which cannot be captured).  0: off. */
+                              is captured; results are bitwise those of direct launches).  Needs
+                              a caller stream (xlbomd_init's cuda_stream, not the legacy default
+                              stream, which cannot be captured).  On many concurrent 32-512-atom
+                              trajectories it measured slower than direct launches, so it is
+                              off by default.  0: off. */
 } xlbomd_params;
 
 /* One trajectory.  R and V are natoms x 3 row-major (A, A/fs), Z natoms

@@ -161,7 +161,7 @@ __device__ __forceinline__ bool tile_coords(const TcArgs& a, int id, int& tm, in
     tm = a.tile_list[2 * id];
     tn = a.tile_list[2 * id + 1];
   } else {
-    const int tiles_m = a.K / BM;
+    const int tiles_m = a.n / BM;
     const int per_group = kGroupM * a.tiles_n;
     const int g = id / per_group, r = id % per_group;
     const int first = g * kGroupM;
@@ -169,7 +169,7 @@ __device__ __forceinline__ bool tile_coords(const TcArgs& a, int id, int& tm, in
     tm = first + r % gm;
     tn = r / gm;
   }
-  return tm >= 0 && tm < a.K / BM && tn >= 0 && tn < a.tiles_n;
+  return tm >= 0 && tm < a.n / BM && tn >= 0 && tn < a.tiles_n;
 }
 
 // L2 prefetch of the side inputs of tile (tm, tn) by the 128 epilogue threads (t = 0..127)
@@ -209,6 +209,15 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, float (&v)[32], 
                                                float& vmax) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] *= inv;
+  if (a.P) {
+    // the other K part of a split-K product, row-major: staged so that 32 lanes read whole rows
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) tx[i][lane] = a.P[(size_t)(row0 + i) * a.ldc + col0 + lane];
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] += tx[lane][i];
+    __syncwarp();
+  }
   // FP32 side inputs of symmetric value, read transposed: for a fixed
   // column the 32 lanes read 32 consecutive rows (coalesced)
   if (a.E) {
@@ -314,7 +323,7 @@ __global__ void __launch_bounds__(192, 1)
   } else {
     // grouped raster: GROUP_M row panels at a time, so that the CTAs in flight
     // share their A and B panels in L2
-    const int tiles_m = a.K / BM;
+    const int tiles_m = a.n / BM;
     const int per_group = kGroupM * a.tiles_n;
     const int g = blockIdx.x / per_group, r = blockIdx.x % per_group;
     const int first = g * kGroupM;
@@ -323,7 +332,7 @@ __global__ void __launch_bounds__(192, 1)
     tn = r / gm;
   }
   // a tile outside the matrix (a bad tile list) is reported, never stored
-  if (tm < 0 || tm >= a.K / BM || tn < 0 || tn >= a.tiles_n) {
+  if (tm < 0 || tm >= a.n / BM || tn < 0 || tn >= a.tiles_n) {
     if (threadIdx.x == 0 && a.err) atomicExch(a.err, 4);
     return;
   }
@@ -362,7 +371,7 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-        const int seg = kb / nk, kk = (kb % nk) * BK;
+        const int seg = kb / nk, kk = a.k0 + (kb % nk) * BK;
         const CUtensorMap* ma = (seg == 2) ? &mAlo : &mAhi;
         const CUtensorMap* mb = (seg == 1) ? &mBlo : &mBhi;
         tma_load_2d(sA + s * A_BYTES, ma, kk, tm * BM, &full[s]);
@@ -536,7 +545,7 @@ __global__ void __launch_bounds__(192, 1)
             break;
           }
           mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-          const int seg = kb / nk, kk = (kb % nk) * BK;
+          const int seg = kb / nk, kk = a.k0 + (kb % nk) * BK;
           const CUtensorMap* ma = (seg == 2) ? &mAlo : &mAhi;
           const CUtensorMap* mb = (seg == 1) ? &mBlo : &mBhi;
           tma_load_2d(sA + s * A_BYTES, ma, kk, tm * BM, &full[s]);
@@ -766,7 +775,9 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
   if (!make_map(&mAhi, Ahi, n, BM, args.bf16) || !make_map(&mAlo, Alo ? Alo : Ahi, n, BM, args.bf16) ||
       !make_map(&mBhi, Bhi, n, bn, args.bf16) || !make_map(&mBlo, Blo ? Blo : Bhi, n, bn, args.bf16))
     return cudaErrorInvalidValue;
-  args.K = n;
+  args.n = n;
+  args.K = args.kext > 0 ? args.kext : n;
+  if (args.k0 < 0 || args.k0 % 64 != 0 || args.K % 64 != 0 || args.k0 + args.K > n) return cudaErrorInvalidValue;
   args.tiles_n = n / bn;
   int nblocks;
   if (args.sym) {

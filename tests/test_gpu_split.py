@@ -27,7 +27,7 @@ def sysdict(s):
     return dict(natoms=s.natoms, L=s.L, R=s.R, V=s.V, Z=s.Z, mass=s.mass)
 
 
-@pytest.mark.parametrize("n", [128, 256, 384, 1024, 2944, 4096])
+@pytest.mark.parametrize("n", [128, 256, 384, 1024, 2944, 4096, 8192])
 @pytest.mark.parametrize("sym", [False, True])
 @pytest.mark.parametrize("prec,bound", [("fp16x3", 1e-6), ("bf16x3", 2e-5)])
 def test_tensor_core_product_matches_fp64(X, n, sym, prec, bound):
