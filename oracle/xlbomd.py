@@ -18,10 +18,14 @@ section / equation it follows.  Readings of points where the paper is silent:
   orthogonal s/p Slater-Koster tight-binding Hamiltonian with
   V(r) = t0 exp(-r/r_decay) S(r), a quintic C2 taper S on [r_taper, r_cut],
   periodic Ohno-Klopman Coulomb gamma (Ewald splitting; real-space part over
-  the 27 images of the minimum-image vector), and no repulsive pair potential.
-  The plain 27-image sum of the Ohno-Klopman kernel is indefinite on neutral
-  charge vectors, which drives the ground state to +-4 e charges; the Ewald
-  form is positive definite there.
+  the 27 images of the minimum-image vector).  The plain 27-image sum of the
+  Ohno-Klopman kernel is indefinite on neutral charge vectors, which drives
+  the ground state to +-4 e charges; the Ewald form is positive definite there.
+* Pair repulsion: the model has none, and its atoms then fall into each other
+  within a few hundred MD steps whatever the kernel; an optional Born-Mayer
+  term A exp(-r/rho) S(r) over the image pairs (off by default, rep_A = 0)
+  keeps long runs physical (A = 40 eV, rho = 0.3 A balances the band
+  attraction near 1.5 A).
 * Occupations: the recursive Fermi-operator expansion with n squarings
   (canonical density-matrix perturbation theory, the paper's Ref. ANiklasson15,
   cited in Section V.B) does not give the Fermi-Dirac function for finite n.
@@ -34,10 +38,16 @@ section / equation it follows.  Readings of points where the paper is silent:
 * Kernel: J_0 = c I (Eq. JCI), K_0 = (c - 1)^-1 I (Eq. KCI); the rank-m
   kernel is rebuilt from K_0 every step with v_1 = K_0 r / |K_0 r| (Eq. v_1)
   and v_i = K_{i-1} r Gram-Schmidt orthonormalised against v_<i
-  (Section V.F).
+  (Section V.F).  The exact kernel (Eq. KK) takes J from the responses to the
+  N_at unit directions and is kept from t0 or recomputed every kernel_every
+  steps (Section VI.A).  The accumulated kernel (end of Section V.F) carries
+  K and J between steps with one rank-1 update per step, started at K_0 with
+  no update at t0, where the residual is rounding noise.  The t0 ground state
+  comes from linear mixing or from the kernel SCF of Eq. SCF_K.
 * Integrator: velocity Verlet for R (Eq. Integration, with the typo in the
   position update read as R(t+dt) = R(t) + dt Rdot(t+dt/2)) and the
-  dissipative Verlet of Eq. VRL_Damp for n with the K_max = 5 row of Table I;
+  dissipative Verlet of Eq. VRL_Damp for n with a K_max = 5, 6 or 7 row of
+  Table I;
   dt^2 ndot = -kappa K (q - n).  The n history starts with every slot equal
   to n(t0).
 """
