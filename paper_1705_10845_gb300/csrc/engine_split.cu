@@ -28,6 +28,11 @@ namespace {
 
 inline unsigned nblk(size_t count, int tpb = 256) { return (unsigned)((count + tpb - 1) / tpb); }
 
+// element-wise kernels that raise a matrix's max |x| walk their elements grid-stride with at
+// most this many blocks, so that each launch issues few atomics on the one max
+constexpr unsigned kEwBlocks = 152 * 16;
+inline unsigned ew_blocks(size_t count) { return (unsigned)std::min<size_t>(nblk(count), kEwBlocks); }
+
 // products of at least this size run as two half-K launches (split-K)
 constexpr int kSplitKMin = 8192;
 
@@ -48,8 +53,22 @@ __device__ __forceinline__ void raise_amax(unsigned* amax, float v) {
   }
 }
 
-// Conversion to the split operand pair.  All threads derive the same scale
-// from amax; thread 0 of block 0 publishes it.
+// Conversion to the split operand pair: hi = rn16(x s), lo = rn16(x s - hi).
+template <bool BF16>
+__device__ __forceinline__ void split16(float x, unsigned short& h, unsigned short& l) {
+  if (BF16) {
+    const __nv_bfloat16 hb = __float2bfloat16_rn(x);
+    h = __bfloat16_as_ushort(hb);
+    l = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(hb)));
+  } else {
+    const __half hh = __float2half_rn(x);
+    h = __half_as_ushort(hh);
+    l = __half_as_ushort(__float2half_rn(x - __half2float(hh)));
+  }
+}
+
+// All threads derive the same scale from amax; thread 0 of block 0 publishes it.  Four
+// elements per thread and step (16-byte loads, 8-byte stores; count is a multiple of 4).
 template <bool BF16>
 __global__ void convert_split_kernel(size_t count, const float* __restrict__ f, const unsigned* __restrict__ amax,
                                      uint16_t* __restrict__ hi, uint16_t* __restrict__ lo, float* __restrict__ scale) {
@@ -57,115 +76,59 @@ __global__ void convert_split_kernel(size_t count, const float* __restrict__ f, 
   float s = 1.0f;
   if (m > 0.0f && isfinite(m)) s = ldexpf(1.0f, 10 - ilogbf(m));
   if (blockIdx.x == 0 && threadIdx.x == 0) *scale = s;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-    const float x = f[i] * s;
-    if (BF16) {
-      const __nv_bfloat16 h = __float2bfloat16_rn(x);
-      const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-      hi[i] = __bfloat16_as_ushort(h);
-      lo[i] = __bfloat16_as_ushort(l);
-    } else {
-      const __half h = __float2half_rn(x);
-      const __half l = __float2half_rn(x - __half2float(h));
-      hi[i] = __half_as_ushort(h);
-      lo[i] = __half_as_ushort(l);
-    }
+  const float4* f4 = reinterpret_cast<const float4*>(f);
+  ushort4* h4 = reinterpret_cast<ushort4*>(hi);
+  ushort4* l4 = reinterpret_cast<ushort4*>(lo);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count / 4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 x = f4[i];
+    ushort4 h, l;
+    split16<BF16>(x.x * s, h.x, l.x);
+    split16<BF16>(x.y * s, h.y, l.y);
+    split16<BF16>(x.z * s, h.z, l.z);
+    split16<BF16>(x.w * s, h.w, l.w);
+    h4[i] = h;
+    l4[i] = l;
   }
 }
 
-__global__ void t0_init_f32_kernel(int n, int np, const double* __restrict__ H, double mu, double sc,
-                                   float* __restrict__ T0, unsigned* amax) {
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  float v = 0.0f;
-  if (idx < (size_t)np * np) {
-    const int i = (int)(idx / np), j = (int)(idx % np);
-    if (i < n && j < n) v = (float)(-sc * (H[idx] - (i == j ? mu : 0.0)));
-    T0[idx] = v;
-  }
-  raise_amax(amax, v);
-}
-
-// Y = a I + b X
+// Y = a I + b X (grid-stride, one max-|Y| atomic per block)
 __global__ void axpi_f32_kernel(int np, float a, float b, const float* __restrict__ X, float* __restrict__ Y,
                                 unsigned* amax, const double* __restrict__ dc = nullptr) {
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (dc) {   // a = 1 - c, b = c from the device copy of c
     a = (float)(1.0 - dc[0]);
     b = (float)dc[0];
   }
-  float v = 0.0f;
-  if (idx < (size_t)np * np) {
-    const int i = (int)(idx / np), j = (int)(idx % np);
-    v = b * X[idx] + (i == j ? a : 0.0f);
-    Y[idx] = v;
-  }
-  raise_amax(amax, v);
-}
-
-__global__ void level0_A1_f32_kernel(int np, const float* __restrict__ T0, const double* __restrict__ d,
-                                     float* __restrict__ A1, unsigned* amax) {
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  float v = 0.0f;
-  if (idx < (size_t)np * np) {
-    const int i = (int)(idx / np), j = (int)(idx % np);
-    v = (float)((double)T0[idx] * (d[i] + d[j]));
-    A1[idx] = v;
-  }
-  raise_amax(amax, v);
-}
-
-__global__ void transpose_add_f32_kernel(int np, const float* __restrict__ G, float* __restrict__ A1,
-                                         unsigned* amax) {
-  __shared__ float tile[32][33];
-  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  for (int r = ty; r < 32; r += 8) tile[r][tx] = G[(size_t)(bx + r) * np + by + tx];
-  __syncthreads();
+  const size_t count = (size_t)np * np;
   float m = 0.0f;
-  for (int r = ty; r < 32; r += 8) {
-    const size_t o = (size_t)(by + r) * np + bx + tx;
-    const float v = G[o] + tile[tx][r];
-    A1[o] = v;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / np), j = (int)(idx % np);
+    const float v = b * X[idx] + (i == j ? a : 0.0f);
+    Y[idx] = v;
     m = fmaxf(m, fabsf(v));
   }
   raise_amax(amax, m);
 }
 
-__global__ void row_dot_f32_kernel(int n, int np, const float* __restrict__ Y, const float* __restrict__ M,
-                                   double* __restrict__ out) {
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (i >= n) return;
-  double acc = 0.0;
-  for (int j = lane; j < np; j += 32) acc += (double)Y[(size_t)i * np + j] * (double)M[(size_t)i * np + j];
-  acc = warp_sum(acc);
-  if (lane == 0) out[i] = acc;
-}
-
-__global__ void get_diag_f32_kernel(int n, int np, const float* __restrict__ X, double* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (double)X[(size_t)i * np + i];
-}
-
-__global__ void diag_sum_f32_kernel(int n, int np, const float* __restrict__ X, double* __restrict__ out) {
-  __shared__ double sh[32];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += (double)X[(size_t)i * np + i];
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) *out = acc;
-}
-
-__global__ void density_out_f32_kernel(int N, int np, const float* __restrict__ Tn, const float* __restrict__ Tmu,
-                                       double dmu, double* __restrict__ ddiag, double* __restrict__ D) {
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (size_t)np * np) return;
-  const int i = (int)(idx / np), j = (int)(idx % np);
-  double v = 0.0;
-  if (i < N && j < N) {
-    v = 0.5 * ((double)Tn[idx] + dmu * (double)Tmu[idx] + (i == j ? 1.0 : 0.0));
-    if (i == j) ddiag[i] = 2.0 * v;
+// A1 = G + G^T over 32 x 32 tiles, each block walking tiles grid-stride (one atomic per block)
+__global__ void transpose_add_f32_kernel(int np, const float* __restrict__ G, float* __restrict__ A1,
+                                         unsigned* amax) {
+  __shared__ float tile[32][33];
+  const int nt = np / 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  float m = 0.0f;
+  for (int t = blockIdx.x; t < nt * nt; t += gridDim.x) {
+    const int bx = (t % nt) * 32, by = (t / nt) * 32;
+    __syncthreads();   // the previous tile's reads of `tile` are done
+    for (int r = ty; r < 32; r += 8) tile[r][tx] = G[(size_t)(bx + r) * np + by + tx];
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const size_t o = (size_t)(by + r) * np + bx + tx;
+      const float v = G[o] + tile[tx][r];
+      A1[o] = v;
+      m = fmaxf(m, fabsf(v));
+    }
   }
-  D[idx] = v;
+  raise_amax(amax, m);
 }
 
 __global__ void df_to_f64_kernel(size_t count, const float2* __restrict__ x, double* __restrict__ y) {
@@ -182,6 +145,8 @@ __global__ void ident_minus_f32_to_f64_kernel(size_t count, int np, const float*
   dst[i] = (r == c ? 1.0 : 0.0) - (double)W[i];
 }
 
+// The same from a double-float value hi + lo: the 16-bit pair splits (xh - hi16) + xl, so the
+// low FP32 word is not lost (s is a power of two, so x s is exact).
 template <bool BF16>
 __global__ void convert_split_d_kernel(size_t count, const float2* __restrict__ d, const unsigned* __restrict__ amax,
                                        uint16_t* __restrict__ hi, uint16_t* __restrict__ lo,
@@ -190,50 +155,60 @@ __global__ void convert_split_d_kernel(size_t count, const float2* __restrict__ 
   float s = 1.0f;
   if (m > 0.0f && isfinite(m)) s = ldexpf(1.0f, 10 - ilogbf(m));
   if (blockIdx.x == 0 && threadIdx.x == 0) *scale = s;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-    const float2 v = d[i];
-    const float xh = v.x * s, xl = v.y * s;      // exact: s is a power of two
-    if (BF16) {
-      const __nv_bfloat16 h = __float2bfloat16_rn(xh);
-      const __nv_bfloat16 l = __float2bfloat16_rn((xh - __bfloat162float(h)) + xl);
-      hi[i] = __bfloat16_as_ushort(h);
-      lo[i] = __bfloat16_as_ushort(l);
-    } else {
-      const __half h = __float2half_rn(xh);
-      const __half l = __float2half_rn((xh - __half2float(h)) + xl);
-      hi[i] = __half_as_ushort(h);
-      lo[i] = __half_as_ushort(l);
+  const float4* d4 = reinterpret_cast<const float4*>(d);   // two double-float values per float4
+  ushort4* h4 = reinterpret_cast<ushort4*>(hi);
+  ushort4* l4 = reinterpret_cast<ushort4*>(lo);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count / 4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 a = d4[2 * i], b = d4[2 * i + 1];
+    const float xs[4] = {a.x * s, a.z * s, b.x * s, b.z * s};
+    const float xl[4] = {a.y * s, a.w * s, b.y * s, b.w * s};
+    unsigned short h[4], l[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (BF16) {
+        const __nv_bfloat16 hb = __float2bfloat16_rn(xs[k]);
+        h[k] = __bfloat16_as_ushort(hb);
+        l[k] = __bfloat16_as_ushort(__float2bfloat16_rn((xs[k] - __bfloat162float(hb)) + xl[k]));
+      } else {
+        const __half hh = __float2half_rn(xs[k]);
+        h[k] = __half_as_ushort(hh);
+        l[k] = __half_as_ushort(__float2half_rn((xs[k] - __half2float(hh)) + xl[k]));
+      }
     }
+    h4[i] = make_ushort4(h[0], h[1], h[2], h[3]);
+    l4[i] = make_ushort4(l[0], l[1], l[2], l[3]);
   }
 }
 
 // T0 = -sc (H - mu I) as a double-float (hi = rn32(v), lo = rn32(v - hi))
 __global__ void t0_init_d_kernel(int n, int np, const double* __restrict__ H, double mu, double sc,
                                  float2* __restrict__ T0, unsigned* amax, const double* __restrict__ dmu = nullptr) {
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (dmu) mu = dmu[0];
-  float vh = 0.0f;
-  if (idx < (size_t)np * np) {
+  const size_t count = (size_t)np * np;
+  float m = 0.0f;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx / np), j = (int)(idx % np);
     double v = 0.0;
     if (i < n && j < n) v = -sc * (H[idx] - (i == j ? mu : 0.0));
-    vh = (float)v;
+    const float vh = (float)v;
     T0[idx] = make_float2(vh, (float)(v - (double)vh));
+    m = fmaxf(m, fabsf(vh));
   }
-  raise_amax(amax, vh);
+  raise_amax(amax, m);
 }
 
 __global__ void level0_A1_d_kernel(int np, const float2* __restrict__ T0, const double* __restrict__ d,
                                    float* __restrict__ A1, unsigned* amax) {
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  float v = 0.0f;
-  if (idx < (size_t)np * np) {
+  const size_t count = (size_t)np * np;
+  float m = 0.0f;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(idx / np), j = (int)(idx % np);
     const float2 t = T0[idx];
-    v = (t.x + t.y) * (float)(d[i] + d[j]);
+    const float v = (t.x + t.y) * (float)(d[i] + d[j]);
     A1[idx] = v;
+    m = fmaxf(m, fabsf(v));
   }
-  raise_amax(amax, v);
+  raise_amax(amax, m);
 }
 
 __device__ __forceinline__ double df_val(float2 v) { return (double)v.x + (double)v.y; }
@@ -431,7 +406,7 @@ class EngineSplit : public Engine {
     const int np = m.np, n = m.n;
     const size_t cnt = (size_t)np * np;
     RET(cudaMemsetAsync(m.sT[0].amax, 0, sizeof(unsigned), s));
-    t0_init_d_kernel<<<nblk(cnt), 256, 0, s>>>(N, np, H, mu, sc, m.sT[0].d, m.sT[0].amax, dpar);
+    t0_init_d_kernel<<<ew_blocks(cnt), 256, 0, s>>>(N, np, H, mu, sc, m.sT[0].d, m.sT[0].amax, dpar);
     note_launch();
     RET(cudaGetLastError());
     RET(convert_d(s, m.sT[0], np));
@@ -445,9 +420,9 @@ class EngineSplit : public Engine {
       SplitMat* Wn = (W == &m.sY[k]) ? &m.sYw : &m.sY[k];
       RET(cudaMemsetAsync(W->amax, 0, sizeof(unsigned), s));
       if (k == 0)
-        axpi_f32_kernel<<<nblk(cnt), 256, 0, s>>>(np, 0.f, 1.f, m.sS.f, W->f, W->amax);        // W = S
+        axpi_f32_kernel<<<ew_blocks(cnt), 256, 0, s>>>(np, 0.f, 1.f, m.sS.f, W->f, W->amax);        // W = S
       else
-        axpi_f32_kernel<<<nblk(cnt), 256, 0, s>>>(np, (float)(1.0 - nc[k]), (float)nc[k], m.sY[k - 1].f, W->f,
+        axpi_f32_kernel<<<ew_blocks(cnt), 256, 0, s>>>(np, (float)(1.0 - nc[k]), (float)nc[k], m.sY[k - 1].f, W->f,
                                                  W->amax, dpar ? dpar + 1 + k : nullptr);  // W = (1-c) I + c W_{k-1}
       note_launch();
       RET(cudaGetLastError());
@@ -497,7 +472,7 @@ class EngineSplit : public Engine {
       em.out64 = true;
       em.nseg = nseg;
       if (k == 0) {
-        level0_A1_d_kernel<<<nblk(cnt), 256, 0, s>>>(np, m.sT[0].d, dvec, m.sA1.f, m.sA1.amax);
+        level0_A1_d_kernel<<<ew_blocks(cnt), 256, 0, s>>>(np, m.sT[0].d, dvec, m.sA1.f, m.sA1.amax);
         note_launch();
         RET(cudaGetLastError());
         em.dvec = dvec;
@@ -507,8 +482,9 @@ class EngineSplit : public Engine {
         eg.convert = false;
         eg.nseg = nseg;
         RET(gemm(s, np, m.sT[k], *T1, m.sG, eg, false, stats));                  // G = T T1
-        dim3 grid(np / 32, np / 32), block(32, 8);
-        transpose_add_f32_kernel<<<grid, block, 0, s>>>(np, m.sG.f, m.sA1.f, m.sA1.amax);
+        const unsigned tiles = (unsigned)((np / 32) * (np / 32));
+        transpose_add_f32_kernel<<<std::min(tiles, kEwBlocks), dim3(32, 8), 0, s>>>(np, m.sG.f, m.sA1.f,
+                                                                                   m.sA1.amax);
         note_launch();
         RET(cudaGetLastError());
         em.E64 = T1->d;                                                           // symmetric: read transposed
