@@ -246,7 +246,8 @@ xlbomd_status xlbomd_set(xlbomd_ctx* ctx, int sys, int what, const double* host_
 xlbomd_status xlbomd_sizes(xlbomd_ctx* ctx, int sys, int* natoms, int* n_orb, int* n_pad);
 
 /* Diagnostics: one split-precision tensor-core product C = A B^T (n x n, n a
- * multiple of 128, prec FP16x3 or BF16x3, sym = symmetric-output mode) of
+ * multiple of 128, prec FP16x3 or BF16x3; sym = 1: symmetric-output mode with
+ * a symmetric B; sym = 2: the symmetric-output pair product A B^T + B A^T) of
  * seeded uniform [-1, 1) matrices, compared on the device with the FP64
  * product of the same FP64 inputs.  result[0] = max |C_tc - C_fp64|,
  * result[2] = device wait-timeout flag, result[3] = ms per product.

@@ -128,11 +128,13 @@ def launch_count() -> int:
     return int(load().xlbomd_launch_count())
 
 
-def selftest_gemm(n: int, prec: str = "fp16x3", sym: bool = False):
+def selftest_gemm(n: int, prec: str = "fp16x3", sym=False):
     """One tensor-core split product of seeded matrices checked on the device
-    against the FP64 product: returns (max abs error, timeout flag, ms)."""
+    against the FP64 product: returns (max abs error, timeout flag, ms).
+    sym: False (A B^T), True (symmetric output), or 2 (A B^T + B A^T)."""
     out = np.zeros(4)
-    st = load().xlbomd_selftest_gemm(int(n), PREC[prec], int(bool(sym)), _dptr(out))
+    mode = 2 if (not isinstance(sym, bool) and sym == 2) else int(bool(sym))
+    st = load().xlbomd_selftest_gemm(int(n), PREC[prec], mode, _dptr(out))
     if st != XLBOMD_OK:
         raise XlbomdError(st, "xlbomd_selftest_gemm")
     return float(out[0]), int(out[2]), float(out[3])

@@ -109,28 +109,6 @@ __global__ void axpi_f32_kernel(int np, float a, float b, const float* __restric
   raise_amax(amax, m);
 }
 
-// A1 = G + G^T over 32 x 32 tiles, each block walking tiles grid-stride (one atomic per block)
-__global__ void transpose_add_f32_kernel(int np, const float* __restrict__ G, float* __restrict__ A1,
-                                         unsigned* amax) {
-  __shared__ float tile[32][33];
-  const int nt = np / 32;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  float m = 0.0f;
-  for (int t = blockIdx.x; t < nt * nt; t += gridDim.x) {
-    const int bx = (t % nt) * 32, by = (t / nt) * 32;
-    __syncthreads();   // the previous tile's reads of `tile` are done
-    for (int r = ty; r < 32; r += 8) tile[r][tx] = G[(size_t)(bx + r) * np + by + tx];
-    __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-      const size_t o = (size_t)(by + r) * np + bx + tx;
-      const float v = G[o] + tile[tx][r];
-      A1[o] = v;
-      m = fmaxf(m, fabsf(v));
-    }
-  }
-  raise_amax(amax, m);
-}
-
 __global__ void df_to_f64_kernel(size_t count, const float2* __restrict__ x, double* __restrict__ y) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) y[i] = (double)x[i].x + (double)x[i].y;
@@ -279,6 +257,7 @@ struct Epi {
   bool out64 = false;       // write C.d (and convert from it) instead of C.f
   bool convert = true;      // produce the split operand pair of C
   int nseg = 3;             // 3: hi*hi + hi*lo + lo*hi; 1: hi*hi only
+  int pairs = 1;            // 2: C = A B^T + B A^T
 };
 
 // The recursion is carried in correction form so that its exact leading
@@ -346,6 +325,7 @@ class EngineSplit : public Engine {
     RET(cudaMemsetAsync(C.amax, 0, sizeof(unsigned), s));
     TcArgs a;
     a.nseg = e.nseg;
+    a.pairs = e.pairs;
     a.sym = sym ? 1 : 0;
     a.bf16 = bf16_;
     a.alpha = e.alpha;
@@ -394,8 +374,8 @@ class EngineSplit : public Engine {
     // kind bits: 1 sym, 2 E, 4 E2, 8 E64, 16 E64 transposed, 32 FP64 output
     const int kind = (sym ? 1 : 0) | (e.E ? 2 : 0) | (e.E2 ? 4 : 0) | (e.E64 ? 8 : 0) | (e.e64_trans ? 16 : 0) |
                      (e.out64 ? 32 : 0);
-    RET(prof_end(s, 2.0 * (double)np * np * np * (sym ? 0.5 : 1.0), kind));
-    if (stats) stats[3] += sym ? 0.5 : 1.0;
+    RET(prof_end(s, 2.0 * (double)np * np * np * (sym ? 0.5 : 1.0) * e.pairs, kind));
+    if (stats) stats[3] += (sym ? 0.5 : 1.0) * e.pairs;
     if (!e.convert) return cudaSuccess;
     return e.out64 ? convert_d(s, C, np) : convert(s, C, np);
   }
@@ -478,15 +458,12 @@ class EngineSplit : public Engine {
         em.dvec = dvec;
         em.dvec_scale = 2.f;
       } else {
-        Epi eg;
-        eg.convert = false;
-        eg.nseg = nseg;
-        RET(gemm(s, np, m.sT[k], *T1, m.sG, eg, false, stats));                  // G = T T1
-        const unsigned tiles = (unsigned)((np / 32) * (np / 32));
-        transpose_add_f32_kernel<<<std::min(tiles, kEwBlocks), dim3(32, 8), 0, s>>>(np, m.sG.f, m.sA1.f,
-                                                                                   m.sA1.amax);
-        note_launch();
-        RET(cudaGetLastError());
+        // A1 = T T1 + T1 T (T, T1 symmetric): one symmetric-output product over the two K pairs
+        Epi ea;
+        ea.convert = false;
+        ea.nseg = nseg;
+        ea.pairs = 2;
+        RET(gemm(s, np, m.sT[k], *T1, m.sA1, ea, true, stats));
         em.E64 = T1->d;                                                           // symmetric: read transposed
         em.e64_trans = 1;
         em.beta64 = 2.0f;
@@ -637,7 +614,7 @@ cudaError_t alloc_matset_split(MatSet& m, cudaStream_t s) {
   struct W {
     SplitMat* m;
     int what;
-  } w[] = {{&m.sS, kF},  {&m.sQ, kF},  {&m.sYw, kF},  {&m.sG, kF},  {&m.sA1, kF},
+  } w[] = {{&m.sS, kF},  {&m.sQ, kF},  {&m.sYw, kF},  {&m.sA1, kF},
            {&m.sMt, kD}, {&m.sT1a, kD}, {&m.sT1b, kD}, {&m.sTmu, kD}};
   for (auto& x : w) {
     RET(alloc_split(*x.m, np, sf + idx, su + idx, x.what, s));
@@ -651,7 +628,7 @@ void free_matset_split(MatSet& m) {
   for (auto& x : m.sY) free_split(x);
   m.sT.clear();
   m.sY.clear();
-  SplitMat* w[] = {&m.sS, &m.sQ, &m.sYw, &m.sG, &m.sA1, &m.sMt, &m.sT1a, &m.sT1b, &m.sTmu};
+  SplitMat* w[] = {&m.sS, &m.sQ, &m.sYw, &m.sA1, &m.sMt, &m.sT1a, &m.sT1b, &m.sTmu};
   for (SplitMat* x : w) free_split(*x);
   if (m.tc_plan) cudaFree(m.tc_plan);
   m.tc_plan = nullptr;
@@ -715,7 +692,8 @@ int selftest_gemm(int n, int prec, int sym, double* result) {
   if (n % 128 || n <= 0 || (prec != XLBOMD_FP16x3_ID && prec != XLBOMD_BF16x3_ID)) return -1;
   EngineSplit eng(prec);
   const size_t cnt = (size_t)n * n;
-  double *A = nullptr, *B = nullptr, *Cref = nullptr, *out = nullptr;
+  double *A = nullptr, *B = nullptr, *Cref = nullptr, *Cref2 = nullptr, *out = nullptr;
+  const bool pair = (sym == 2);   // C = A B^T + B A^T
   float* scal = nullptr;
   SplitMat sa, sb, sc;
   cudaStream_t s = nullptr;
@@ -723,7 +701,8 @@ int selftest_gemm(int n, int prec, int sym, double* result) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   float ms = 0.f;
   if (cudaMalloc((void**)&A, cnt * 8) || cudaMalloc((void**)&B, cnt * 8) || cudaMalloc((void**)&Cref, cnt * 8) ||
-      cudaMalloc((void**)&out, 8) || cudaMalloc((void**)&scal, 6 * sizeof(float)))
+      cudaMalloc((void**)&out, 8) || cudaMalloc((void**)&scal, 6 * sizeof(float)) ||
+      (pair && cudaMalloc((void**)&Cref2, cnt * 8)))
     goto done;
   cudaMemset(scal, 0, 6 * sizeof(float));
   if (alloc_split(sa, n, scal, (unsigned*)scal + 3, kF, s) || alloc_split(sb, n, scal + 1, (unsigned*)scal + 4, kF, s) ||
@@ -740,19 +719,30 @@ int selftest_gemm(int n, int prec, int sym, double* result) {
   if (eng.convert(s, sa, n) || eng.convert(s, sb, n)) goto done;
   {
     EpiF64 e;
-    if (gemm_f64_nt(s, n, n, n, A, n, B, n, Cref, n, e, sym != 0)) goto done;
+    if (gemm_f64_nt(s, n, n, n, A, n, B, n, Cref, n, e, sym == 1)) goto done;
+    if (pair) {   // Cref2 = B A^T + A B^T
+      EpiF64 e2;
+      e2.E = Cref;
+      e2.lde = n;
+      e2.beta = 1.0;
+      if (gemm_f64_nt(s, n, n, n, B, n, A, n, Cref2, n, e2, false)) goto done;
+    }
   }
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  if (eng.gemm(s, n, sa, sb, sc, Epi(), sym != 0, nullptr)) goto done;
-  cudaEventRecord(e0, s);
-  for (int r = 0; r < 5; ++r)
-    if (eng.gemm(s, n, sa, sb, sc, Epi(), sym != 0, nullptr)) goto done;
+  {
+    Epi ep;
+    ep.pairs = pair ? 2 : 1;
+    if (eng.gemm(s, n, sa, sb, sc, ep, sym != 0, nullptr)) goto done;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 5; ++r)
+      if (eng.gemm(s, n, sa, sb, sc, ep, sym != 0, nullptr)) goto done;
+  }
   cudaEventRecord(e1, s);
   if (cudaDeviceSynchronize() != cudaSuccess) goto done;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaMemset(out, 0, 8);
-  max_abs_diff_kernel<<<304, 256>>>(cnt, sc.f, Cref, out);
+  max_abs_diff_kernel<<<304, 256>>>(cnt, sc.f, pair ? Cref2 : Cref, out);
   note_launch();
   if (cudaDeviceSynchronize() != cudaSuccess) goto done;
   {
@@ -775,6 +765,7 @@ done:
   if (A) cudaFree(A);
   if (B) cudaFree(B);
   if (Cref) cudaFree(Cref);
+  if (Cref2) cudaFree(Cref2);
   if (out) cudaFree(out);
   if (scal) cudaFree(scal);
   return rc;

@@ -172,6 +172,21 @@ __device__ __forceinline__ bool tile_coords(const TcArgs& a, int id, int& tm, in
   return tm >= 0 && tm < a.n / BM && tn >= 0 && tn < a.tiles_n;
 }
 
+// Segment of K block kb: pair p (0: A B^T, 1: the swapped pair B A^T), kind 0 = hi*hi
+// (accumulator 0), 1 = hi*lo, 2 = lo*hi (accumulator 1).  The hi*hi segments of every pair come
+// first, so accumulator 0 is written only in the first nseg-th of a tile's K blocks.
+__device__ __forceinline__ void seg_of(int kb, int nk, int pairs, int& p, int& kind) {
+  const int si = kb / nk;
+  if (si < pairs) {
+    p = si;
+    kind = 0;
+  } else {
+    const int r = si - pairs;
+    p = r >> 1;
+    kind = 1 + (r & 1);
+  }
+}
+
 // L2 prefetch of the side inputs of tile (tm, tn) by the 128 epilogue threads (t = 0..127)
 template <int BN>
 __device__ __forceinline__ void prefetch_sides(const TcArgs& a, int tm, int tn, int t) {
@@ -303,7 +318,9 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, float (&v)[32], 
 template <int BN>
 __global__ void __launch_bounds__(192, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
-                   const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, TcArgs a) {
+                   const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
+                   const __grid_constant__ CUtensorMap mA2hi, const __grid_constant__ CUtensorMap mA2lo,
+                   const __grid_constant__ CUtensorMap mB2hi, const __grid_constant__ CUtensorMap mB2lo, TcArgs a) {
   constexpr int B_BYTES = BN * BK * 2;
   constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators: 256 or 512 columns
   extern __shared__ uint8_t smem_raw[];
@@ -358,7 +375,7 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t tmem = *tmem_slot;
 
   const int nk = a.K / BK;
-  const int total = a.nseg * nk;
+  const int total = a.nseg * a.pairs * nk;
   bool ok = true;
 
   if (warp == 0) {
@@ -371,9 +388,11 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-        const int seg = kb / nk, kk = a.k0 + (kb % nk) * BK;
-        const CUtensorMap* ma = (seg == 2) ? &mAlo : &mAhi;
-        const CUtensorMap* mb = (seg == 1) ? &mBlo : &mBhi;
+        const int kk = a.k0 + (kb % nk) * BK;
+        int pr, kind;
+        seg_of(kb, nk, a.pairs, pr, kind);
+        const CUtensorMap* ma = (kind == 2) ? (pr ? &mA2lo : &mAlo) : (pr ? &mA2hi : &mAhi);
+        const CUtensorMap* mb = (kind == 1) ? (pr ? &mB2lo : &mBlo) : (pr ? &mB2hi : &mBhi);
         tma_load_2d(sA + s * A_BYTES, ma, kk, tm * BM, &full[s]);
         tma_load_2d(sB + s * B_BYTES, mb, kk, tn * BN, &full[s]);
       }
@@ -392,9 +411,10 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const bool corr = kb >= nk;                       // hi*lo or lo*hi segment
+        const int nk0 = a.pairs * nk;                     // K blocks of the hi*hi segments
+        const bool corr = kb >= nk0;                      // hi*lo or lo*hi segment
         const uint32_t dcol = corr ? (uint32_t)BN : 0u;
-        const bool first = (kb == 0) || (kb == nk);
+        const bool first = (kb == 0) || (kb == nk0);
 #pragma unroll
         for (int j = 0; j < BK / 16; ++j) {
           const uint64_t ad = smem_desc(sA + s * A_BYTES + j * 32);
@@ -480,6 +500,8 @@ template <int BN>
 __global__ void __launch_bounds__(192, 1)
     gemm_tc_persistent_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                               const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
+                   const __grid_constant__ CUtensorMap mA2hi, const __grid_constant__ CUtensorMap mA2lo,
+                   const __grid_constant__ CUtensorMap mB2hi, const __grid_constant__ CUtensorMap mB2lo,
                               TcArgs a, int ntiles) {
   constexpr int B_BYTES = BN * BK * 2;
   constexpr uint32_t TMEM_COLS = 2 * BN;
@@ -522,7 +544,7 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t tmem = *tmem_slot;
 
   const int nk = a.K / BK;
-  const int total = a.nseg * nk;
+  const int total = a.nseg * a.pairs * nk;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -545,9 +567,11 @@ __global__ void __launch_bounds__(192, 1)
             break;
           }
           mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-          const int seg = kb / nk, kk = a.k0 + (kb % nk) * BK;
-          const CUtensorMap* ma = (seg == 2) ? &mAlo : &mAhi;
-          const CUtensorMap* mb = (seg == 1) ? &mBlo : &mBhi;
+          const int kk = a.k0 + (kb % nk) * BK;
+          int pr, kind;
+          seg_of(kb, nk, a.pairs, pr, kind);
+          const CUtensorMap* ma = (kind == 2) ? (pr ? &mA2lo : &mAlo) : (pr ? &mA2hi : &mAhi);
+          const CUtensorMap* mb = (kind == 1) ? (pr ? &mB2lo : &mBlo) : (pr ? &mB2hi : &mBhi);
           tma_load_2d(sA + s * A_BYTES, ma, kk, tm * BM, &full[s]);
           tma_load_2d(sB + s * B_BYTES, mb, kk, tn * BN, &full[s]);
         }
@@ -566,7 +590,8 @@ __global__ void __launch_bounds__(192, 1)
         bool ok = true;
         for (int kb = 0; kb < total; ++kb, ++g) {
           // the previous tile's epilogue must have released the accumulator this segment writes
-          if (it > 0 && (kb == 0 || kb == nk)) {
+          const int nk0 = a.pairs * nk;                   // K blocks of the hi*hi segments
+          if (it > 0 && (kb == 0 || kb == nk0)) {
             if (!mbar_wait(kb == 0 ? acc0_free : acc1_free, (uint32_t)((it - 1) & 1)) || *abort_flag) {
               ok = false;
               break;
@@ -580,9 +605,9 @@ __global__ void __launch_bounds__(192, 1)
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const bool corr = kb >= nk;
+          const bool corr = kb >= nk0;
           const uint32_t dcol = corr ? (uint32_t)BN : 0u;
-          const bool first = (kb == 0) || (kb == nk);
+          const bool first = (kb == 0) || (kb == nk0);
 #pragma unroll
           for (int j = 0; j < BK / 16; ++j) {
             const uint64_t ad = smem_desc(sA + s * A_BYTES + j * 32);
@@ -771,10 +796,22 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
   if (n % 128 != 0 || n <= 0) return cudaErrorInvalidValue;
   const bool wide = (n % 256 == 0);
   const int bn = wide ? 256 : 128;
-  CUtensorMap mAhi, mAlo, mBhi, mBlo;
+  CUtensorMap mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo;
   if (!make_map(&mAhi, Ahi, n, BM, args.bf16) || !make_map(&mAlo, Alo ? Alo : Ahi, n, BM, args.bf16) ||
       !make_map(&mBhi, Bhi, n, bn, args.bf16) || !make_map(&mBlo, Blo ? Blo : Bhi, n, bn, args.bf16))
     return cudaErrorInvalidValue;
+  if (args.pairs != 1 && args.pairs != 2) return cudaErrorInvalidValue;
+  if (args.pairs == 2) {
+    // the swapped pair: B in the A role (BM-row boxes), A in the B role (bn-row boxes)
+    if (!make_map(&mA2hi, Bhi, n, BM, args.bf16) || !make_map(&mA2lo, Blo ? Blo : Bhi, n, BM, args.bf16) ||
+        !make_map(&mB2hi, Ahi, n, bn, args.bf16) || !make_map(&mB2lo, Alo ? Alo : Ahi, n, bn, args.bf16))
+      return cudaErrorInvalidValue;
+  } else {
+    mA2hi = mAhi;
+    mA2lo = mAlo;
+    mB2hi = mBhi;
+    mB2lo = mBlo;
+  }
   args.n = n;
   args.K = args.kext > 0 ? args.kext : n;
   if (args.k0 < 0 || args.k0 % 64 != 0 || args.K % 64 != 0 || args.k0 + args.K > n) return cudaErrorInvalidValue;
@@ -797,7 +834,7 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
         attr = cudaFuncSetAttribute(gemm_tc_persistent_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
       });
       if (attr != cudaSuccess) return attr;
-      gemm_tc_persistent_kernel<256><<<grid, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, args, nblocks);
+      gemm_tc_persistent_kernel<256><<<grid, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo, args, nblocks);
     } else {
       static std::once_flag once;
       static cudaError_t attr = cudaSuccess;
@@ -806,7 +843,7 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
         attr = cudaFuncSetAttribute(gemm_tc_persistent_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
       });
       if (attr != cudaSuccess) return attr;
-      gemm_tc_persistent_kernel<128><<<grid, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, args, nblocks);
+      gemm_tc_persistent_kernel<128><<<grid, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo, args, nblocks);
     }
     note_launch();
     return cudaGetLastError();
@@ -819,7 +856,7 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
       attr = cudaFuncSetAttribute(gemm_tc_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
     });
     if (attr != cudaSuccess) return attr;
-    gemm_tc_kernel<256><<<nblocks, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, args);
+    gemm_tc_kernel<256><<<nblocks, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo, args);
     note_launch();
   } else {
     static std::once_flag once;
@@ -829,7 +866,7 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
       attr = cudaFuncSetAttribute(gemm_tc_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
     });
     if (attr != cudaSuccess) return attr;
-    gemm_tc_kernel<128><<<nblocks, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, args);
+    gemm_tc_kernel<128><<<nblocks, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo, args);
     note_launch();
   }
   return cudaGetLastError();

@@ -36,7 +36,7 @@ struct MatSet {
   double *T1a = nullptr, *T1b = nullptr, *Tmu = nullptr;
   // split engines
   std::vector<SplitMat> sT, sY;
-  SplitMat sS, sQ, sYw, sG, sA1, sMt, sT1a, sT1b, sTmu;
+  SplitMat sS, sQ, sYw, sA1, sMt, sT1a, sT1b, sTmu;
   void* tc_plan = nullptr;   // device scalars (scales, max |x|) of the split engine
   double t0max = 0.0;        // spectral bound |T_0| of the last expansion
   // FP64 work matrices of the split engine's entropy (allocated on first use)

@@ -15,6 +15,7 @@ struct TcArgs {
   const float* P = nullptr;       // FP32 partial result added after scaling, read row-major
                                   // at the output's own positions (the other K part of a split-K)
   int nseg = 3;                   // 1: hi only; 3: hi*hi + hi*lo + lo*hi
+  int pairs = 1;                  // 2: C = A B^T + B A^T (the swapped pair as a second K range)
   int sym = 0;                    // symmetric output (upper tiles, mirrored)
   int bf16 = 0;                   // operand type: 0 FP16, 1 BF16
   int tiles_n = 0;                // set by gemm_tc

@@ -40,6 +40,17 @@ def test_tensor_core_product_matches_fp64(X, n, sym, prec, bound):
     assert err < bound * n, (err, ms)
 
 
+@pytest.mark.parametrize("n", [256, 384, 1024, 4096])
+@pytest.mark.parametrize("prec,bound", [("fp16x3", 1e-6), ("bf16x3", 2e-5)])
+def test_pair_product_matches_fp64(X, n, prec, bound):
+    # C = A B^T + B A^T as one symmetric-output product over two K ranges (the
+    # A1 = T T1 + T1 T of the response chains); twice the sums of one product
+    err, flag, ms = X.binding.selftest_gemm(n, prec, 2)
+    print(prec, n, "pair", err, ms)
+    assert flag == 0
+    assert err < 2 * bound * n, (err, ms)
+
+
 @pytest.mark.parametrize("prec", ["fp16x3", "bf16x3"])
 @pytest.mark.parametrize("case", ["tiny24", "ragged37"])
 def test_split_density_against_oracle(X, prec, case):
