@@ -40,7 +40,7 @@ def test_tensor_core_product_matches_fp64(X, n, sym, prec, bound):
     assert err < bound * n, (err, ms)
 
 
-@pytest.mark.parametrize("n", [256, 384, 1024, 4096])
+@pytest.mark.parametrize("n", [256, 384, 1024, 4096, 8192])
 @pytest.mark.parametrize("prec,bound", [("fp16x3", 1e-6), ("bf16x3", 2e-5)])
 def test_pair_product_matches_fp64(X, n, prec, bound):
     # C = A B^T + B A^T as one symmetric-output product over two K ranges (the
