@@ -33,7 +33,7 @@ inline unsigned nblk(size_t count, int tpb = 256) { return (unsigned)((count + t
 constexpr unsigned kEwBlocks = 152 * 16;
 inline unsigned ew_blocks(size_t count) { return (unsigned)std::min<size_t>(nblk(count), kEwBlocks); }
 
-// products of at least this size run as two half-K launches (split-K)
+// products of at least this size split their hi*hi sums over both accumulators
 constexpr int kSplitKMin = 8192;
 
 // Raise *amax to the block's max |v| with one atomic per block (all threads
@@ -274,7 +274,6 @@ class EngineSplit : public Engine {
   ~EngineSplit() override {
     for (auto& kv : tiles_) cudaFree(kv.second.first);
     if (err_) cudaFree(err_);
-    if (part_) cudaFree(part_);
   }
 
   cudaError_t convert(cudaStream_t s, SplitMat& m, int np) {
@@ -349,27 +348,9 @@ class EngineSplit : public Engine {
     a.err = err_;
     const int n128 = tl.second.first, n256 = tl.second.second;
     RET(prof_begin(s));
-    if (np >= kSplitKMin) {
-      // split-K: the tensor core truncates as it accumulates, so the error of a K-long sum grows
-      // with K; two half-K launches halve it.  The first writes alpha A B^T over K[0, n/2) to an
-      // FP32 partial, the second adds it to the rest in its epilogue.
-      if (!part_) RET(cudaMalloc((void**)&part_, sizeof(float) * (size_t)np * np));
-      TcArgs a1 = a;
-      a1.k0 = 0;
-      a1.kext = np / 2;
-      a1.E = a1.E2 = nullptr;
-      a1.E64 = nullptr;
-      a1.diag = 0.0f;
-      a1.dvec = nullptr;
-      a1.ndvec = 0;
-      a1.C = part_;
-      a1.C64 = nullptr;
-      a1.amax = nullptr;
-      RET(gemm_tc(s, np, A.hi, A.lo, B.hi, B.lo, a1, tl.first, tl.first + 2 * n128, n128, n256));
-      a.k0 = np / 2;
-      a.kext = np - np / 2;
-      a.P = part_;
-    }
+    // large products: split the hi*hi sums over both accumulators (the tensor core truncates as it
+    // accumulates, so a K-long sum's error grows with K)
+    a.split_acc = (np >= kSplitKMin) ? 1 : 0;
     RET(gemm_tc(s, np, A.hi, A.lo, B.hi, B.lo, a, tl.first, tl.first + 2 * n128, n128, n256));
     // kind bits: 1 sym, 2 E, 4 E2, 8 E64, 16 E64 transposed, 32 FP64 output
     const int kind = (sym ? 1 : 0) | (e.E ? 2 : 0) | (e.E2 ? 4 : 0) | (e.E64 ? 8 : 0) | (e.e64_trans ? 16 : 0) |
@@ -541,7 +522,6 @@ class EngineSplit : public Engine {
  private:
   int bf16_;
   int probe_nseg_ = 3;
-  float* part_ = nullptr;   // split-K partial (np x np FP32), allocated for np >= kSplitKMin
   std::unordered_map<int, std::pair<int*, std::pair<int, int>>> tiles_;
 };
 

@@ -172,19 +172,62 @@ __device__ __forceinline__ bool tile_coords(const TcArgs& a, int id, int& tm, in
   return tm >= 0 && tm < a.n / BM && tn >= 0 && tn < a.tiles_n;
 }
 
-// Segment of K block kb: pair p (0: A B^T, 1: the swapped pair B A^T), kind 0 = hi*hi
-// (accumulator 0), 1 = hi*lo, 2 = lo*hi (accumulator 1).  The hi*hi segments of every pair come
-// first, so accumulator 0 is written only in the first nseg-th of a tile's K blocks.
-__device__ __forceinline__ void seg_of(int kb, int nk, int pairs, int& p, int& kind) {
-  const int si = kb / nk;
-  if (si < pairs) {
-    p = si;
-    kind = 0;
+// The K blocks of a tile run as a few segments, each one operand pair pr (0: A B^T, 1: the
+// swapped pair B A^T) and split part kind (0 = hi*hi, 1 = hi*lo, 2 = lo*hi) over K blocks
+// [k0, k1).  Default order: the hi*hi segments of every pair (accumulator 0), then the
+// corrections (accumulator 1).  split_acc (large n): the first half of the hi*hi K blocks
+// (accumulator 0), the corrections into accumulator 1 while it is still small, then the second
+// half of the hi*hi K blocks on top of accumulator 1 -- the tensor core truncates as it
+// accumulates, so each large sum is half as long.  Accumulator 1 starts at K block acc1_start.
+struct KSeg {
+  int seg, kidx, k1, pr, kind;
+};
+
+__device__ __forceinline__ void kseg_decode(const TcArgs& a, int nk, KSeg& q) {
+  const int P = a.pairs, NC = (a.nseg - 1) * a.pairs;   // hi*hi pairs, correction segments
+  int k0 = 0;
+  q.k1 = nk;
+  if (!a.split_acc) {
+    if (q.seg < P) {
+      q.pr = q.seg;
+      q.kind = 0;
+    } else {
+      const int r = q.seg - P;
+      q.pr = r >> 1;
+      q.kind = 1 + (r & 1);
+    }
+  } else if (q.seg == 0 || q.seg > NC) {
+    const bool second = q.seg > NC;
+    q.kind = 0;
+    if (P == 2) {
+      q.pr = second ? 1 : 0;
+    } else {
+      q.pr = 0;
+      k0 = second ? nk / 2 : 0;
+      q.k1 = second ? nk : nk / 2;
+    }
   } else {
-    const int r = si - pairs;
-    p = r >> 1;
-    kind = 1 + (r & 1);
+    const int r = q.seg - 1;
+    q.pr = r >> 1;
+    q.kind = 1 + (r & 1);
   }
+  q.kidx = k0;
+}
+
+__device__ __forceinline__ void kseg_begin(const TcArgs& a, int nk, KSeg& q) {
+  q.seg = 0;
+  kseg_decode(a, nk, q);
+}
+
+__device__ __forceinline__ void kseg_next(const TcArgs& a, int nk, KSeg& q) {
+  if (++q.kidx == q.k1) {
+    ++q.seg;
+    kseg_decode(a, nk, q);
+  }
+}
+
+__device__ __forceinline__ int acc1_start(const TcArgs& a, int nk) {
+  return a.split_acc ? a.pairs * nk / 2 : a.pairs * nk;
 }
 
 // L2 prefetch of the side inputs of tile (tm, tn) by the 128 epilogue threads (t = 0..127)
@@ -224,15 +267,6 @@ __device__ __forceinline__ void epilogue_chunk(const TcArgs& a, float (&v)[32], 
                                                float& vmax) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] *= inv;
-  if (a.P) {
-    // the other K part of a split-K product, row-major: staged so that 32 lanes read whole rows
-#pragma unroll 8
-    for (int i = 0; i < 32; ++i) tx[i][lane] = a.P[(size_t)(row0 + i) * a.ldc + col0 + lane];
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] += tx[lane][i];
-    __syncwarp();
-  }
   // FP32 side inputs of symmetric value, read transposed: for a fixed
   // column the 32 lanes read 32 consecutive rows (coalesced)
   if (a.E) {
@@ -380,7 +414,9 @@ __global__ void __launch_bounds__(192, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      for (int kb = 0; kb < total; ++kb) {
+      KSeg q;
+      kseg_begin(a, nk, q);
+      for (int kb = 0; kb < total; ++kb, kseg_next(a, nk, q)) {
         const int s = kb % STAGES;
         const uint32_t ph = (kb / STAGES) & 1;
         if (kb >= STAGES && !mbar_wait(&empty[s], ph ^ 1)) {
@@ -388,11 +424,9 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-        const int kk = a.k0 + (kb % nk) * BK;
-        int pr, kind;
-        seg_of(kb, nk, a.pairs, pr, kind);
-        const CUtensorMap* ma = (kind == 2) ? (pr ? &mA2lo : &mAlo) : (pr ? &mA2hi : &mAhi);
-        const CUtensorMap* mb = (kind == 1) ? (pr ? &mB2lo : &mBlo) : (pr ? &mB2hi : &mBhi);
+        const int kk = q.kidx * BK;
+        const CUtensorMap* ma = (q.kind == 2) ? (q.pr ? &mA2lo : &mAlo) : (q.pr ? &mA2hi : &mAhi);
+        const CUtensorMap* mb = (q.kind == 1) ? (q.pr ? &mB2lo : &mBlo) : (q.pr ? &mB2hi : &mBhi);
         tma_load_2d(sA + s * A_BYTES, ma, kk, tm * BM, &full[s]);
         tma_load_2d(sB + s * B_BYTES, mb, kk, tn * BN, &full[s]);
       }
@@ -411,9 +445,8 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int nk0 = a.pairs * nk;                     // K blocks of the hi*hi segments
-        const bool corr = kb >= nk0;                      // hi*lo or lo*hi segment
-        const uint32_t dcol = corr ? (uint32_t)BN : 0u;
+        const int nk0 = acc1_start(a, nk);                // first K block of accumulator 1
+        const uint32_t dcol = kb >= nk0 ? (uint32_t)BN : 0u;
         const bool first = (kb == 0) || (kb == nk0);
 #pragma unroll
         for (int j = 0; j < BK / 16; ++j) {
@@ -462,7 +495,7 @@ __global__ void __launch_bounds__(192, 1)
       for (int ch = 0; ch < BN / 32; ++ch) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 32), v);
-        if (a.nseg > 1) {
+        if (a.nseg > 1 || a.split_acc) {
           float w[32];
           tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(BN + ch * 32), w);
 #pragma unroll
@@ -557,7 +590,9 @@ __global__ void __launch_bounds__(192, 1)
           *abort_flag = 1;
           break;
         }
-        for (int kb = 0; kb < total; ++kb, ++g) {
+        KSeg q;
+        kseg_begin(a, nk, q);
+        for (int kb = 0; kb < total; ++kb, ++g, kseg_next(a, nk, q)) {
           const int s = g % STAGES;
           const uint32_t ph = (g / STAGES) & 1;
           if (g >= STAGES && !mbar_wait(&empty[s], ph ^ 1)) {
@@ -567,11 +602,9 @@ __global__ void __launch_bounds__(192, 1)
             break;
           }
           mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-          const int kk = a.k0 + (kb % nk) * BK;
-          int pr, kind;
-          seg_of(kb, nk, a.pairs, pr, kind);
-          const CUtensorMap* ma = (kind == 2) ? (pr ? &mA2lo : &mAlo) : (pr ? &mA2hi : &mAhi);
-          const CUtensorMap* mb = (kind == 1) ? (pr ? &mB2lo : &mBlo) : (pr ? &mB2hi : &mBhi);
+          const int kk = q.kidx * BK;
+          const CUtensorMap* ma = (q.kind == 2) ? (q.pr ? &mA2lo : &mAlo) : (q.pr ? &mA2hi : &mAhi);
+          const CUtensorMap* mb = (q.kind == 1) ? (q.pr ? &mB2lo : &mBlo) : (q.pr ? &mB2hi : &mBhi);
           tma_load_2d(sA + s * A_BYTES, ma, kk, tm * BM, &full[s]);
           tma_load_2d(sB + s * B_BYTES, mb, kk, tn * BN, &full[s]);
         }
@@ -590,7 +623,7 @@ __global__ void __launch_bounds__(192, 1)
         bool ok = true;
         for (int kb = 0; kb < total; ++kb, ++g) {
           // the previous tile's epilogue must have released the accumulator this segment writes
-          const int nk0 = a.pairs * nk;                   // K blocks of the hi*hi segments
+          const int nk0 = acc1_start(a, nk);              // first K block of accumulator 1
           if (it > 0 && (kb == 0 || kb == nk0)) {
             if (!mbar_wait(kb == 0 ? acc0_free : acc1_free, (uint32_t)((it - 1) & 1)) || *abort_flag) {
               ok = false;
@@ -605,8 +638,7 @@ __global__ void __launch_bounds__(192, 1)
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const bool corr = kb >= nk0;
-          const uint32_t dcol = corr ? (uint32_t)BN : 0u;
+          const uint32_t dcol = kb >= nk0 ? (uint32_t)BN : 0u;
           const bool first = (kb == 0) || (kb == nk0);
 #pragma unroll
           for (int j = 0; j < BK / 16; ++j) {
@@ -644,7 +676,8 @@ __global__ void __launch_bounds__(192, 1)
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // pass 1: accumulator 1 <- accumulator 0 + accumulator 1, then release accumulator 0
-      if (a.nseg > 1) {
+      const bool two_acc = a.nseg > 1 || a.split_acc;
+      if (two_acc) {
         for (int ch = 0; ch < BN / 32; ++ch) {
           float v[32], w[32];
           tmem_ld32(tmem + lane_base + (uint32_t)(ch * 32), v);
@@ -659,7 +692,7 @@ __global__ void __launch_bounds__(192, 1)
         if (lane == 0) mbar_arrive(acc0_free);
       }
       // pass 2: the epilogue proper from the summed accumulator
-      const uint32_t src = a.nseg > 1 ? (uint32_t)BN : 0u;
+      const uint32_t src = two_acc ? (uint32_t)BN : 0u;
       const int row0 = tm * BM + q * 32;
       const int row = row0 + lane;
       float vmax = 0.0f;
@@ -673,7 +706,7 @@ __global__ void __launch_bounds__(192, 1)
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) {
-        if (a.nseg == 1) mbar_arrive(acc0_free);
+        if (!two_acc) mbar_arrive(acc0_free);
         mbar_arrive(acc1_free);
       }
     }
@@ -813,8 +846,8 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
     mB2lo = mBlo;
   }
   args.n = n;
-  args.K = args.kext > 0 ? args.kext : n;
-  if (args.k0 < 0 || args.k0 % 64 != 0 || args.K % 64 != 0 || args.k0 + args.K > n) return cudaErrorInvalidValue;
+  args.K = n;
+  if (args.split_acc && n / BK < 2) return cudaErrorInvalidValue;   // both accumulators get K blocks
   args.tiles_n = n / bn;
   int nblocks;
   if (args.sym) {

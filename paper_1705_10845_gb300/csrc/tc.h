@@ -8,12 +8,9 @@
 namespace xl {
 
 struct TcArgs {
-  int K = 0;                      // K extent of this launch (set by gemm_tc: kext, or n)
+  int K = 0;                      // inner dimension (set by gemm_tc)
   int n = 0;                      // matrix size (set by gemm_tc)
-  int k0 = 0;                     // first K column of this launch (split-K)
-  int kext = 0;                   // K extent requested (0: the whole n)
-  const float* P = nullptr;       // FP32 partial result added after scaling, read row-major
-                                  // at the output's own positions (the other K part of a split-K)
+  int split_acc = 0;              // 1: the hi*hi K blocks split over both accumulators (below)
   int nseg = 3;                   // 1: hi only; 3: hi*hi + hi*lo + lo*hi
   int pairs = 1;                  // 2: C = A B^T + B A^T (the swapped pair as a second K range)
   int sym = 0;                    // symmetric output (upper tiles, mirrored)
