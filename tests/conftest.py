@@ -1,11 +1,22 @@
+import importlib.util
 import os
 import sys
 
 import pytest
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+
+
+@pytest.fixture(scope="session")
+def golden():
+    """The readers of tests/golden/ (values printed in the paper)."""
+    spec = importlib.util.spec_from_file_location("xlbomd_golden", os.path.join(HERE, "golden", "__init__.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
 
 
 def pytest_configure(config):

@@ -62,6 +62,15 @@ def test_forces_sum_to_zero(small):
     assert np.allclose(ev.F.sum(axis=0), 0.0, atol=1e-11)
 
 
+def test_table_I_of_the_oracle_is_the_printed_table(golden):
+    printed = golden.table_i()
+    assert sorted(printed) == sorted(O.TABLE_I) == [5, 6, 7]
+    for kmax, (kappa, alpha, c) in printed.items():
+        okappa, oalpha, oc = O.TABLE_I[kmax]
+        assert (okappa, oalpha) == (kappa, alpha)
+        assert tuple(oc) == c
+
+
 @pytest.mark.parametrize("kmax", [5, 6, 7])
 def test_table_I_coefficients_annihilate_constant_and_linear_histories(kmax):
     kappa, alpha, c = O.TABLE_I[kmax]
