@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--kernel-prec", type=int, default=1, choices=[0, 1],
                     help="1 (default): the kernel's probe chains take one 16-bit product instead of three; "
                          "0: three, as the expansion")
+    ap.add_argument("--mu-prec", type=int, default=1, choices=[0, 1],
+                    help="1 (default): the chemical-potential chain (dD/dmu) takes one 16-bit product instead "
+                         "of three; 0: three, as the expansion")
     ap.add_argument("--rep-A", type=float, default=40.0,
                     help="pair repulsion A exp(-r/0.3 A) (eV): the model's atoms collapse without it in long runs")
     ap.add_argument("--e2e-steps", type=int, default=None)
@@ -83,6 +86,7 @@ def workload_config(a, parallel):
         "natoms": a.natoms, "n_orb": 4 * a.natoms, "Te_K": a.Te, "n_squarings": a.nsq, "rank_m": a.rank,
         "pair_repulsion": f"{a.rep_A:g} exp(-r/0.3 A) eV" if a.rep_A else "off",
         "kernel_probe_products": "one 16-bit product" if a.kernel_prec else "three (full split)",
+        "mu_chain_products": "one 16-bit product" if a.mu_prec else "three (full split)",
         "prec": a.prec, "parallelism": parallel,
         "l2": "inputs larger than L2: about 11 GB of expansion matrices are rewritten every step",
     }
@@ -171,9 +175,14 @@ def peaks():
         return 1900.0, 1700.0, 6800.0, "fallback"
 
 
+def single_product_chains(a):
+    chains = [c for c, on in (("probe", a.kernel_prec), ("mu", a.mu_prec)) if on]
+    return f"1 in the {' and '.join(chains)} chains" if chains else "3 in every chain"
+
+
 def make_params(X, a, prec):
     return X.default_params(Te=a.Te, n_sq=a.nsq, rank_m=a.rank, dt=0.25, mix_alpha=ALPHA_MIX,
-                            rep_A=a.rep_A, rep_rho=0.3, kernel_prec=a.kernel_prec,
+                            rep_A=a.rep_A, rep_rho=0.3, kernel_prec=a.kernel_prec, mu_prec=a.mu_prec,
                             kernel_c=1.0 - 1.0 / ALPHA_MIX, prec=prec,
                             scf_tol=1e-10 if prec == "fp64" else 1e-5, scf_mode=1, kernel_auto=1,
                             mu_tol=1e-9 if prec == "fp64" else 1e-3, scf_max_iter=200)
@@ -483,7 +492,7 @@ def main():
                      "kernel": f"gemm_tc {gemm_variant()} kernel (split-precision tcgen05 product)",
                      "note": f"algorithmic 2n^3 per product (n^3 when symmetric-output) over CUDA-event time of "
                              f"{int(gemm_launches)} launches; each split product runs 3 half-precision "
-                             f"tensor products ({'1 in the probe chains' if a.kernel_prec else 'also in the probe chains'}), "
+                             f"tensor products ({single_product_chains(a)}), "
                              f"so tensor-pipe work is up to 3x the algorithmic flops; peak = {src} sustained bf16"},
         "foe_tflops": (gemm_flops / sec / 1e12) if sec > 0 else None,
         "gemm_time_share": (gemm_ms / ms) if ms > 0 else None,

@@ -112,8 +112,8 @@ typedef struct {
                               stiffest-mode search, exact-kernel columns) take the three products
                               of the split; 1 = one 16-bit product (hi operands only, FP32
                               accumulation).  The kernel only preconditions the n dynamics and
-                              the forces do not contain it; the expansion and the chemical-
-                              potential chain always take three.  Ignored by FP64. */
+                              the forces do not contain it; the expansion always takes three,
+                              the chemical-potential chain follows mu_prec.  Ignored by FP64. */
   int graphs;              /* 1: split precisions with at most 2048 padded orbitals capture each
                               chemical-potential pass (per Newton-Schulz plan) and each probe's
                               response in CUDA graphs and replay them (the second run of a plan
@@ -122,6 +122,13 @@ typedef struct {
                               stream, which cannot be captured).  On many concurrent 32-512-atom
                               trajectories it measured slower than direct launches, so it is
                               off by default.  0: off. */
+  int mu_prec;             /* split precisions: 0 = the chemical-potential chain (dD/dmu) takes the
+                              three products of the split; 1 = one 16-bit product.  dD/dmu only
+                              sets the Newton step on mu and the first-order correction
+                              D(mu + dmu) = D(mu) + dmu dD/dmu, whose trace stays exact whatever
+                              its error; D's error from it is at most |dmu| times the error of
+                              dD/dmu, and the last Newton step has |dmu| < mu_tol / beta.
+                              Ignored by FP64. */
 } xlbomd_params;
 
 /* One trajectory.  R and V are natoms x 3 row-major (A, A/fs), Z natoms

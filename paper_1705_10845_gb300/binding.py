@@ -39,6 +39,7 @@ class Params(C.Structure):
         ("energy_every", C.c_int), ("scf_mode", C.c_int),
         ("kernel_auto", C.c_int), ("kernel_mode", C.c_int), ("kernel_every", C.c_int),
         ("rep_A", C.c_double), ("rep_rho", C.c_double), ("kernel_prec", C.c_int), ("graphs", C.c_int),
+        ("mu_prec", C.c_int),
     ]
 
 

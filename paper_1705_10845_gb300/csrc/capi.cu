@@ -784,6 +784,7 @@ void xlbomd_default_params(xlbomd_params* p) {
   p->rep_rho = 0.3;
   p->kernel_prec = 0;
   p->graphs = 0;
+  p->mu_prec = 0;
 }
 
 xlbomd_status xlbomd_table_i(xlbomd_params* p, int kmax) {
@@ -809,7 +810,7 @@ xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* syst
   if (p.n_sq < 1 || p.n_sq > 40 || p.kmax < 1 || p.kmax > 7 || p.rank_m < 0 || p.rank_m > kMaxRank ||
       p.kernel_c == 1.0 || !(p.Te > 0) || !(p.dt > 0) || p.mu_max_iter < 1 || p.scf_mode < 0 || p.scf_mode > 1 ||
       p.kernel_mode < 0 || p.kernel_mode > 2 || p.kernel_every < 0 || p.rep_A < 0.0 || !(p.rep_rho > 0.0) ||
-      p.kernel_prec < 0 || p.kernel_prec > 1 || p.graphs < 0 || p.graphs > 1)
+      p.kernel_prec < 0 || p.kernel_prec > 1 || p.graphs < 0 || p.graphs > 1 || p.mu_prec < 0 || p.mu_prec > 1)
     return XLBOMD_ERR_ARG;
   if (p.prec != XLBOMD_FP64 && p.prec != XLBOMD_FP16x3 && p.prec != XLBOMD_BF16x3) return XLBOMD_ERR_ARG;
   for (int i = 0; i < nsys; ++i) {
@@ -824,7 +825,7 @@ xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* syst
     delete ctx;
     return XLBOMD_ERR_UNSUPPORTED;
   }
-  ctx->eng->set_probe_segments(p.kernel_prec == 1 ? 1 : 3);
+  ctx->eng->set_chain_segments(p.kernel_prec == 1 ? 1 : 3, p.mu_prec == 1 ? 1 : 3);
   auto bail = [&](xlbomd_status st) {
     xlbomd_free(ctx);
     return st;

@@ -421,8 +421,8 @@ class EngineSplit : public Engine {
                     double* stats) override {
     const int np = m.np, n = m.n;
     const size_t cnt = (size_t)np * np;
-    // probe chains may run on the hi operands alone; the mu chain always takes all three products
-    const int nseg = full_last ? 3 : probe_nseg_;
+    // either chain may run on the hi operands alone (the mu chain is the one with a full last level)
+    const int nseg = full_last ? mu_nseg_ : probe_nseg_;
     SplitMat* T1 = &m.sT1a;
     SplitMat* T1n = &m.sT1b;
     for (int k = 0; k < n; ++k) {
@@ -478,7 +478,10 @@ class EngineSplit : public Engine {
   }
 
   const int* device_error() const override { return err_; }
-  void set_probe_segments(int nseg) override { probe_nseg_ = (nseg == 1) ? 1 : 3; }
+  void set_chain_segments(int probe_nseg, int mu_nseg) override {
+    probe_nseg_ = (probe_nseg == 1) ? 1 : 3;
+    mu_nseg_ = (mu_nseg == 1) ? 1 : 3;
+  }
 
   cudaError_t trace_tn(cudaStream_t s, MatSet& m, int N, double* out) override {
     diag_sum_d_kernel<<<1, 1024, 0, s>>>(N, m.np, m.sT[m.n].d, out);
@@ -522,6 +525,7 @@ class EngineSplit : public Engine {
  private:
   int bf16_;
   int probe_nseg_ = 3;
+  int mu_nseg_ = 3;
   std::unordered_map<int, std::pair<int*, std::pair<int, int>>> tiles_;
 };
 

@@ -122,8 +122,9 @@ class Engine {
   // Device flag that the tensor-core product sets when a bounded wait gives up or a
   // tile falls outside the matrix (null: this engine has none).
   virtual const int* device_error() const { return nullptr; }
-  // Split engines: tensor products per step of the probe chains (3, or 1 = hi operands only)
-  virtual void set_probe_segments(int) {}
+  // Split engines: tensor products per level of the probe chains and of the mu chain
+  // (3, or 1 = hi operands only)
+  virtual void set_chain_segments(int, int) {}
   virtual cudaError_t trace_tn(cudaStream_t s, MatSet& m, int N, double* out) = 0;
   // ddiag = 1 + diag(T_n) + dmu dmu_diag (= 2 D_aa);  D = (I + T_n)/2 + dmu Tmu / 2 (FP64)
   virtual cudaError_t density_out(cudaStream_t s, MatSet& m, int N, double dmu, const double* dmu_diag,

@@ -87,7 +87,7 @@ def make_context(X, job: Job, stream_ptr: int):
     n_sq = squarings_for(job.Te)
     p = X.default_params(Te=job.Te, n_sq=n_sq, rank_m=2, dt=0.25, mix_alpha=0.06, kernel_c=1 - 1 / 0.06,
                          prec=job.prec, scf_mode=1, kernel_auto=1, scf_tol=1e-5, scf_max_iter=400,
-                         mu_tol=1e-3, rep_A=40.0, rep_rho=0.3, kernel_prec=1)
+                         mu_tol=1e-3, rep_A=40.0, rep_rho=0.3, kernel_prec=1, mu_prec=1)
     ctx = X.Context(p, [dict(natoms=s.natoms, L=s.L, R=s.R, V=s.V, Z=s.Z, mass=s.mass)], stream=stream_ptr)
     ctx.scf(0)
     return ctx

@@ -308,3 +308,26 @@ def test_kernel_and_dissipation_variants_follow_oracle(X, variant):
             assert np.max(np.abs(ctx.get(0, X.Q) - ev.q)) < 1e-9, k
             assert np.max(np.abs(ctx.get(0, X.N) - st.nhist[0])) < 1e-9, k
             assert np.max(np.abs(ctx.get(0, X.KR) - ev.Kr)) < 1e-9, k
+
+
+def test_residual_and_energy_fluctuations_scale_as_dt_squared_on_gpu(X):
+    # Section VI.C, Figs. 9-10, through the C ABI: over the same 10 fs from the t0 ground state,
+    # halving dt divides the RMS residual |q[n] - n| and the total-energy fluctuation by about 4
+    s = synth.make_system(24, 1705, L=7.0)
+    res, fluct = [], []
+    for dt in (0.5, 0.25, 0.125):
+        p = model_params(X, dt=dt, rank_m=2)
+        with X.Context(p, [sysdict(s)]) as ctx:
+            ctx.scf(0)
+            r, E = [], []
+            for _ in range(int(round(10.0 / dt))):
+                ctx.step(1)
+                ctx.energy(0)
+                r.append(np.sqrt(np.mean(ctx.get(0, X.RES) ** 2)))
+                E.append(ctx.get(0, X.ENERGY)[5])
+        assert np.max(np.abs(np.asarray(E) - E[0])) < 1e-3, dt
+        res.append(np.mean(r))
+        fluct.append(np.std(E))
+    print("dt study: residual RMS", res, "energy std", fluct)
+    for a, b in ((res[0], res[1]), (res[1], res[2]), (fluct[0], fluct[1]), (fluct[1], fluct[2])):
+        assert 3.0 < a / b < 5.5, (res, fluct)

@@ -53,9 +53,13 @@ def test_pair_product_matches_fp64(X, n, prec, bound):
 
 @pytest.mark.parametrize("prec", ["fp16x3", "bf16x3"])
 @pytest.mark.parametrize("case", ["tiny24", "ragged37"])
-def test_split_density_against_oracle(X, prec, case):
+@pytest.mark.parametrize("mu_prec", [0, 1])
+def test_split_density_against_oracle(X, prec, case, mu_prec):
+    # mu_prec = 1: the chemical-potential chain at one 16-bit product (the mu start is 0.01 eV
+    # off, so the Newton steps and the first-order correction both use it)
     s = synth.make_system(24, 1705, L=7.0) if case == "tiny24" else synth.make_system(37, 11)
-    p = X.default_params(mix_alpha=ALPHA_MIX, kernel_c=1 - 1 / ALPHA_MIX, prec=prec, mu_tol=1e-3)
+    p = X.default_params(mix_alpha=ALPHA_MIX, kernel_c=1 - 1 / ALPHA_MIX, prec=prec, mu_tol=1e-3,
+                         mu_prec=mu_prec)
     m = O.Model(Te=p.Te, n_sq=p.n_sq)
     rng = np.random.default_rng(2)
     n = rng.normal(scale=0.02, size=s.natoms)
@@ -73,7 +77,7 @@ def test_split_density_against_oracle(X, prec, case):
         E = ctx.get(0, X.ENERGY)
     tol_q = 1e-5 if prec == "fp16x3" else 1e-4
     tol_f = 1e-4 if prec == "fp16x3" else 1e-3
-    print(prec, case, "dq", np.abs(q - ref.q).max(), "dF", np.abs(F - ref.F).max(), "dKr",
+    print(prec, case, "mu_prec", mu_prec, "dq", np.abs(q - ref.q).max(), "dF", np.abs(F - ref.F).max(), "dKr",
           np.abs(Kr - ref.Kr).max())
     assert np.max(np.abs(q - ref.q)) < tol_q
     assert np.max(np.abs(F - ref.F)) < tol_f
@@ -84,15 +88,17 @@ def test_split_density_against_oracle(X, prec, case):
     assert abs(E[0] - ref.Omega) < (2e-3 if prec == "fp16x3" else 2e-2)
 
 
-def test_full_size_charges_against_oracle(X):
+@pytest.mark.parametrize("mu_prec", [0, 1])
+def test_full_size_charges_against_oracle(X, mu_prec):
     # the bench workload: 1536 atoms (N = 6144), Te = 1500 K, 14 squarings,
     # FP16x3, at the t0 ground state that the MD starts from (kernel SCF with
     # the automatic J_0); the oracle diagonalises H on the host at the same
-    # (R, n) and the charges must agree to 1e-5 e
+    # (R, n) and the charges must agree to 1e-5 e, with the mu chain at three
+    # products or at one
     s = synth.make_system(1536, 1705)
     p = X.default_params(Te=1500.0, n_sq=14, rank_m=4, mix_alpha=ALPHA_MIX, kernel_c=1 - 1 / ALPHA_MIX,
                          prec="fp16x3", mu_tol=1e-3, scf_mode=1, kernel_auto=1, scf_tol=1e-5,
-                         scf_max_iter=200)
+                         scf_max_iter=200, mu_prec=mu_prec)
     with X.Context(p, [sysdict(s)]) as ctx:
         ctx.scf(0)
         n = ctx.get(0, X.N)
@@ -101,7 +107,7 @@ def test_full_size_charges_against_oracle(X):
         q = ctx.get(0, X.Q)
     q_ref = O.charges_at(s.R, s.L, s.Z, n, O.Model(Te=1500.0, n_sq=14))
     err = np.max(np.abs(q - q_ref))
-    print("full size fp16x3 |dq|", err)
+    print("full size fp16x3 mu_prec", mu_prec, "|dq|", err)
     assert err < 1e-5
 
 
