@@ -82,3 +82,38 @@ def test_table_i_rows_of_the_library_match_the_printed_table(golden):
         assert all(p.c[k] == 0.0 for k in range(kmax + 1, 8))
     with pytest.raises(X.XlbomdError):
         X.default_params(kmax=8)
+
+
+BAD_PARAMS = [dict(mu_prec=2), dict(kernel_prec=-1), dict(graphs=2), dict(rank_m=9), dict(n_sq=0),
+              dict(n_sq=41), dict(Te=0.0), dict(dt=0.0), dict(kernel_c=1.0), dict(mu_max_iter=0),
+              dict(scf_mode=2), dict(kernel_mode=3), dict(kernel_every=-1), dict(rep_A=-1.0),
+              dict(rep_rho=0.0), dict(prec=5)]
+
+
+@pytest.mark.parametrize("bad", BAD_PARAMS, ids=lambda d: "-".join(f"{k}={v}" for k, v in d.items()))
+def test_init_rejects_bad_params_before_any_device_call(bad):
+    # xlbomd_init validates every parameter on the host and returns ERR_ARG before it touches a
+    # device, so these run without a GPU
+    import numpy as np
+    import paper_1705_10845_gb300 as X
+    X.build.build()
+    p = X.default_params(**bad)
+    s = dict(natoms=2, L=12.0, R=np.array([[1.0, 1.0, 1.0], [2.4, 1.0, 1.0]]), V=np.zeros((2, 3)),
+             Z=np.full(2, 4.0), mass=12.0)
+    with pytest.raises(X.XlbomdError) as e:
+        X.Context(p, [s])
+    assert e.value.status == -1
+
+
+@pytest.mark.parametrize("change", [dict(natoms=0), dict(L=4.0), dict(mass=0.0)],
+                         ids=["natoms0", "box-inside-cutoff", "mass0"])
+def test_init_rejects_bad_systems_before_any_device_call(change):
+    import numpy as np
+    import paper_1705_10845_gb300 as X
+    X.build.build()
+    s = dict(natoms=2, L=12.0, R=np.array([[1.0, 1.0, 1.0], [2.4, 1.0, 1.0]]), V=np.zeros((2, 3)),
+             Z=np.full(2, 4.0), mass=12.0)
+    s.update(change)
+    with pytest.raises(X.XlbomdError) as e:
+        X.Context(X.default_params(), [s])
+    assert e.value.status == -1
