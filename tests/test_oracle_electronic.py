@@ -92,6 +92,25 @@ def test_entropy_stable_form_matches_direct_formula(tiny):
     assert np.allclose(O.entropy_terms(d)[ok], direct, atol=1e-12)
 
 
+@pytest.mark.parametrize("Te", [1000.0, 3000.0])
+def test_omega_temperature_derivative_is_minus_twice_kB_entropy(tiny, Te):
+    # At fixed n and R, Omega = 2 Tr[D H[n]] - 2 kB Te S + (terms without D), and the occupations
+    # minimise that electronic free energy at fixed electron count (Fermi-Dirac; 20 squarings
+    # make g_n equal to it within 1e-13).  By the envelope theorem dOmega/dTe = -2 kB S: a wrong
+    # factor or sign of the entropy term, or a wrong s(f), breaks it.
+    s, H0, gam, n = tiny
+
+    def ev(T):
+        return O.evaluate(s.R, s.L, s.Z, n, O.Model(Te=T, n_sq=20), None, with_kernel=False,
+                          with_forces=False)
+
+    h = 2.0
+    e0 = ev(Te)
+    fd = (ev(Te + h).Omega - ev(Te - h).Omega) / (2 * h)
+    assert e0.parts["S"] > 0.05
+    assert fd == pytest.approx(-2.0 * O.KB_EV * e0.parts["S"], rel=1e-5)
+
+
 def test_divided_differences_against_naive_and_degenerate_limit(tiny):
     s, H0, gam, n = tiny
     d = O.density(O.hamiltonian(H0, gam, n), M.beta, M.n_sq, 16)
