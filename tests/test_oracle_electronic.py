@@ -111,6 +111,28 @@ def test_omega_temperature_derivative_is_minus_twice_kB_entropy(tiny, Te):
     assert fd == pytest.approx(-2.0 * O.KB_EV * e0.parts["S"], rel=1e-5)
 
 
+def test_omega_gradient_in_n_is_gamma_times_residual(tiny):
+    # Omega[n] = 2 Tr[D H[n]] - 2 kB Te S - Z.gamma n - 1/2 n.gamma n with D[n] minimising the first
+    # two terms, and 2 Tr[D H[n]] depends on n through (q + Z).gamma n: so dOmega/dn = gamma (q[n] - n)
+    # exactly (Fermi-Dirac occupations, here 20 squarings), zero at the SCF ground state.  This fixes
+    # the Coulomb term's factor and the charge definition independently of the forces.
+    s, H0, gam, n = tiny
+    m = O.Model(n_sq=20)
+
+    def ev(nn):
+        return O.evaluate(s.R, s.L, s.Z, nn, m, None, with_kernel=False, with_forces=False)
+
+    e0 = ev(n)
+    g = O.build_gamma(s.R, s.L, m) @ (e0.q - n)
+    assert np.max(np.abs(g)) > 0.05
+    h = 2.5e-5                     # central-difference error ~3e-8 here, falling as h^2
+    for I in range(len(n)):
+        d = np.zeros_like(n)
+        d[I] = h
+        fd = (ev(n + d).Omega - ev(n - d).Omega) / (2 * h)
+        assert fd == pytest.approx(g[I], abs=1e-6), I
+
+
 def test_divided_differences_against_naive_and_degenerate_limit(tiny):
     s, H0, gam, n = tiny
     d = O.density(O.hamiltonian(H0, gam, n), M.beta, M.n_sq, 16)
