@@ -4,8 +4,10 @@ response, and the low-rank kernel.
 The references are independent of the oracle's formulas: the matrix recursion
 of the Fermi-operator expansion run by brute force, the Fermi-Dirac limit,
 commutation and trace invariants, finite differences of q[n], the explicit
-Sherman-Morrison sequence of Eq. K_up, and the inverse of a finite-difference
-Jacobian (the exact kernel, Eq. KK).
+Sherman-Morrison sequence of Eq. K_up, the inverse of a finite-difference
+Jacobian (the exact kernel, Eq. KK), and two consequences of the occupations
+minimising the electronic free energy: dOmega/dTe = -2 kB S and
+dOmega/dn = gamma (q[n] - n).
 """
 import math
 
