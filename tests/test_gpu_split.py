@@ -141,13 +141,14 @@ def test_one_cta_per_tile_variant_matches_fp64(X):
     import subprocess
     import sys
     code = ("import json, paper_1705_10845_gb300 as X; X.load(); "
-            "print(json.dumps([X.binding.selftest_gemm(n, p, s) for n in (256, 384) "
-            "for p in ('fp16x3', 'bf16x3') for s in (False, True)]))")
+            "print(json.dumps([[X.binding.selftest_gemm(n, p, s) for n in (256, 384) "
+            "for p in ('fp16x3', 'bf16x3') for s in (False, True)], "
+            "[X.binding.selftest_gemm(8192, 'fp16x3', s) for s in (False, True, 2)]]))")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     out = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True,
                          env=dict(os.environ, XLBOMD_GEMM="classic"), timeout=300)
     assert out.returncode == 0, out.stderr[-2000:]
-    res = json.loads(out.stdout.strip().splitlines()[-1])
+    res, large = json.loads(out.stdout.strip().splitlines()[-1])
     k = 0
     for n in (256, 384):
         for bound in (1e-6, 2e-5):
@@ -155,6 +156,11 @@ def test_one_cta_per_tile_variant_matches_fp64(X):
                 err, flag, ms = res[k]
                 k += 1
                 assert flag == 0 and err < bound * n, (n, err)
+    # n = 8192: the hi*hi sums split over both accumulators (dense, symmetric, pair), with the
+    # bounds of the persistent kernel's tests
+    for (err, flag, ms), bound in zip(large, (1e-6, 1e-6, 2e-6)):
+        print("classic fp16x3 8192", err, ms)
+        assert flag == 0 and err < bound * 8192, (err, ms)
 
 
 @pytest.mark.parametrize("prec", ["fp16x3", "bf16x3"])
