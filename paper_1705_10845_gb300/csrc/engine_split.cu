@@ -34,7 +34,7 @@ constexpr unsigned kEwBlocks = 152 * 16;
 inline unsigned ew_blocks(size_t count) { return (unsigned)std::min<size_t>(nblk(count), kEwBlocks); }
 
 // products of at least this size split their hi*hi sums over both accumulators
-constexpr int kSplitKMin = 8192;
+constexpr int kSplitAccMin = 8192;
 
 // Raise *amax to the block's max |v| with one atomic per block (all threads
 // of the block must call it).
@@ -350,7 +350,7 @@ class EngineSplit : public Engine {
     RET(prof_begin(s));
     // large products: split the hi*hi sums over both accumulators (the tensor core truncates as it
     // accumulates, so a K-long sum's error grows with K)
-    a.split_acc = (np >= kSplitKMin) ? 1 : 0;
+    a.split_acc = (np >= kSplitAccMin) ? 1 : 0;
     RET(gemm_tc(s, np, A.hi, A.lo, B.hi, B.lo, a, tl.first, tl.first + 2 * n128, n128, n256));
     // kind bits: 1 sym, 2 E, 4 E2, 8 E64, 16 E64 transposed, 32 FP64 output
     const int kind = (sym ? 1 : 0) | (e.E ? 2 : 0) | (e.E2 ? 4 : 0) | (e.E64 ? 8 : 0) | (e.e64_trans ? 16 : 0) |
