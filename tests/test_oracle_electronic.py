@@ -9,7 +9,6 @@ Jacobian (the exact kernel, Eq. KK), and two consequences of the occupations
 minimising the electronic free energy: dOmega/dTe = -2 kB S and
 dOmega/dn = gamma (q[n] - n).
 """
-import math
 
 import numpy as np
 import pytest
