@@ -117,3 +117,52 @@ def test_init_rejects_bad_systems_before_any_device_call(change):
     with pytest.raises(X.XlbomdError) as e:
         X.Context(X.default_params(), [s])
     assert e.value.status == -1
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include "xlbomd.h"
+
+int main(void) {
+  xlbomd_params p;
+  xlbomd_system s;
+  xlbomd_ctx* ctx = (xlbomd_ctx*)&p;   /* must be overwritten with NULL on failure */
+  const double R[6] = {1.0, 1.0, 1.0, 2.4, 1.0, 1.0}, V[6] = {0, 0, 0, 0, 0, 0}, Z[2] = {4.0, 4.0};
+  xlbomd_default_params(&p);
+  if (p.n_sq != 10 || p.kmax != 5 || p.rank_m != 2) return 1;
+  if (xlbomd_table_i(&p, 6) != XLBOMD_OK || p.kmax != 6 || p.c[6] != 1.0 || p.kappa != 1.84) return 2;
+  if (xlbomd_table_i(&p, 8) != XLBOMD_ERR_ARG) return 3;
+  s.natoms = 2;
+  s.box_L = 12.0;
+  s.R = R;
+  s.V = V;
+  s.Z = Z;
+  s.mass = 12.0;
+  p.mu_prec = 2;                          /* out of range: refused on the host */
+  if (xlbomd_init(&p, &s, 1, NULL, &ctx) != XLBOMD_ERR_ARG || ctx != NULL) return 4;
+  if (xlbomd_init(NULL, &s, 1, NULL, &ctx) != XLBOMD_ERR_ARG) return 5;
+  if (xlbomd_free(NULL) != XLBOMD_ERR_ARG) return 6;
+  printf("ok %s\n", xlbomd_last_error(NULL));
+  return 0;
+}
+"""
+
+
+def test_c_client_links_and_calls_the_host_side_entry_points(tmp_path):
+    # the boundary as a C user meets it: the header compiles as strict C99, the program links
+    # against libxlbomd.so, and the calls that need no device behave as the header states
+    import shutil
+    import subprocess
+    from paper_1705_10845_gb300 import build
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    libdir = os.path.dirname(build.build())
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe), "-L", libdir, "-lxlbomd", f"-Wl,-rpath,{libdir}"], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, (out.returncode, out.stderr[-2000:])
+    assert out.stdout.startswith("ok null context")
