@@ -5,20 +5,28 @@
 // A_hi B_hi + A_hi B_lo + A_lo B_hi, accumulated into one TMEM tile; the
 // operands carry power-of-two scales that the epilogue removes.
 //
-// Per CTA: one 128 x BN output tile.  Warp 0 issues TMA loads (128-byte
-// swizzle, K-major) into a STAGES-deep ring guarded by mbarriers; warp 1
-// allocates TMEM and one elected thread issues tcgen05.mma (M = 128,
-// N = BN, K = 16) per 32-byte K step; warps 2-5 wait for the accumulators,
-// read them with tcgen05.ld (32 lanes x 32 columns per load), apply the
-// epilogue and store FP32 rows (and the mirrored columns of a symmetric
-// product).
+// Two kernels share the pipeline.  The default is persistent: one CTA per SM
+// walks the 128 x BN output tiles.  The other (XLBOMD_GEMM=classic) gives
+// each CTA one tile.  Warp 0 issues TMA loads (128-byte swizzle, K-major) into
+// a STAGES-deep ring guarded by mbarriers; warp 1 allocates TMEM and one
+// elected thread issues tcgen05.mma (M = 128, N = BN, K = 16) per 32-byte K
+// step; warps 2-5 wait for the accumulators, read them with tcgen05.ld (32
+// lanes x 32 columns per load), apply the epilogue and store FP32 or
+// double-float rows (and the mirrored columns of a symmetric product).  In the
+// persistent kernel the epilogue folds accumulator 0 into accumulator 1 and
+// releases it at once, so the next tile's first K blocks overlap the rest of
+// the epilogue.
 //
 // The tensor core adds each K = 16 step into its FP32 accumulator with
 // truncation, so a small term added to a large accumulator loses bits.  The
 // hi*hi segment and the two correction segments (hi*lo, lo*hi, about 2^-11
 // smaller) therefore go to two separate TMEM accumulators (2 x BN columns)
-// that the epilogue adds in FP32.  Every mbarrier wait is bounded: on timeout the kernel records an
-// error code and leaves its loops, and TMEM is always released.
+// that the epilogue adds in FP32.  Products of large n also split the hi*hi
+// sum over the two accumulators (split_acc), since the truncation error of a
+// sum grows with its length.  A pair product (pairs = 2) adds the swapped
+// operands as a second K range, C = A B^T + B A^T.  Every mbarrier wait is
+// bounded: on timeout the kernel records an error code and leaves its loops,
+// and TMEM is always released.
 #include <cuda.h>
 
 #include <algorithm>
