@@ -1,12 +1,15 @@
 // Split-precision engine: the expansion and response chains with tensor-core
-// products on hi/lo 16-bit operands (FP16x3 or BF16x3) and FP32 values.
+// products on hi/lo 16-bit operands (FP16x3 or BF16x3).
 //
-// Every matrix keeps an FP32 value array and a split operand pair
-// hi = rn16(x s), lo = rn16(x s - hi) with a power-of-two scale s chosen from
-// max |x| so that max |x s| lies in [2^10, 2^11) (FP16 keeps full precision
-// in both parts); producers raise max |x| atomically and a conversion pass
-// writes hi/lo.  Traces, charges and the density matrix handed to the forces
-// are accumulated in FP64.
+// Every matrix keeps a value array -- FP32, or double-float (an FP32 hi + lo
+// pair) for T_k, M and T1, whose leading terms the correction form keeps out of
+// the products -- and a split operand pair hi = rn16(x s), lo = rn16(x s - hi)
+// with a power-of-two scale s chosen from max |x| so that max |x s| lies in
+// [2^10, 2^11) (FP16 keeps full precision in both parts); producers raise
+// max |x| atomically and a conversion pass writes hi/lo.  A product takes three
+// 16-bit products (hi*hi, hi*lo, lo*hi), or one (hi*hi) in the probe chains
+// and the mu chain when the context asks for it.  Traces, charges and the
+// density matrix handed to the forces are accumulated in FP64.
 #include <cuda_bf16.h>
 
 #include <algorithm>
