@@ -1,9 +1,9 @@
 // Split-precision tensor-core products for sm_103a (tcgen05 + TMEM + TMA).
 //
 // C = epi( sum_seg A_seg B_seg^T ) with 16-bit operands (FP16 or BF16) and an
-// FP32 accumulator in tensor memory.  A split product uses three K segments,
-// A_hi B_hi + A_hi B_lo + A_lo B_hi, accumulated into one TMEM tile; the
-// operands carry power-of-two scales that the epilogue removes.
+// FP32 accumulation in tensor memory.  A split product uses three K segments,
+// A_hi B_hi + A_hi B_lo + A_lo B_hi (one, A_hi B_hi, for single-product
+// chains); the operands carry power-of-two scales that the epilogue removes.
 //
 // Two kernels share the pipeline.  The default is persistent: one CTA per SM
 // walks the 128 x BN output tiles.  The other (XLBOMD_GEMM=classic) gives
