@@ -1,17 +1,25 @@
 #!/usr/bin/env python
 """Benchmark of the XL-BOMD hot path on GB300.
 
-Workload (default): one trajectory of 1536 carbon-like atoms (N = 6144
-orbitals) in a 28 A periodic cube, Te = 1500 K, 14 squarings of the recursive
-Fermi-operator expansion, rank-4 kernel, dt = 0.25 fs; split FP16x3
-tensor-core products with FP64 traces, charges, forces and integration.
-A step is one full XL-BOMD step (H build, expansion with the
-chemical-potential loop, charges, forces, four response chains, kernel
-update, Verlet).  With --gpus N each rank runs its own replica trajectory
-(seed 1705 + rank): weak scaling, no collective on the data path.
+Workload (default): the precision workload -- one trajectory of 4096
+carbon-like atoms (N = 16384 orbitals) in a 38.8 A periodic cube, Te = 1000 K,
+10 squarings of the recursive Fermi-operator expansion, rank-4 kernel,
+dt = 0.25 fs; split FP16x3 tensor-core products in the expansion (one 16-bit
+product in the probe and chemical-potential chains) with FP32 accumulation and
+FP64 traces, charges, forces and integration.  A step is one full XL-BOMD step
+(H build, expansion with the chemical-potential loop, charges, forces, four
+response chains, kernel update, Verlet).  With --gpus N each rank runs its own
+replica trajectory (seed 1705 + rank): weak scaling, no collective on the data
+path.
+
+Beside the timed steps the line carries: the plain-FP64 GPU path's step rate
+(bounded from above by one timed FP64 product of the same size times the
+step's product count), charge, force and energy parity against one FP64 oracle
+step at the final state, and that oracle step's time on the host cores (the
+CPU baseline).
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
-on the host cores instead (bounded sample per step).
+on the host cores instead (one full oracle step).
 """
 from __future__ import annotations
 
@@ -29,11 +37,10 @@ if ROOT not in sys.path:
 
 METRIC = "XL-BOMD steps/s and FOE TFLOP/s vs peak, mixed vs FP64 GPU at |dq|<=1e-5 e"
 ALPHA_MIX = 0.06
-# DRAM bytes (read + write) of one dense n = 6144 launch of each product-kernel variant, from
-# the ncu captures summarised in profiles/ (None: not captured since the kernel last changed)
-# DRAM bytes per dense n = 6144 launch of the current kernels (ncu dram__bytes_read + _write);
-# None where the kernel changed after its counters were taken
-GEMM_TRAFFIC_N6144 = {"classic": None, "persistent": 1.217e9 + 0.142e9}
+# DRAM bytes (read + write) per launch of the product kernel, averaged over the launches of one
+# MD step, keyed by (variant, padded orbital count), from the ncu captures summarised in profiles/;
+# a workload or kernel without a capture since the kernel last changed reports null
+GEMM_TRAFFIC = {}
 
 
 def gemm_variant():
@@ -47,9 +54,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp16x3", choices=["fp16x3", "bf16x3", "fp64"])
-    ap.add_argument("--natoms", type=int, default=1536)
-    ap.add_argument("--Te", type=float, default=1500.0)
-    ap.add_argument("--nsq", type=int, default=14)
+    ap.add_argument("--natoms", type=int, default=4096)
+    ap.add_argument("--Te", type=float, default=1000.0)
+    ap.add_argument("--nsq", type=int, default=10)
     ap.add_argument("--rank", type=int, default=4)
     ap.add_argument("--kernel-prec", type=int, default=1, choices=[0, 1],
                     help="1 (default): the kernel's probe chains take one 16-bit product instead of three; "
@@ -62,7 +69,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=0,
-                    help="also time this many plain-FP64 GPU steps of the same workload")
+                    help="also time this many plain-FP64 GPU steps of the same workload (minutes per step at "
+                         "the default size)")
+    ap.add_argument("--no-fp64-product", action="store_true",
+                    help="skip the timed FP64 product that bounds the plain-FP64 GPU step rate")
     ap.add_argument("--trajectory-check", type=int, default=0, metavar="K",
                     help="study run instead of the timing: --steps MD steps after the t0 SCF, the energy "
                          "monitor every --energy-every steps, and every K steps the oracle re-evaluates q, "
@@ -87,8 +97,16 @@ def workload_config(a, parallel):
         "kernel_probe_products": "one 16-bit product" if a.kernel_prec else "three (full split)",
         "mu_chain_products": "one 16-bit product" if a.mu_prec else "three (full split)",
         "prec": a.prec, "parallelism": parallel,
-        "l2": "inputs larger than L2: about 11 GB of expansion matrices are rewritten every step",
+        "l2": f"inputs larger than L2: about {expansion_bytes(a) / 1e9:.0f} GB of expansion matrices are "
+              f"rewritten every step",
     }
+
+
+def expansion_bytes(a) -> float:
+    """Device bytes of the split engine's matrices for this workload (the per-context estimate the
+    serving loop admits by)."""
+    from paper_1705_10845_gb300.serve import bytes_estimate
+    return float(bytes_estimate(a.natoms, a.nsq, a.prec))
 
 
 def replica_seed(rank: int) -> int:
@@ -179,6 +197,17 @@ def single_product_chains(a):
     return f"1 in the {' and '.join(chains)} chains" if chains else "3 in every chain"
 
 
+def dtype_label(a):
+    """The products' arithmetic: FP64, or the 16-bit split (three products per split product) with
+    the chains that take one 16-bit product named."""
+    if a.prec == "fp64":
+        return "f64"
+    base = a.prec[:4]
+    single = [c for c, on in (("probe", a.kernel_prec), ("mu", a.mu_prec)) if on]
+    chains = f", {base} x1 in the {' and '.join(single)} chains" if single else ""
+    return f"{a.prec} expansion{chains}; fp32 accumulate; f64 traces, charges, forces, integration"
+
+
 def make_params(X, a, prec):
     return X.default_params(Te=a.Te, n_sq=a.nsq, rank_m=a.rank, dt=0.25, mix_alpha=ALPHA_MIX,
                             rep_A=a.rep_A, rep_rho=0.3, kernel_prec=a.kernel_prec, mu_prec=a.mu_prec,
@@ -187,46 +216,69 @@ def make_params(X, a, prec):
                             mu_tol=1e-9 if prec == "fp64" else 1e-3, scf_max_iter=200)
 
 
-def oracle_sample(R, L, Z, n, a):
-    """One oracle density evaluation (H0, gamma, eigendecomposition, mu,
-    Mulliken charges) at the given state; returns (seconds, q)."""
+def oracle_model(a):
     import oracle as O
-    m = O.Model(Te=a.Te, n_sq=a.nsq)
+    return O.Model(Te=a.Te, n_sq=a.nsq, rep_A=a.rep_A, rep_rho=0.3)
+
+
+ORACLE_STEP = ("one full XL-BOMD step of the FP64 oracle (oracle.md_step) on the whole system: half kick, "
+               "drift, n update, then at the new state H0, Ewald gamma, full eigendecomposition, chemical "
+               "potential, Mulliken charges, Hellmann-Feynman forces, the free energy and the rank-{m} kernel's "
+               "{m} probe responses (eigenbasis divided differences), and the second half kick")
+
+
+def oracle_step(st, L, Z, mass, a, kernel_c):
+    """One XL-BOMD step of the FP64 oracle from the MD state st (R, V, n history, F and K r at t;
+    Eqs. Integration, VRL_Damp).  Returns (seconds, new state, evaluation at the new state)."""
+    import oracle as O
+    xl = O.XLParams(rank_m=a.rank, kernel_c=kernel_c, dt=0.25)
     t = time.perf_counter()
-    q = O.charges_at(R, L, Z, n, m)
-    return time.perf_counter() - t, q
+    st1, ev = O.md_step(st, L, Z, mass, oracle_model(a), xl)
+    return time.perf_counter() - t, st1, ev
 
 
 def run_reference(a, ws, rank):
-    """The oracle as it stands on the host cores (FP64 CPU), same workload."""
+    """The oracle as it stands on the host cores (FP64 CPU), same workload: full oracle MD steps
+    from the seeded initial positions and velocities."""
     import numpy as np
 
+    import oracle as O
     import synth
     if ws > 1 and rank != 0:
         return 0
     cores = len(os.sched_getaffinity(0))
     s = synth.make_system(a.natoms, 1705)
-    rng = np.random.default_rng(0)
-    n = rng.normal(scale=0.01, size=a.natoms)
-    n -= n.mean()
-    # each step: one oracle density evaluation of the whole system; the
-    # number of timed steps is capped so the run ends within a few minutes
-    t_first, _ = oracle_sample(s.R, s.L, s.Z, n, a)          # warm-up
-    k = max(1, min(a.steps, int(150.0 / max(t_first, 1e-3))))
-    t0 = time.perf_counter()
-    for _ in range(k):
-        oracle_sample(s.R, s.L, s.Z, n, a)
-    dt = time.perf_counter() - t0
-    v = k / dt
+    nat = s.natoms
+    # MD state at t: the seeded R, V; n history at zero charges with F = 0, K r = 0 at t (the
+    # cost of a step does not depend on these values)
+    st = O.MDState(R=np.array(s.R), V=np.array(s.V), nhist=np.zeros((6, nat)), F=np.zeros((nat, 3)),
+                   Kr=np.zeros(nat))
+    # the first step doubles as the warm-up; a step of more than 30 s is itself the timed sample
+    # so that the run ends within minutes (one step at 4096 atoms takes minutes on 16 cores)
+    t_first, st, _ = oracle_step(st, s.L, s.Z, s.mass, a, 1.0 - 1.0 / ALPHA_MIX)
+    times = [t_first]
+    warm = 1
+    if t_first < 30.0:
+        times = []
+        budget = 150.0
+        k = max(1, min(a.steps, int(budget / max(t_first, 1e-3))))
+        for _ in range(k):
+            dt, st, _ = oracle_step(st, s.L, s.Z, s.mass, a, 1.0 - 1.0 / ALPHA_MIX)
+            times.append(dt)
+    else:
+        warm = 0
+    sec = sum(times)
+    v = len(times) / sec
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": a.gpus,
-            "steps": k, "warmup": 1, "ms_per_step": 1000.0 * dt / k, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(a, "oracle on host cores"),
+            "steps": len(times), "warmup": warm, "ms_per_step": 1000.0 * sec / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(a, "oracle on host cores"),
             "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
-                             "sample": "one oracle density evaluation (H0, Ewald gamma, full eigendecomposition, "
-                                       "chemical potential, Mulliken charges) of the whole system per step; "
-                                       "the response chains, forces and integration of a full step are not "
-                                       "included, so this overstates the CPU step rate"},
+                             "sample": ORACLE_STEP.format(m=a.rank) + "; from the seeded initial positions "
+                                       "and velocities at zero charges (the GPU arm steps from its t0 ground "
+                                       "state; the work per step is the same)" +
+                                       ("" if warm else "; one step of several minutes is the whole timed "
+                                        "sample, without a separate warm-up step")},
             "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -437,8 +489,15 @@ def main():
     h2d = 8 * (3 * nat + 3 * nat + k1 * nat)
     d2h = 8 * (3 * nat + 3 * nat + k1 * nat + nat + 3 * nat)
 
-    # ---- optional plain-FP64 GPU steps of the same workload from this state ----
+    # ---- plain-FP64 GPU path of the same workload ----
+    # One FP64 step at this size takes tens of minutes, so by default one timed FP64 product of the
+    # same size bounds it: the FP64 path runs at least the mixed step's dense-equivalent product
+    # count (its Newton-Schulz inverses take as many or more iterations, and its A1 takes the same
+    # work), so products x product time is a lower bound on its step time and the rate below an
+    # upper bound on its step rate.  --fp64-steps K times K real FP64 steps instead.
     fp64 = None
+    per_step_products = (st1[3] - st0[3]) / a.steps
+    np_pad = (4 * a.natoms + 127) // 128 * 128
     if a.fp64_steps > 0:
         p64 = make_params(X, a, "fp64")
         sysd64 = dict(sysd)
@@ -455,24 +514,43 @@ def main():
         ctx64.step(a.fp64_steps)
         torch.cuda.synchronize()
         f64s = time.perf_counter() - f0
-        fp64 = {"steps": a.fp64_steps, "steps_per_s": a.fp64_steps / f64s, "s_per_step": f64s / a.fp64_steps}
+        fp64 = {"kind": "measured FP64 GPU steps", "steps": a.fp64_steps, "steps_per_s": a.fp64_steps / f64s,
+                "s_per_step": f64s / a.fp64_steps}
         ctx64.close()
+    elif not a.no_fp64_product:
+        _, _, ms64 = X.binding.selftest_gemm(np_pad, "fp64", False)
+        s64 = per_step_products * ms64 / 1000.0
+        fp64 = {"kind": "bound: one timed FP64 product (n = %d, plain-FP64 path kernel) x the mixed step's "
+                        "dense-equivalent product count; the FP64 path runs at least as many, so this is an "
+                        "upper bound on its step rate" % np_pad,
+                "product_ms": ms64, "product_tflops": 2.0 * np_pad ** 3 / (ms64 / 1000.0) / 1e12,
+                "products_per_step": per_step_products, "s_per_step": s64, "steps_per_s": 1.0 / s64,
+                "mixed_over_fp64": value / (1.0 / s64)}
 
-    # ---- parity at the final state and the CPU baseline (rank 0) ----
+    # ---- parity and the CPU baseline (rank 0): one more step on both sides from the same state ----
+    # The GPU's state at t (R, V, n history, F, K r) goes to the FP64 oracle, which takes one full
+    # step from it (oracle.md_step); the GPU takes the same step.  The Verlet updates are FP64 on
+    # both sides, so R and n at t + dt agree to rounding and the oracle's q, F and Omega there are
+    # the reference for the GPU's (the trajectory itself is chaotic, so parity is state-wise).
     cpu = None
     parity = None
     if rank == 0 and not a.no_cpu_baseline:
-        R = ctx.get(0, X.R)
-        nn = ctx.get(0, X.N)
-        ctx.build_H(0)
-        ctx.density(0)
-        qg = ctx.get(0, X.Q)
-        tcpu, qo = oracle_sample(R, s.L, s.Z, nn, a)
+        import oracle as O
+        st_t = O.MDState(R=ctx.get(0, X.R), V=ctx.get(0, X.V), nhist=ctx.get(0, X.NHIST), F=ctx.get(0, X.F),
+                         Kr=ctx.get(0, X.KR))
+        ctx.step(1)
+        ctx.energy(0)
+        qg, Fg, Rg, ng = ctx.get(0, X.Q), ctx.get(0, X.F), ctx.get(0, X.R), ctx.get(0, X.N)
+        Eg = ctx.get(0, X.ENERGY)
+        tcpu, st_o, ev = oracle_step(st_t, s.L, s.Z, s.mass, a, 1.0 - 1.0 / ALPHA_MIX)
         cpu = {"value": 1.0 / tcpu, "unit": "steps/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-               "sample": "one oracle density evaluation (H0, Ewald gamma, full eigendecomposition, chemical "
-                         "potential, Mulliken charges) at the final GPU state; response chains, forces and "
-                         "integration are not included, so this overstates the CPU step rate"}
-        parity = {"max_abs_dq_vs_fp64_oracle": float(np.max(np.abs(qg - qo))), "tolerance": 1e-5}
+               "sample": ORACLE_STEP.format(m=a.rank) + ", from the GPU's state after the timed steps"}
+        parity = {"max_abs_dq": float(np.max(np.abs(qg - ev.q))), "tol_q": 1e-5,
+                  "max_abs_dF": float(np.max(np.abs(Fg - ev.F))), "tol_F": 1e-4,
+                  "dOmega_eV": float(Eg[0] - ev.Omega), "Omega_eV": float(ev.Omega),
+                  "max_abs_dR": float(np.max(np.abs(O.min_image(Rg - st_o.R, s.L)))),
+                  "max_abs_dn": float(np.max(np.abs(ng - st_o.nhist[0]))),
+                  "against": "FP64 oracle step from the GPU's state (q, F, Omega at t + dt)"}
 
     bf, bf_sus, hbm, src = peaks()
     gemm_launches, gemm_ms, gemm_flops = prof
@@ -482,12 +560,13 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": a.prec, "data": "synthetic", "config": workload_config(a, f"replicas x{ws}"),
+        "dtype": dtype_label(a), "data": "synthetic", "config": workload_config(a, f"replicas x{ws}"),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None,
-                     "traffic": GEMM_TRAFFIC_N6144[gemm_variant()] if (a.natoms == 1536 and a.prec == "fp16x3")
-                     else None,
-                     "traffic_note": "bytes per dense n = 6144 launch (ncu); algorithmic 0.453 GB",
+                     "traffic": GEMM_TRAFFIC.get((gemm_variant(), np_pad)) if a.prec == "fp16x3" else None,
+                     "traffic_note": "DRAM bytes per product launch (ncu dram__bytes_read + write), averaged "
+                                     "over one step's launches; null where no capture of the current kernel "
+                                     "at this size exists",
                      "kernel": f"gemm_tc {gemm_variant()} kernel (split-precision tcgen05 product)",
                      "note": f"algorithmic 2n^3 per product (n^3 when symmetric-output) over CUDA-event time of "
                              f"{int(gemm_launches)} launches; each split product runs 3 half-precision "

@@ -189,7 +189,14 @@ xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* syst
  * max|q - n| > 1e3), and those of xlbomd_density. */
 xlbomd_status xlbomd_scf(xlbomd_ctx* ctx, int sys);
 
-/* a1-a2: H0 and gamma at the current R, H[n] = H0 + diag(gamma n). */
+/* H0, gamma and H[n] at the current R (rows a1-a2 of the path).  H[n] is the
+ * Hamiltonian of the linearised functional at the dynamical charges n
+ * (Section IV.A, the Kohn-Sham shadow potential: H_KS[n] with the Hartree
+ * term evaluated at n): in the SCC-TB model H[n] = H0 + diag(gamma n) per
+ * orbital, gamma the Coulomb matrix (Hubbard U on the diagonal).  Enqueued
+ * asynchronously; clears the context's density (a later xlbomd_density must
+ * run before xlbomd_response / xlbomd_kernel_update).  Errors: ERR_ARG (bad
+ * sys), ERR_CUDA. */
 xlbomd_status xlbomd_build_H(xlbomd_ctx* ctx, int sys);
 
 /* a3-a6: recursive expansion D = f(H[n]) with mu from Tr D = N_occ
@@ -216,8 +223,11 @@ xlbomd_status xlbomd_response(xlbomd_ctx* ctx, int sys, const double* v_dev, dou
  * device address (cudaGetSymbolAddress), so make that first call before any
  * stream capture.  All calls share the one array and it keeps the last call's
  * contents: calls that overlap on the GPU (other streams, other contexts,
- * other host threads) race on it.  The paper has no counterpart to this entry
- * point; it exists for callers that cannot allocate. */
+ * other host threads) race on it.  Every argument check (including the
+ * reciprocal-vector count of the Coulomb sum) comes before the first
+ * operation on the shared array, and its products are counted in
+ * XLBOMD_STATS like those of xlbomd_response.  The paper has no counterpart to
+ * this entry point; it exists for callers that cannot allocate. */
 xlbomd_status xlbomd_response_noalloc(xlbomd_ctx* ctx, int sys, const double* v_dev, double* w_dev);
 
 /* a7-a8: K r into KR.  kernel_mode 0: rank-m kernel on r (Eqs. K_up, v_1;
@@ -237,7 +247,13 @@ xlbomd_status xlbomd_kernel_update(xlbomd_ctx* ctx, int sys);
  * ERR_NOT_CONVERGED (J - I numerically singular), ERR_OOM. */
 xlbomd_status xlbomd_kernel_exact(xlbomd_ctx* ctx, int sys);
 
-/* a10: energy monitor (shadow free energy Omega and kinetic energy). */
+/* Energy monitor (row a10): the free-energy shadow potential
+ * Omega[n](R) = U[n](R) - Te S[f] of Section IV.B (Eq. S_entropy for S, with
+ * the occupations of the expansion) and the constant of motion of Section IV.C
+ * (Eq. ShadowH1: kinetic energy + Omega), written to XLBOMD_ENERGY as
+ * [Omega, 2 Tr[D H0], 1/2 sum (2q - n) gamma n, -2 kB Te S, kinetic, total,
+ * repulsion].  Requires xlbomd_density on the same state; synchronises the
+ * stream.  Errors: ERR_ARG (no density), ERR_CUDA. */
 xlbomd_status xlbomd_energy(xlbomd_ctx* ctx, int sys);
 
 /* a1-a10 for every system, nsteps times (Eqs. Integration, VRL_Damp). */
@@ -254,11 +270,16 @@ xlbomd_status xlbomd_sizes(xlbomd_ctx* ctx, int sys, int* natoms, int* n_orb, in
 
 /* Diagnostics: one split-precision tensor-core product C = A B^T (n x n, n a
  * multiple of 128, prec FP16x3 or BF16x3; sym = 1: symmetric-output mode with
- * a symmetric B; sym = 2: the symmetric-output pair product A B^T + B A^T) of
- * seeded uniform [-1, 1) matrices, compared on the device with the FP64
- * product of the same FP64 inputs.  result[0] = max |C_tc - C_fp64|,
+ * a symmetric B; sym = 2: the symmetric-output pair product A B^T + B A^T;
+ * sym + 4: the same with one 16-bit product, hi operands only, as in the
+ * single-product chains) of seeded uniform [-1, 1) matrices, compared on the
+ * device with the FP64 product of the same FP64 inputs.  Other sym values:
+ * ERR_ARG.  result[0] = max |C_tc - C_fp64|,
  * result[2] = device wait-timeout flag, result[3] = ms per product.
- * This is a check of the matrix-product engine; the paper has no counterpart. */
+ * prec = XLBOMD_FP64 (sym 0 or 1) times one product of the plain-FP64 path
+ * instead (result[3]; no comparison, result[0..2] = 0), synchronising the
+ * device.  This is a check of the matrix-product engine; the paper has no
+ * counterpart. */
 xlbomd_status xlbomd_selftest_gemm(int n, int prec, int sym, double* result);
 
 /* Diagnostics: number of CUDA kernels the library has launched since it was

@@ -129,12 +129,16 @@ def launch_count() -> int:
     return int(load().xlbomd_launch_count())
 
 
-def selftest_gemm(n: int, prec: str = "fp16x3", sym=False):
+def selftest_gemm(n: int, prec: str = "fp16x3", sym=False, single: bool = False):
     """One tensor-core split product of seeded matrices checked on the device
     against the FP64 product: returns (max abs error, timeout flag, ms).
-    sym: False (A B^T), True (symmetric output), or 2 (A B^T + B A^T)."""
+    sym: False (A B^T), True (symmetric output), or 2 (A B^T + B A^T);
+    single: one 16-bit product (hi operands only) instead of three.
+    prec "fp64" times one plain-FP64 product instead (error 0)."""
     out = np.zeros(4)
     mode = 2 if (not isinstance(sym, bool) and sym == 2) else int(bool(sym))
+    if single:
+        mode += 4
     st = load().xlbomd_selftest_gemm(int(n), PREC[prec], mode, _dptr(out))
     if st != XLBOMD_OK:
         raise XlbomdError(st, "xlbomd_selftest_gemm")

@@ -714,6 +714,8 @@ xlbomd_status xlbomd_response_noalloc(xlbomd_ctx* ctx, int sys, const double* v_
                     " exceeds the static work-array limit of " + std::to_string(kStaticMaxNp) +
                     " (64 atoms); use xlbomd_response");
   if (!S.have_density) return fail(ctx, XLBOMD_ERR_ARG, "xlbomd_density must run first");
+  if (S.kp > kStaticSf) return fail(ctx, XLBOMD_ERR_ARG, "xlbomd_response_noalloc: too many reciprocal vectors");
+  // every argument check is above: nothing is enqueued on the shared array before the call is accepted
   double* base = nullptr;
   CKS(static_scratch(ctx, &base));
   cudaStream_t st = ctx->stream;
@@ -732,12 +734,11 @@ xlbomd_status xlbomd_response_noalloc(xlbomd_ctx* ctx, int sys, const double* v_
   double* scal = d1 + kStaticMaxNp;
   // the array keeps the previous call's contents: the diagonal accumulator starts at zero
   CK(cudaMemsetAsync(d1, 0, sizeof(double) * kStaticMaxNp, st));
-  if (S.kp > kStaticSf) return fail(ctx, XLBOMD_ERR_ARG, "xlbomd_response_noalloc: too many reciprocal vectors");
   CK(gamma_apply(ctx, S, v_dev, potv, scal + 64));
   CK(launch_expand_potential(st, S.nat, S.np, -sc, potv, dvec));
   const bool prof = ctx->eng->prof;
   ctx->eng->prof = false;   // event timing would create CUDA events
-  const cudaError_t ce = ctx->eng->chain(st, m, dvec, S.N, false, d1, nullptr);
+  const cudaError_t ce = ctx->eng->chain(st, m, dvec, S.N, false, d1, S.stats);   // counted in XLBOMD_STATS
   ctx->eng->prof = prof;
   CK(ce);
   CK(launch_response_finish(st, S.nat, S.N, d1, S.dmu_diag, scal, w_dev));
@@ -1106,7 +1107,7 @@ xlbomd_status xlbomd_gemm_profile(xlbomd_ctx* ctx, int mode, double* out) {
 }
 
 xlbomd_status xlbomd_selftest_gemm(int n, int prec, int sym, double* result) {
-  if (!result || n <= 0 || n % 128) return XLBOMD_ERR_ARG;
+  if (!result || n <= 0 || n % 128 || sym < 0 || sym > 6 || sym == 3) return XLBOMD_ERR_ARG;
   const int rc = selftest_gemm(n, prec, sym, result);
   if (rc == -1) return XLBOMD_ERR_ARG;
   return rc == 0 ? XLBOMD_OK : XLBOMD_ERR_CUDA;

@@ -674,9 +674,48 @@ __global__ void max_abs_diff_kernel(size_t count, const float* __restrict__ a, c
 
 }  // namespace
 
+// Timing of the plain-FP64 product (the product of the FP64 path) at size n: one warm-up
+// product at 128, then one timed product at n (sym: symmetric-output mode, half the tiles).
+// Writes [0, 0, 0, ms per product].
+int selftest_gemm_f64(int n, int sym, double* result) {
+  const size_t cnt = (size_t)n * n;
+  double *A = nullptr, *B = nullptr, *C = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = 0.f;
+  int rc = -2;
+  EpiF64 e;
+  if (cudaMalloc((void**)&A, cnt * 8) || cudaMalloc((void**)&B, cnt * 8) || cudaMalloc((void**)&C, cnt * 8))
+    goto done;
+  fill_random_kernel<<<nblk(cnt), 256>>>(cnt, n, 11, 0, A);
+  note_launch();
+  fill_random_kernel<<<nblk(cnt), 256>>>(cnt, n, 23, sym, B);
+  note_launch();
+  if (gemm_f64_nt(nullptr, 128, 128, 128, A, n, B, n, C, n, e, sym != 0)) goto done;
+  if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) goto done;
+  cudaEventRecord(e0, nullptr);
+  if (gemm_f64_nt(nullptr, n, n, n, A, n, B, n, C, n, e, sym != 0)) goto done;
+  cudaEventRecord(e1, nullptr);
+  if (cudaDeviceSynchronize() != cudaSuccess) goto done;
+  cudaEventElapsedTime(&ms, e0, e1);
+  result[0] = result[1] = result[2] = 0.0;
+  result[3] = ms;
+  rc = 0;
+done:
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (A) cudaFree(A);
+  if (B) cudaFree(B);
+  if (C) cudaFree(C);
+  return rc;
+}
+
 // Returns 0 on success and writes [max |C_tc - C_ref|, max |C_ref|, error flag, ms per product].
 int selftest_gemm(int n, int prec, int sym, double* result) {
+  if (prec == 0 && n % 128 == 0 && n > 0 && sym >= 0 && sym <= 1) return selftest_gemm_f64(n, sym, result);
   if (n % 128 || n <= 0 || (prec != XLBOMD_FP16x3_ID && prec != XLBOMD_BF16x3_ID)) return -1;
+  const bool single = sym >= 4;   // one 16-bit product (hi operands only), as in the single-product chains
+  if (single) sym -= 4;
+  if (sym < 0 || sym > 2) return -1;
   EngineSplit eng(prec);
   const size_t cnt = (size_t)n * n;
   double *A = nullptr, *B = nullptr, *Cref = nullptr, *Cref2 = nullptr, *out = nullptr;
@@ -720,6 +759,7 @@ int selftest_gemm(int n, int prec, int sym, double* result) {
   {
     Epi ep;
     ep.pairs = pair ? 2 : 1;
+    ep.nseg = single ? 1 : 3;
     if (eng.gemm(s, n, sa, sb, sc, ep, sym != 0, nullptr)) goto done;
     cudaEventRecord(e0, s);
     for (int r = 0; r < 5; ++r)

@@ -528,15 +528,21 @@ __global__ void __launch_bounds__(192, 1)
 
 // Persistent variant: one CTA per SM walks the tiles id = blockIdx.x, blockIdx.x + gridDim.x, ...
 // The producer and MMA threads run ahead into the next tile while the epilogue drains the
-// previous one.  The three segments run in order (hi*hi over all K into accumulator 0, then
-// the two corrections into accumulator 1), so accumulator 0 is busy for the first third of a
-// tile only: the epilogue first folds accumulator 0 into accumulator 1 in tensor memory
-// (tcgen05.ld + tcgen05.st) and releases it, and the next tile's hi*hi third overlaps the rest
-// of the epilogue (side inputs, stores), which releases accumulator 1 before the next tile's
-// correction segments need it.  Barriers: full/empty (operand ring), acc_full (MMA -> epilogue,
-// one phase per tile), acc0_free and acc1_free (epilogue -> MMA, four warp arrivals per tile).
-// Every wait is bounded; a role that gives up records an error and raises a shared abort flag
-// that ends the other roles' loops.
+// previous one.  Two accumulator modes:
+//  - split products (three segments, or the accumulator split): the segments run in order
+//    (hi*hi into accumulator 0, then the corrections into accumulator 1), so accumulator 0 is
+//    busy for the first part of a tile only: the epilogue first folds accumulator 0 into
+//    accumulator 1 in tensor memory (tcgen05.ld + tcgen05.st) and releases it, and the next
+//    tile's hi*hi blocks overlap the rest of the epilogue (side inputs, stores), which releases
+//    accumulator 1 before the next tile's correction segments need it.  acc_full[0] carries one
+//    phase per tile; acc_free[0] and acc_free[1] one phase per tile each.
+//  - single products (one segment): tiles alternate between the two accumulators (tile it
+//    uses accumulator it % 2), so the whole MMA of the next tile overlaps the epilogue of the
+//    previous one.  acc_full[b] and acc_free[b] carry one phase per use of accumulator b; with
+//    one barrier pair per accumulator no barrier can run two phases ahead of its waiter.
+// Barriers: full/empty (operand ring), acc_full[2] (MMA -> epilogue), acc_free[2] (epilogue ->
+// MMA, four warp arrivals per phase).  Every wait is bounded; a role that gives up records an
+// error and raises a shared abort flag that ends the other roles' loops.
 template <int BN>
 __global__ void __launch_bounds__(192, 1)
     gemm_tc_persistent_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
@@ -554,10 +560,9 @@ __global__ void __launch_bounds__(192, 1)
   uint8_t* stage = sB + STAGES * B_BYTES;   // 4 warps x 2 staging tiles of the epilogue
   uint64_t* full = reinterpret_cast<uint64_t*>(stage + 4 * 2 * STAGE_TILE);
   uint64_t* empty = full + STAGES;
-  uint64_t* acc_full = empty + STAGES;
-  uint64_t* acc0_free = acc_full + 1;
-  uint64_t* acc1_free = acc_full + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 3);
+  uint64_t* acc_full = empty + STAGES;     // [2]
+  uint64_t* acc_free = acc_full + 2;       // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -566,9 +571,10 @@ __global__ void __launch_bounds__(192, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(acc0_free, 4);
-    mbar_init(acc1_free, 4);
+    mbar_init(&acc_full[0], 1);
+    mbar_init(&acc_full[1], 1);
+    mbar_init(&acc_free[0], 4);
+    mbar_init(&acc_free[1], 4);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -586,6 +592,7 @@ __global__ void __launch_bounds__(192, 1)
 
   const int nk = a.K / BK;
   const int total = a.nseg * a.pairs * nk;
+  const bool two_acc = a.nseg > 1 || a.split_acc;   // else: single products alternate accumulators
 
   if (warp == 0) {
     if (lane == 0) {
@@ -629,11 +636,16 @@ __global__ void __launch_bounds__(192, 1)
         int tm, tn;
         if (!tile_coords(a, id, tm, tn)) break;
         bool ok = true;
+        const int buf = two_acc ? 0 : (it & 1);            // single products: accumulator of this tile
+        const int use = two_acc ? it : (it >> 1);          // earlier uses of acc_full[buf]
+        const int nk0 = two_acc ? acc1_start(a, nk) : total;   // first K block of accumulator 1
         for (int kb = 0; kb < total; ++kb, ++g) {
-          // the previous tile's epilogue must have released the accumulator this segment writes
-          const int nk0 = acc1_start(a, nk);              // first K block of accumulator 1
-          if (it > 0 && (kb == 0 || kb == nk0)) {
-            if (!mbar_wait(kb == 0 ? acc0_free : acc1_free, (uint32_t)((it - 1) & 1)) || *abort_flag) {
+          // the epilogue must have released the accumulator this K block writes: the previous
+          // tile's (split products) or the one two tiles back (single products)
+          const bool wait0 = two_acc ? (it > 0 && (kb == 0 || kb == nk0)) : (use > 0 && kb == 0);
+          if (wait0) {
+            const int fb = two_acc ? (kb == 0 ? 0 : 1) : buf;
+            if (!mbar_wait(&acc_free[fb], (uint32_t)((use - 1) & 1)) || *abort_flag) {
               ok = false;
               break;
             }
@@ -646,7 +658,7 @@ __global__ void __launch_bounds__(192, 1)
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t dcol = kb >= nk0 ? (uint32_t)BN : 0u;
+          const uint32_t dcol = (two_acc ? kb >= nk0 : buf == 1) ? (uint32_t)BN : 0u;
           const bool first = (kb == 0) || (kb == nk0);
 #pragma unroll
           for (int j = 0; j < BK / 16; ++j) {
@@ -661,7 +673,7 @@ __global__ void __launch_bounds__(192, 1)
           *abort_flag = 1;
           break;
         }
-        mma_commit(acc_full);
+        mma_commit(&acc_full[buf]);
       }
     }
   } else {
@@ -676,15 +688,17 @@ __global__ void __launch_bounds__(192, 1)
       int tm, tn;
       if (!tile_coords(a, id, tm, tn)) break;
       prefetch_sides<BN>(a, tm, tn, (warp - 2) * 32 + lane);
-      const bool got = mbar_wait(acc_full, (uint32_t)(it & 1));
+      const int buf = two_acc ? 0 : (it & 1);
+      const int use = two_acc ? it : (it >> 1);
+      const bool got = mbar_wait(&acc_full[buf], (uint32_t)(use & 1));
       if (!__all_sync(0xffffffffu, got) || *abort_flag) {
         if (lane == 0) atomicExch(a.err, 3);
         *abort_flag = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // pass 1: accumulator 1 <- accumulator 0 + accumulator 1, then release accumulator 0
-      const bool two_acc = a.nseg > 1 || a.split_acc;
+      // pass 1 (split products): accumulator 1 <- accumulator 0 + accumulator 1, then release
+      // accumulator 0
       if (two_acc) {
         for (int ch = 0; ch < BN / 32; ++ch) {
           float v[32], w[32];
@@ -697,10 +711,11 @@ __global__ void __launch_bounds__(192, 1)
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(acc0_free);
+        if (lane == 0) mbar_arrive(&acc_free[0]);
       }
-      // pass 2: the epilogue proper from the summed accumulator
-      const uint32_t src = two_acc ? (uint32_t)BN : 0u;
+      // pass 2: the epilogue proper from the summed accumulator (split products) or from this
+      // tile's accumulator (single products)
+      const uint32_t src = (two_acc || buf == 1) ? (uint32_t)BN : 0u;
       const int row0 = tm * BM + q * 32;
       const int row = row0 + lane;
       float vmax = 0.0f;
@@ -713,10 +728,7 @@ __global__ void __launch_bounds__(192, 1)
       if (lane == 0 && a.amax) atomicMax(a.amax, __float_as_uint(vmax));
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) {
-        if (!two_acc) mbar_arrive(acc0_free);
-        mbar_arrive(acc1_free);
-      }
+      if (lane == 0) mbar_arrive(&acc_free[two_acc ? 1 : buf]);
     }
   }
 
@@ -792,7 +804,7 @@ int smem_bytes() {
 
 template <int BN>
 int smem_bytes_persistent() {
-  return STAGES * (A_BYTES + BN * BK * 2) + 4 * 2 * 32 * 33 * 4 + (2 * STAGES + 3) * 8 + 16 + 1024;
+  return STAGES * (A_BYTES + BN * BK * 2) + 4 * 2 * 32 * 33 * 4 + (2 * STAGES + 4) * 8 + 16 + 1024;
 }
 
 // 1: persistent CTAs (default); 0: one CTA per output tile (XLBOMD_GEMM=classic).
@@ -806,18 +818,48 @@ int tc_variant() {
   return v;
 }
 
-int sm_count() {
-  static int n = 0;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      n = 0;
-  });
-  return n > 0 ? n : 148;
+// Per-device launch state: the SM count and whether each kernel's dynamic shared-memory limit
+// has been raised on that device (a process may drive several devices).
+constexpr int kMaxDevices = 64;
+struct DeviceState {
+  int sms = 0;
+  bool smem_set[4] = {false, false, false, false};
+};
+std::mutex g_dev_mu;
+DeviceState g_dev[kMaxDevices];
+
+int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+  return dev;
 }
 
+int sm_count() {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  DeviceState& d = g_dev[dev];
+  if (d.sms <= 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      return 148;
+    }
+    d.sms = n;
+  }
+  return d.sms;
+}
+
+// Raise kernel `slot`'s dynamic shared-memory limit to `bytes` on the current device (once per
+// device; a failed attempt is retried on the next launch).
+template <typename Kern>
+cudaError_t ensure_smem(int slot, Kern kern, int bytes) {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (g_dev[dev].smem_set[slot]) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) g_dev[dev].smem_set[slot] = true;
+  return e;
+}
 
 }  // namespace
 
@@ -868,21 +910,13 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
   if (tc_variant() == 1) {
     const int grid = std::min(nblocks, sm_count());
     if (wide) {
-      static std::once_flag once;
-      static cudaError_t attr = cudaSuccess;
       const int sb = smem_bytes_persistent<256>();
-      std::call_once(once, [&] {
-        attr = cudaFuncSetAttribute(gemm_tc_persistent_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
-      });
+      const cudaError_t attr = ensure_smem(0, gemm_tc_persistent_kernel<256>, sb);
       if (attr != cudaSuccess) return attr;
       gemm_tc_persistent_kernel<256><<<grid, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo, args, nblocks);
     } else {
-      static std::once_flag once;
-      static cudaError_t attr = cudaSuccess;
       const int sb = smem_bytes_persistent<128>();
-      std::call_once(once, [&] {
-        attr = cudaFuncSetAttribute(gemm_tc_persistent_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
-      });
+      const cudaError_t attr = ensure_smem(1, gemm_tc_persistent_kernel<128>, sb);
       if (attr != cudaSuccess) return attr;
       gemm_tc_persistent_kernel<128><<<grid, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo, args, nblocks);
     }
@@ -890,22 +924,14 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
     return cudaGetLastError();
   }
   if (wide) {
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
     const int sb = smem_bytes<256>();
-    std::call_once(once, [&] {
-      attr = cudaFuncSetAttribute(gemm_tc_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
-    });
+    const cudaError_t attr = ensure_smem(2, gemm_tc_kernel<256>, sb);
     if (attr != cudaSuccess) return attr;
     gemm_tc_kernel<256><<<nblocks, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo, args);
     note_launch();
   } else {
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
     const int sb = smem_bytes<128>();
-    std::call_once(once, [&] {
-      attr = cudaFuncSetAttribute(gemm_tc_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
-    });
+    const cudaError_t attr = ensure_smem(3, gemm_tc_kernel<128>, sb);
     if (attr != cudaSuccess) return attr;
     gemm_tc_kernel<128><<<nblocks, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo, args);
     note_launch();

@@ -51,6 +51,23 @@ def test_pair_product_matches_fp64(X, n, prec, bound):
     assert err < 2 * bound * n, (err, ms)
 
 
+@pytest.mark.parametrize("n", [384, 2944, 4096, 6144, 8192])
+@pytest.mark.parametrize("sym", [0, 1, 2])
+@pytest.mark.parametrize("prec,u", [("fp16x3", 2.0 ** -11), ("bf16x3", 2.0 ** -8)])
+def test_single_product_matches_fp64(X, n, sym, prec, u):
+    # one 16-bit product (hi operands only), the product of the single-product chains; below
+    # n = 8192 consecutive tiles of a CTA alternate between the two TMEM accumulators, at
+    # n = 8192 the hi*hi sum splits over both.  Each operand carries a relative rounding error of
+    # at most u, so an entry's error is a sum of n terms a db + b da with standard deviation about
+    # u sqrt(2 n / 27) for U(-1, 1) inputs; the bound is 8 of those (twice that for the pair
+    # product), far below the O(sqrt(n)) error of a wrong tile or accumulator
+    err, flag, ms = X.binding.selftest_gemm(n, prec, sym if sym != 2 else 2, single=True)
+    bound = 8.0 * u * np.sqrt(2.0 * n / 27.0) * (2.0 if sym == 2 else 1.0)
+    print(prec, n, "single", sym, err, bound, ms)
+    assert flag == 0
+    assert err < bound, (err, bound, ms)
+
+
 @pytest.mark.parametrize("prec", ["fp16x3", "bf16x3"])
 @pytest.mark.parametrize("case", ["tiny24", "ragged37"])
 @pytest.mark.parametrize("mu_prec", [0, 1])
@@ -109,6 +126,39 @@ def test_full_size_charges_against_oracle(X, mu_prec):
     err = np.max(np.abs(q - q_ref))
     print("full size fp16x3 mu_prec", mu_prec, "|dq|", err)
     assert err < 1e-5
+
+
+def test_accumulator_split_size_against_oracle(X):
+    # 2048 atoms (N = 8192): the first size whose products split their hi*hi sums over both
+    # TMEM accumulators.  At a seeded (R, n) with the Newton search started 5 meV off the
+    # oracle's mu (no SCF needed), the FP16x3 path with the bench's chain precisions (probe and
+    # mu chains at one 16-bit product) must match the oracle's eigendecomposition element by
+    # element: charges to 1e-5 e, forces to 1e-4 eV/A; Omega and the rank-4 K r are reported
+    # against it too.  Te = 1000 K and 10 squarings are the 4096-atom precision workload's.
+    s = synth.make_system(2048, 1705)
+    p = X.default_params(Te=1000.0, n_sq=10, rank_m=4, mix_alpha=ALPHA_MIX, kernel_c=1 - 1 / ALPHA_MIX,
+                         prec="fp16x3", mu_tol=1e-3, rep_A=40.0, rep_rho=0.3, kernel_prec=1, mu_prec=1)
+    m = O.Model(Te=1000.0, n_sq=10, rep_A=40.0, rep_rho=0.3)
+    rng = np.random.default_rng(2048)
+    n = rng.normal(scale=0.01, size=s.natoms)
+    n -= n.mean()
+    ref = O.evaluate(s.R, s.L, s.Z, n, m, O.XLParams(rank_m=4, kernel_c=p.kernel_c))
+    with X.Context(p, [sysdict(s)]) as ctx:
+        assert ctx.sizes(0)[2] == 8192
+        ctx.set(0, X.N, n)
+        ctx.set(0, X.MU, [ref.dens.mu + 0.005])
+        ctx.build_H(0)
+        ctx.density(0)
+        ctx.kernel_update(0)
+        ctx.energy(0)
+        q, F, Kr, E = ctx.get(0, X.Q), ctx.get(0, X.F), ctx.get(0, X.KR), ctx.get(0, X.ENERGY)
+    dq, dF = np.abs(q - ref.q).max(), np.abs(F - ref.F).max()
+    dK = np.abs(Kr - ref.Kr).max() / np.abs(ref.Kr).max()
+    print("2048 atoms fp16x3: |dq|", dq, "|dF|", dF, "dOmega", E[0] - ref.Omega, "K r rel", dK)
+    assert dq < 1e-5
+    assert dF < 1e-4
+    assert abs(E[0] - ref.Omega) < 1e-6 * abs(ref.Omega)
+    assert dK < 2e-3
 
 
 @pytest.mark.parametrize("prec,tol", [("fp16x3", 1e-4), ("bf16x3", 1e-3)])

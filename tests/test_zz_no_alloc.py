@@ -57,6 +57,16 @@ def test_noalloc_response_matches_allocating_entry_point(X):
             a, b = w_ref.cpu().numpy(), w_new.cpu().numpy()
             assert np.all(np.isfinite(b)), call
             assert np.max(np.abs(a - b)) < 1e-8 * max(1.0, np.max(np.abs(a))), call
+        # the defining property: a call after the first one (which looks up the array's device
+        # address) takes no device memory; cudaMemGetInfo would see any allocation (>= 2 MB pages)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        st = lib.xlbomd_response_noalloc(ctx.h, 0, ctypes.c_void_p(vd.data_ptr()),
+                                         ctypes.c_void_p(w_new.data_ptr()))
+        assert st == 0, lib.xlbomd_last_error(ctx.h)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0, (free0, free1)
 
 
 def test_noalloc_response_rejects_systems_beyond_the_static_limit(X):
