@@ -36,8 +36,15 @@ inline unsigned nblk(size_t count, int tpb = 256) { return (unsigned)((count + t
 constexpr unsigned kEwBlocks = 152 * 16;
 inline unsigned ew_blocks(size_t count) { return (unsigned)std::min<size_t>(nblk(count), kEwBlocks); }
 
-// products of at least this size split their hi*hi sums over both accumulators
+// One-CTA-per-tile product kernel: products of at least this size split their hi*hi sums over
+// both accumulators.
 constexpr int kSplitAccMin = 8192;
+// Persistent product kernel, split products: the hi*hi sum is accumulated in chunks of this many
+// 64-wide K blocks (K = 1024), each folded into the running sum with round-to-nearest FP32 adds.
+// The tensor core truncates as it accumulates, so a sum's error grows with its length: at 2048
+// atoms (N = 8192) the charge error fell from 4.7e-5 e (one 8192-long sum) to 2.5e-5 e (two
+// halves), and it keeps halving with the chunk length.
+constexpr int kChunkKb = 16;
 
 // Raise *amax to the block's max |v| with one atomic per block (all threads
 // of the block must call it).
@@ -91,6 +98,34 @@ __global__ void convert_split_kernel(size_t count, const float* __restrict__ f, 
     split16<BF16>(x.w * s, h.w, l.w);
     h4[i] = h;
     l4[i] = l;
+  }
+}
+
+// The hi part alone, for matrices that only enter single products (hi*hi).
+template <bool BF16>
+__global__ void convert_hi_kernel(size_t count, const float* __restrict__ f, const unsigned* __restrict__ amax,
+                                  uint16_t* __restrict__ hi, float* __restrict__ scale) {
+  const float m = __uint_as_float(*amax);
+  float s = 1.0f;
+  if (m > 0.0f && isfinite(m)) s = ldexpf(1.0f, 10 - ilogbf(m));
+  if (blockIdx.x == 0 && threadIdx.x == 0) *scale = s;
+  const float4* f4 = reinterpret_cast<const float4*>(f);
+  ushort4* h4 = reinterpret_cast<ushort4*>(hi);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count / 4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 x = f4[i];
+    ushort4 h;
+    if (BF16) {
+      h.x = __bfloat16_as_ushort(__float2bfloat16_rn(x.x * s));
+      h.y = __bfloat16_as_ushort(__float2bfloat16_rn(x.y * s));
+      h.z = __bfloat16_as_ushort(__float2bfloat16_rn(x.z * s));
+      h.w = __bfloat16_as_ushort(__float2bfloat16_rn(x.w * s));
+    } else {
+      h.x = __half_as_ushort(__float2half_rn(x.x * s));
+      h.y = __half_as_ushort(__float2half_rn(x.y * s));
+      h.z = __half_as_ushort(__float2half_rn(x.z * s));
+      h.w = __half_as_ushort(__float2half_rn(x.w * s));
+    }
+    h4[i] = h;
   }
 }
 
@@ -259,6 +294,7 @@ struct Epi {
   float dvec_scale = 1.0f;
   bool out64 = false;       // write C.d (and convert from it) instead of C.f
   bool convert = true;      // produce the split operand pair of C
+  bool hi_only = false;     // produce only the hi operand (C enters single products only)
   int nseg = 3;             // 3: hi*hi + hi*lo + lo*hi; 1: hi*hi only
   int pairs = 1;            // 2: C = A B^T + B A^T
 };
@@ -286,6 +322,17 @@ class EngineSplit : public Engine {
       convert_split_kernel<true><<<g, 256, 0, s>>>(count, m.f, m.amax, m.hi, m.lo, m.scale);
     else
       convert_split_kernel<false><<<g, 256, 0, s>>>(count, m.f, m.amax, m.hi, m.lo, m.scale);
+    note_launch();
+    return cudaGetLastError();
+  }
+
+  cudaError_t convert_hi(cudaStream_t s, SplitMat& m, int np) {
+    const size_t count = (size_t)np * np;
+    const unsigned g = std::min<size_t>(nblk(count), 152 * 16);
+    if (bf16_)
+      convert_hi_kernel<true><<<g, 256, 0, s>>>(count, m.f, m.amax, m.hi, m.scale);
+    else
+      convert_hi_kernel<false><<<g, 256, 0, s>>>(count, m.f, m.amax, m.hi, m.scale);
     note_launch();
     return cudaGetLastError();
   }
@@ -354,6 +401,7 @@ class EngineSplit : public Engine {
     // large products: split the hi*hi sums over both accumulators (the tensor core truncates as it
     // accumulates, so a K-long sum's error grows with K)
     a.split_acc = (np >= kSplitAccMin) ? 1 : 0;
+    a.chunk_kb = kChunkKb;
     RET(gemm_tc(s, np, A.hi, A.lo, B.hi, B.lo, a, tl.first, tl.first + 2 * n128, n128, n256));
     // kind bits: 1 sym, 2 E, 4 E2, 8 E64, 16 E64 transposed, 32 FP64 output
     const int kind = (sym ? 1 : 0) | (e.E ? 2 : 0) | (e.E2 ? 4 : 0) | (e.E64 ? 8 : 0) | (e.e64_trans ? 16 : 0) |
@@ -361,6 +409,7 @@ class EngineSplit : public Engine {
     RET(prof_end(s, 2.0 * (double)np * np * np * (sym ? 0.5 : 1.0) * e.pairs, kind));
     if (stats) stats[3] += (sym ? 0.5 : 1.0) * e.pairs;
     if (!e.convert) return cudaSuccess;
+    if (e.hi_only && !e.out64) return convert_hi(s, C, np);
     return e.out64 ? convert_d(s, C, np) : convert(s, C, np);
   }
 
@@ -426,6 +475,11 @@ class EngineSplit : public Engine {
     const size_t cnt = (size_t)np * np;
     // either chain may run on the hi operands alone (the mu chain is the one with a full last level)
     const int nseg = full_last ? mu_nseg_ : probe_nseg_;
+    // A single-product chain keeps M and T1 as FP32 values with hi operands only: its products
+    // carry ~2^-11 relative error, so the double-float values and lo operands of the three-product
+    // chain would add traffic and no accuracy.  The last level still writes the double-float array
+    // the reductions read (with a zero low word).
+    const bool single = (nseg == 1);
     SplitMat* T1 = &m.sT1a;
     SplitMat* T1n = &m.sT1b;
     for (int k = 0; k < n; ++k) {
@@ -433,8 +487,10 @@ class EngineSplit : public Engine {
       RET(cudaMemsetAsync(m.sA1.amax, 0, sizeof(unsigned), s));
       Epi em;                                                                    // Mt = 2 T1 - T_{k+1} A1
       em.alpha = -1.f;
-      em.out64 = true;
-      em.nseg = nseg;
+      em.out64 = !single || (last && !full_last);
+      em.hi_only = single;
+      em.convert = !(last && !full_last);                                        // the last M of a probe
+      em.nseg = nseg;                                                            // chain is only reduced
       if (k == 0) {
         level0_A1_d_kernel<<<ew_blocks(cnt), 256, 0, s>>>(np, m.sT[0].d, dvec, m.sA1.f, m.sA1.amax);
         note_launch();
@@ -448,11 +504,16 @@ class EngineSplit : public Engine {
         ea.nseg = nseg;
         ea.pairs = 2;
         RET(gemm(s, np, m.sT[k], *T1, m.sA1, ea, true, stats));
-        em.E64 = T1->d;                                                           // symmetric: read transposed
-        em.e64_trans = 1;
-        em.beta64 = 2.0f;
+        if (single) {
+          em.E = T1;                                                              // FP32, symmetric
+          em.beta = 2.0f;
+        } else {
+          em.E64 = T1->d;                                                         // symmetric: read transposed
+          em.e64_trans = 1;
+          em.beta64 = 2.0f;
+        }
       }
-      RET(convert(s, m.sA1, np));
+      RET(single ? convert_hi(s, m.sA1, np) : convert(s, m.sA1, np));
       RET(gemm(s, np, m.sT[k + 1], m.sA1, m.sMt, em, false, stats));
       if (last && !full_last) {
         row_dot_last_kernel<<<(N + 7) / 8, 256, 0, s>>>(N, np, m.sY[k].f, m.sMt.d, out_diag);
@@ -462,10 +523,17 @@ class EngineSplit : public Engine {
       SplitMat* dst = (last && full_last) ? &m.sTmu : T1n;
       Epi ey;                                                                    // T1' = M - W M
       ey.alpha = -1.f;
-      ey.E64 = m.sMt.d;
-      ey.beta64 = 1.0f;
-      ey.e64_trans = 1;
-      ey.out64 = true;
+      if (single) {
+        ey.E = &m.sMt;                                                            // read transposed: M
+        ey.beta = 1.0f;
+        ey.out64 = last;                                                          // T_mu (double-float)
+        ey.hi_only = true;
+      } else {
+        ey.E64 = m.sMt.d;
+        ey.beta64 = 1.0f;
+        ey.e64_trans = 1;
+        ey.out64 = true;
+      }
       ey.convert = !last;
       ey.nseg = nseg;
       RET(gemm(s, np, m.sY[k], m.sMt, *dst, ey, true, stats));
@@ -602,7 +670,7 @@ cudaError_t alloc_matset_split(MatSet& m, cudaStream_t s) {
     SplitMat* m;
     int what;
   } w[] = {{&m.sS, kF},  {&m.sQ, kF},  {&m.sYw, kF},  {&m.sA1, kF},
-           {&m.sMt, kD}, {&m.sT1a, kD}, {&m.sT1b, kD}, {&m.sTmu, kD}};
+           {&m.sMt, kD | kF}, {&m.sT1a, kD | kF}, {&m.sT1b, kD | kF}, {&m.sTmu, kD}};
   for (auto& x : w) {
     RET(alloc_split(*x.m, np, sf + idx, su + idx, x.what, s));
     ++idx;

@@ -135,7 +135,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  // r tied to the wait: no use of the loaded registers is scheduled before it
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])::"memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
@@ -155,6 +156,27 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
       "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])),
       "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
       : "memory");
+}
+
+// 64 columns of this warp's 32 lanes, without waiting (tcgen05.wait::ld before use)
+__device__ __forceinline__ void tmem_ld64_nowait(uint32_t taddr, uint32_t (&r)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr));
+}
+
+// Wait for this thread's tcgen05.ld results; r is tied to the wait so that no use of the loaded
+// registers is scheduled before it.
+__device__ __forceinline__ void tmem_wait_ld64(uint32_t (&r)[64]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]), "+r"(r[32]), "+r"(r[33]), "+r"(r[34]), "+r"(r[35]), "+r"(r[36]), "+r"(r[37]), "+r"(r[38]), "+r"(r[39]), "+r"(r[40]), "+r"(r[41]), "+r"(r[42]), "+r"(r[43]), "+r"(r[44]), "+r"(r[45]), "+r"(r[46]), "+r"(r[47]), "+r"(r[48]), "+r"(r[49]), "+r"(r[50]), "+r"(r[51]), "+r"(r[52]), "+r"(r[53]), "+r"(r[54]), "+r"(r[55]), "+r"(r[56]), "+r"(r[57]), "+r"(r[58]), "+r"(r[59]), "+r"(r[60]), "+r"(r[61]), "+r"(r[62]), "+r"(r[63])::"memory");
+}
+
+// Orders the uses of r after the preceding tcgen05.wait::ld (volatile asm statements keep their order).
+__device__ __forceinline__ void tmem_after_wait64(uint32_t (&r)[64]) { asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]), "+r"(r[32]), "+r"(r[33]), "+r"(r[34]), "+r"(r[35]), "+r"(r[36]), "+r"(r[37]), "+r"(r[38]), "+r"(r[39]), "+r"(r[40]), "+r"(r[41]), "+r"(r[42]), "+r"(r[43]), "+r"(r[44]), "+r"(r[45]), "+r"(r[46]), "+r"(r[47]), "+r"(r[48]), "+r"(r[49]), "+r"(r[50]), "+r"(r[51]), "+r"(r[52]), "+r"(r[53]), "+r"(r[54]), "+r"(r[55]), "+r"(r[56]), "+r"(r[57]), "+r"(r[58]), "+r"(r[59]), "+r"(r[60]), "+r"(r[61]), "+r"(r[62]), "+r"(r[63])); }
+
+__device__ __forceinline__ void tmem_st64(uint32_t taddr, const uint32_t (&v)[64]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x64.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63, %64};" ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31]), "r"(v[32]), "r"(v[33]), "r"(v[34]), "r"(v[35]), "r"(v[36]), "r"(v[37]), "r"(v[38]), "r"(v[39]), "r"(v[40]), "r"(v[41]), "r"(v[42]), "r"(v[43]), "r"(v[44]), "r"(v[45]), "r"(v[46]), "r"(v[47]), "r"(v[48]), "r"(v[49]), "r"(v[50]), "r"(v[51]), "r"(v[52]), "r"(v[53]), "r"(v[54]), "r"(v[55]), "r"(v[56]), "r"(v[57]), "r"(v[58]), "r"(v[59]), "r"(v[60]), "r"(v[61]), "r"(v[62]), "r"(v[63]) : "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -529,26 +551,91 @@ __global__ void __launch_bounds__(192, 1)
 // Persistent variant: one CTA per SM walks the tiles id = blockIdx.x, blockIdx.x + gridDim.x, ...
 // The producer and MMA threads run ahead into the next tile while the epilogue drains the
 // previous one.  Two accumulator modes:
-//  - split products (three segments, or the accumulator split): the segments run in order
-//    (hi*hi into accumulator 0, then the corrections into accumulator 1), so accumulator 0 is
-//    busy for the first part of a tile only: the epilogue first folds accumulator 0 into
-//    accumulator 1 in tensor memory (tcgen05.ld + tcgen05.st) and releases it, and the next
-//    tile's hi*hi blocks overlap the rest of the epilogue (side inputs, stores), which releases
-//    accumulator 1 before the next tile's correction segments need it.  acc_full[0] carries one
-//    phase per tile; acc_free[0] and acc_free[1] one phase per tile each.
-//  - single products (one segment): tiles alternate between the two accumulators (tile it
-//    uses accumulator it % 2), so the whole MMA of the next tile overlaps the epilogue of the
-//    previous one.  acc_full[b] and acc_free[b] carry one phase per use of accumulator b; with
-//    one barrier pair per accumulator no barrier can run two phases ahead of its waiter.
+//  - single products (one segment, hi*hi only): tiles alternate between the two accumulators
+//    (tile it uses accumulator it % 2), so the whole MMA of the next tile overlaps the epilogue
+//    of the previous one.  acc_full[b] and acc_free[b] carry one phase per use of accumulator b;
+//    with one barrier pair per accumulator no barrier can run two phases ahead of its waiter.
+//  - split products (three segments): the tensor core truncates as it accumulates, so the error
+//    of a K-long sum grows with K.  The hi*hi sum is therefore accumulated in chunks of
+//    chunk_kb K blocks, alternately in the two accumulators, and the epilogue warps fold each
+//    finished chunk into the running sum with round-to-nearest FP32 adds (tcgen05.ld + st).
+//    Steps of a tile with c chunks, accumulators named relative to the tile's parity p: step 0
+//    = chunk 0 into accumulator p; step 1 = the two correction segments into accumulator p ^ 1
+//    while it is small, then chunk 1 on top of them; step s >= 2 = chunk s into accumulator
+//    (s % 2) ^ p.  After step f (f = 1 .. F, F = max(1, c - 1)) the epilogue folds: accumulator
+//    (f % 2) ^ p += the other one, which it releases for step f + 1; the last fold leaves the sum
+//    in accumulator (F % 2) ^ p, which the epilogue writes out and releases.  The next tile's
+//    parity makes its step 0 use the accumulator the last fold released, so that step 0
+//    overlaps the write-out.  acc_full[0] carries one phase per fold; acc_free[b] one phase per
+//    release of accumulator b, and the MMA thread waits for release u - 1 of b before its u-th
+//    fresh write to b.  Each phase needs the previous one consumed, so no barrier runs two
+//    phases ahead.
 // Barriers: full/empty (operand ring), acc_full[2] (MMA -> epilogue), acc_free[2] (epilogue ->
 // MMA, four warp arrivals per phase).  Every wait is bounded; a role that gives up records an
 // error and raises a shared abort flag that ends the other roles' loops.
+
+// K-block order of one tile (the producer and the MMA thread walk it alike): the first hi*hi
+// chunk (K blocks 0 .. L0 - 1 of the hi*hi sequence: pair 0's K blocks, then pair 1's), then the
+// Cn correction K blocks (hi*lo, lo*hi of pair 0, then of pair 1), then the rest of the hi*hi
+// sequence.  Counters only, no divisions.
+struct KWalk {
+  int phase;           // 0: first hi*hi chunk, 1: corrections, 2: remaining hi*hi
+  int pr, kind, kidx;  // current K block: operand pair, split part (0 hi*hi, 1 hi*lo, 2 lo*hi), index
+  int h, c;            // hi*hi and correction K blocks issued before the current one
+  int sp, sk;          // hi*hi position to resume at after the corrections
+};
+
+__device__ __forceinline__ void kwalk_begin(KWalk& w) {
+  w.phase = 0;
+  w.pr = w.kind = w.kidx = 0;
+  w.h = w.c = 0;
+  w.sp = w.sk = 0;
+}
+
+__device__ __forceinline__ void kwalk_next(KWalk& w, int nk, int L0, int Cn) {
+  if (w.phase == 1) {
+    ++w.c;
+    if (++w.kidx == nk) {
+      w.kidx = 0;
+      if (w.kind == 1) {
+        w.kind = 2;
+      } else {
+        w.kind = 1;
+        ++w.pr;
+      }
+    }
+    if (w.c == Cn) {
+      w.phase = 2;
+      w.pr = w.sp;
+      w.kind = 0;
+      w.kidx = w.sk;
+    }
+    return;
+  }
+  ++w.h;
+  if (++w.kidx == nk) {
+    w.kidx = 0;
+    ++w.pr;
+  }
+  if (w.phase == 0 && w.h == L0) {
+    w.phase = 2;
+    if (Cn > 0) {
+      w.sp = w.pr;
+      w.sk = w.kidx;
+      w.phase = 1;
+      w.pr = 0;
+      w.kind = 1;
+      w.kidx = 0;
+    }
+  }
+}
+
 template <int BN>
 __global__ void __launch_bounds__(192, 1)
     gemm_tc_persistent_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                               const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
-                   const __grid_constant__ CUtensorMap mA2hi, const __grid_constant__ CUtensorMap mA2lo,
-                   const __grid_constant__ CUtensorMap mB2hi, const __grid_constant__ CUtensorMap mB2lo,
+                              const __grid_constant__ CUtensorMap mA2hi, const __grid_constant__ CUtensorMap mA2lo,
+                              const __grid_constant__ CUtensorMap mB2hi, const __grid_constant__ CUtensorMap mB2lo,
                               TcArgs a, int ntiles) {
   constexpr int B_BYTES = BN * BK * 2;
   constexpr uint32_t TMEM_COLS = 2 * BN;
@@ -592,7 +679,12 @@ __global__ void __launch_bounds__(192, 1)
 
   const int nk = a.K / BK;
   const int total = a.nseg * a.pairs * nk;
-  const bool two_acc = a.nseg > 1 || a.split_acc;   // else: single products alternate accumulators
+  const bool chunked = a.nseg > 1;                 // split products; else single products alternate
+  const int H = a.pairs * nk;                      // hi*hi K blocks
+  const int Cn = total - H;                        // correction K blocks
+  const int Lc = (chunked && a.chunk_kb > 0 && a.chunk_kb < H) ? a.chunk_kb : H;   // chunk length
+  const int nchunks = (H + Lc - 1) / Lc;
+  const int nfold = chunked ? max(1, nchunks - 1) : 0;   // folds per tile
 
   if (warp == 0) {
     if (lane == 0) {
@@ -605,9 +697,9 @@ __global__ void __launch_bounds__(192, 1)
           *abort_flag = 1;
           break;
         }
-        KSeg q;
-        kseg_begin(a, nk, q);
-        for (int kb = 0; kb < total; ++kb, ++g, kseg_next(a, nk, q)) {
+        KWalk w;
+        kwalk_begin(w);
+        for (int kb = 0; kb < total; ++kb, ++g, kwalk_next(w, nk, Lc, Cn)) {
           const int s = g % STAGES;
           const uint32_t ph = (g / STAGES) & 1;
           if (g >= STAGES && !mbar_wait(&empty[s], ph ^ 1)) {
@@ -617,9 +709,9 @@ __global__ void __launch_bounds__(192, 1)
             break;
           }
           mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-          const int kk = q.kidx * BK;
-          const CUtensorMap* ma = (q.kind == 2) ? (q.pr ? &mA2lo : &mAlo) : (q.pr ? &mA2hi : &mAhi);
-          const CUtensorMap* mb = (q.kind == 1) ? (q.pr ? &mB2lo : &mBlo) : (q.pr ? &mB2hi : &mBhi);
+          const int kk = w.kidx * BK;
+          const CUtensorMap* ma = (w.kind == 2) ? (w.pr ? &mA2lo : &mAlo) : (w.pr ? &mA2hi : &mAhi);
+          const CUtensorMap* mb = (w.kind == 1) ? (w.pr ? &mB2lo : &mBlo) : (w.pr ? &mB2hi : &mBhi);
           tma_load_2d(sA + s * A_BYTES, ma, kk, tm * BM, &full[s]);
           tma_load_2d(sB + s * B_BYTES, mb, kk, tn * BN, &full[s]);
         }
@@ -632,24 +724,48 @@ __global__ void __launch_bounds__(192, 1)
       const uint32_t idesc = a.bf16 ? idesc_bf16 : idesc_f16;
       uint32_t g = 0;
       int it = 0;
-      for (int id = blockIdx.x; id < ntiles && !*abort_flag; id += gridDim.x, ++it) {
+      int uses0 = 0, uses1 = 0;      // fresh writes of each accumulator so far (split products)
+      int par = 0;                   // split products: accumulator parity p of this tile
+      for (int id = blockIdx.x; id < ntiles && !*abort_flag; id += gridDim.x, ++it, par ^= (nfold & 1) ^ 1) {
         int tm, tn;
         if (!tile_coords(a, id, tm, tn)) break;
         bool ok = true;
-        const int buf = two_acc ? 0 : (it & 1);            // single products: accumulator of this tile
-        const int use = two_acc ? it : (it >> 1);          // earlier uses of acc_full[buf]
-        const int nk0 = two_acc ? acc1_start(a, nk) : total;   // first K block of accumulator 1
-        for (int kb = 0; kb < total; ++kb, ++g) {
-          // the epilogue must have released the accumulator this K block writes: the previous
-          // tile's (split products) or the one two tiles back (single products)
-          const bool wait0 = two_acc ? (it > 0 && (kb == 0 || kb == nk0)) : (use > 0 && kb == 0);
-          if (wait0) {
-            const int fb = two_acc ? (kb == 0 ? 0 : 1) : buf;
-            if (!mbar_wait(&acc_free[fb], (uint32_t)((use - 1) & 1)) || *abort_flag) {
-              ok = false;
-              break;
+        const int buf = it & 1;      // single products: accumulator of this tile
+        int cur = 0;                 // accumulator of the current step
+        int bnd = 2 * Lc;            // first hi*hi K block of the next step s >= 2
+        KWalk w;
+        kwalk_begin(w);
+        for (int kb = 0; kb < total; ++kb, ++g, kwalk_next(w, nk, Lc, Cn)) {
+          // does this K block start a step, and into which accumulator?
+          int fresh = -1;            // accumulator written fresh from this K block, or -1
+          if (!chunked) {
+            if (kb == 0) fresh = buf;
+          } else if (w.phase == 0) {
+            if (w.h == 0) fresh = par;
+          } else if (w.phase == 1) {
+            if (w.c == 0) fresh = par ^ 1;
+          } else if (w.h == bnd) {
+            mma_commit(&acc_full[0]);                    // the previous step is complete: fold it
+            fresh = ((bnd / Lc) & 1) ^ par;
+            bnd += Lc;
+          }
+          if (fresh >= 0) {
+            // wait until the epilogue has released the accumulator's previous contents
+            const int u = chunked ? (fresh ? uses1 : uses0) : (it >> 1);
+            if (u > 0) {
+              if (!mbar_wait(&acc_free[fresh], (uint32_t)((u - 1) & 1)) || *abort_flag) {
+                ok = false;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (chunked) {
+              if (fresh)
+                ++uses1;
+              else
+                ++uses0;
+            }
+            cur = fresh;
           }
           const int s = g % STAGES;
           const uint32_t ph = (g / STAGES) & 1;
@@ -658,13 +774,12 @@ __global__ void __launch_bounds__(192, 1)
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t dcol = (two_acc ? kb >= nk0 : buf == 1) ? (uint32_t)BN : 0u;
-          const bool first = (kb == 0) || (kb == nk0);
+          const uint32_t dcol = cur ? (uint32_t)BN : 0u;
 #pragma unroll
           for (int j = 0; j < BK / 16; ++j) {
             const uint64_t ad = smem_desc(sA + s * A_BYTES + j * 32);
             const uint64_t bd = smem_desc(sB + s * B_BYTES + j * 32);
-            mma_f16(tmem + dcol, ad, bd, idesc, (first && j == 0) ? 0u : 1u);
+            mma_f16(tmem + dcol, ad, bd, idesc, (fresh >= 0 && j == 0) ? 0u : 1u);
           }
           mma_commit(&empty[s]);
         }
@@ -673,7 +788,7 @@ __global__ void __launch_bounds__(192, 1)
           *abort_flag = 1;
           break;
         }
-        mma_commit(&acc_full[buf]);
+        mma_commit(&acc_full[chunked ? 0 : buf]);         // last step of the tile
       }
     }
   } else {
@@ -684,51 +799,63 @@ __global__ void __launch_bounds__(192, 1)
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     const float inv = a.alpha / (__ldg(a.sa) * __ldg(a.sb));
     int it = 0;
-    for (int id = blockIdx.x; id < ntiles && !*abort_flag; id += gridDim.x, ++it) {
+    uint32_t ev = 0;                 // acc_full[0] phases consumed (split products)
+    int par = 0;                     // split products: accumulator parity p of this tile
+    for (int id = blockIdx.x; id < ntiles && !*abort_flag; id += gridDim.x, ++it, par ^= (nfold & 1) ^ 1) {
       int tm, tn;
       if (!tile_coords(a, id, tm, tn)) break;
       prefetch_sides<BN>(a, tm, tn, (warp - 2) * 32 + lane);
-      const int buf = two_acc ? 0 : (it & 1);
-      const int use = two_acc ? it : (it >> 1);
-      const bool got = mbar_wait(&acc_full[buf], (uint32_t)(use & 1));
-      if (!__all_sync(0xffffffffu, got) || *abort_flag) {
+      int src;                       // accumulator holding the tile's sum
+      bool ok = true;
+      if (!chunked) {
+        src = it & 1;
+        ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[src], (uint32_t)((it >> 1) & 1)));
+        if (ok) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      } else {
+        // fold f: accumulator (f % 2) ^ p += the other one, which is then released
+        src = par;
+        for (int f = 1; f <= nfold && ok; ++f, ++ev) {
+          ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[0], ev & 1));
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const int dst = (f & 1) ^ par, from = dst ^ 1;
+          // 64 columns at a time: both loads in flight before one wait
+          for (int ch = 0; ch < BN / 64; ++ch) {
+            uint32_t v[64], u[64];
+            tmem_ld64_nowait(tmem + lane_base + (uint32_t)(from * BN + ch * 64), v);
+            tmem_ld64_nowait(tmem + lane_base + (uint32_t)(dst * BN + ch * 64), u);
+            tmem_wait_ld64(v);
+            tmem_after_wait64(u);
+#pragma unroll
+            for (int i = 0; i < 64; ++i) v[i] = __float_as_uint(__uint_as_float(v[i]) + __uint_as_float(u[i]));
+            tmem_st64(tmem + lane_base + (uint32_t)(dst * BN + ch * 64), v);
+          }
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_free[from]);
+          src = dst;
+        }
+      }
+      if (!ok || *abort_flag) {
         if (lane == 0) atomicExch(a.err, 3);
         *abort_flag = 1;
         break;
       }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // pass 1 (split products): accumulator 1 <- accumulator 0 + accumulator 1, then release
-      // accumulator 0
-      if (two_acc) {
-        for (int ch = 0; ch < BN / 32; ++ch) {
-          float v[32], w[32];
-          tmem_ld32(tmem + lane_base + (uint32_t)(ch * 32), v);
-          tmem_ld32(tmem + lane_base + (uint32_t)(BN + ch * 32), w);
-#pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] += w[i];
-          tmem_st32(tmem + lane_base + (uint32_t)(BN + ch * 32), v);
-        }
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&acc_free[0]);
-      }
-      // pass 2: the epilogue proper from the summed accumulator (split products) or from this
-      // tile's accumulator (single products)
-      const uint32_t src = (two_acc || buf == 1) ? (uint32_t)BN : 0u;
+      // the epilogue proper from the accumulator that holds the sum
       const int row0 = tm * BM + q * 32;
       const int row = row0 + lane;
       float vmax = 0.0f;
       for (int ch = 0; ch < BN / 32; ++ch) {
         float v[32];
-        tmem_ld32(tmem + lane_base + src + (uint32_t)(ch * 32), v);
+        tmem_ld32(tmem + lane_base + (uint32_t)(src * BN + ch * 32), v);
         epilogue_chunk(a, v, row, row0, tn * BN + ch * 32, lane, tx, ty, inv, vmax);
       }
       for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
       if (lane == 0 && a.amax) atomicMax(a.amax, __float_as_uint(vmax));
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_free[two_acc ? 1 : buf]);
+      if (lane == 0) mbar_arrive(&acc_free[src]);
     }
   }
 

@@ -10,7 +10,10 @@ namespace xl {
 struct TcArgs {
   int K = 0;                      // inner dimension (set by gemm_tc)
   int n = 0;                      // matrix size (set by gemm_tc)
-  int split_acc = 0;              // 1: the hi*hi K blocks split over both accumulators (below)
+  int split_acc = 0;              // one-CTA-per-tile kernel: 1 = the hi*hi K blocks split over both
+                                  // accumulators (below)
+  int chunk_kb = 0;               // persistent kernel, split products: the hi*hi sum is accumulated in
+                                  // chunks of this many K blocks, folded in FP32 (0: one chunk)
   int nseg = 3;                   // 1: hi only; 3: hi*hi + hi*lo + lo*hi
   int pairs = 1;                  // 2: C = A B^T + B A^T (the swapped pair as a second K range)
   int sym = 0;                    // symmetric output (upper tiles, mirrored)
