@@ -353,13 +353,23 @@ class EngineSplit : public Engine {
   // before the first product).
   cudaError_t prep_tiles(int np, cudaStream_t s) {
     if (tiles_.count(np)) return cudaSuccess;
-    std::vector<int> t128 = tc_sym_tiles(np, 128), t256 = (np % 256 == 0) ? tc_sym_tiles(np, 256) : std::vector<int>();
+    const bool wide = (np % 256 == 0);
+    std::vector<int> t128 = tc_sym_tiles(np, 128), t256 = wide ? tc_sym_tiles(np, 256) : std::vector<int>();
+    std::vector<int> tp = wide ? tc_sym_tiles_pair(np) : std::vector<int>();
     std::vector<int> all(t128);
     all.insert(all.end(), t256.begin(), t256.end());
+    all.insert(all.end(), tp.begin(), tp.end());
     int* d = nullptr;
     RET(cudaMalloc((void**)&d, sizeof(int) * std::max<size_t>(all.size(), 2)));
     RET(cudaMemcpyAsync(d, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice, s));
-    tiles_[np] = {d, {(int)t128.size() / 2, (int)t256.size() / 2}};
+    TcTiles t;
+    t.sym128 = d;
+    t.n128 = (int)t128.size() / 2;
+    t.sym256 = d + t128.size();
+    t.n256 = (int)t256.size() / 2;
+    t.pair = wide ? d + t128.size() + t256.size() : nullptr;
+    t.npair = (int)tp.size() / 2;
+    tiles_[np] = {d, t};
     if (!err_) {
       RET(cudaMalloc((void**)&err_, sizeof(int)));
       RET(cudaMemsetAsync(err_, 0, sizeof(int), s));
@@ -370,7 +380,7 @@ class EngineSplit : public Engine {
   cudaError_t gemm(cudaStream_t s, int np, const SplitMat& A, const SplitMat& B, SplitMat& C, const Epi& e,
                    bool sym, double* stats) {
     RET(prep_tiles(np, s));
-    auto& tl = tiles_[np];
+    const TcTiles& tl = tiles_[np].second;
     RET(cudaMemsetAsync(C.amax, 0, sizeof(unsigned), s));
     TcArgs a;
     a.nseg = e.nseg;
@@ -396,13 +406,12 @@ class EngineSplit : public Engine {
     a.sa = A.scale;
     a.sb = B.scale;
     a.err = err_;
-    const int n128 = tl.second.first, n256 = tl.second.second;
     RET(prof_begin(s));
     // large products: split the hi*hi sums over both accumulators (the tensor core truncates as it
     // accumulates, so a K-long sum's error grows with K)
     a.split_acc = (np >= kSplitAccMin) ? 1 : 0;
     a.chunk_kb = kChunkKb;
-    RET(gemm_tc(s, np, A.hi, A.lo, B.hi, B.lo, a, tl.first, tl.first + 2 * n128, n128, n256));
+    RET(gemm_tc(s, np, A.hi, A.lo, B.hi, B.lo, a, tl));
     // kind bits: 1 sym, 2 E, 4 E2, 8 E64, 16 E64 transposed, 32 FP64 output
     const int kind = (sym ? 1 : 0) | (e.E ? 2 : 0) | (e.E2 ? 4 : 0) | (e.E64 ? 8 : 0) | (e.e64_trans ? 16 : 0) |
                      (e.out64 ? 32 : 0);
@@ -597,7 +606,7 @@ class EngineSplit : public Engine {
   int bf16_;
   int probe_nseg_ = 3;
   int mu_nseg_ = 3;
-  std::unordered_map<int, std::pair<int*, std::pair<int, int>>> tiles_;
+  std::unordered_map<int, std::pair<int*, TcTiles>> tiles_;
 };
 
 // which value arrays a matrix keeps

@@ -104,11 +104,12 @@ __device__ __forceinline__ uint64_t smem_desc(const void* p) {
   return d;
 }
 
-// Instruction descriptor of kind::f16: D = F32, A/B = F16 (0) or BF16 (1), both K-major.
-__host__ __device__ constexpr uint32_t instr_desc(int bn, int ab_fmt) {
+// Instruction descriptor of kind::f16: D = F32, A/B = F16 (0) or BF16 (1), both K-major, M x N.
+__host__ __device__ constexpr uint32_t instr_desc_m(int m, int bn, int ab_fmt) {
   return (1u << 4) | ((uint32_t)ab_fmt << 7) | ((uint32_t)ab_fmt << 10) | ((uint32_t)(bn >> 3) << 17) |
-         ((uint32_t)(BM >> 4) << 24);
+         ((uint32_t)(m >> 4) << 24);
 }
+__host__ __device__ constexpr uint32_t instr_desc(int bn, int ab_fmt) { return instr_desc_m(BM, bn, ab_fmt); }
 
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                         uint32_t accumulate) {
@@ -867,6 +868,350 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
+// ---- two-SM products (cta_group::2) ----
+//
+// A cluster of two CTAs on two SMs computes a 256 x 256 output tile with tcgen05.mma.cta_group::2
+// (M = 256, N = 256, K = 16): CTA r of the pair holds rows 128 r .. 128 r + 127 of the A tile and
+// of the B tile in its own shared memory and rows 128 r .. of the accumulator in its own TMEM.
+// The tensor cores of both SMs read both CTAs' operands, so each SM stages half as many B bytes
+// per flop as the one-SM product: 32 KB per 64-wide K block instead of 48 KB, six ring stages
+// instead of four, a third less shared-memory traffic per flop.  The accumulator modes (single
+// products alternating accumulators, split products with chunked FP32 folds) are those of the
+// one-SM persistent kernel, run by both CTAs' epilogue warps on their own TMEM lanes.
+//
+// Roles.  Both CTAs: warp 0 lane 0 loads the CTA's A and B halves of each K block by TMA,
+// signalling the leader CTA's (rank 0) full barrier; warps 2-5 run the epilogue.  Leader only:
+// warp 1 lane 0 waits for both halves (full), issues the MMAs and commits to the empty, acc_full
+// barriers of both CTAs (multicast).  The epilogue warps of both CTAs release accumulators on the
+// leader's acc_free barriers (eight warp arrivals per phase, four of them remote).  TMEM is
+// allocated and freed collectively by warp 1 of both CTAs.  Cluster barriers after the barrier
+// set-up and before the TMEM release are reached by every thread of both CTAs; every other wait
+// is bounded.
+constexpr int PSTAGES = 6;
+constexpr int PB_BYTES = 128 * BK * 2;           // a CTA's half of the 256-row B tile
+constexpr int kPairGroupM = 8;                   // 256-row panels per raster group
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// the shared::cluster address of the same shared-memory word in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t map_to_rank(const void* p, uint32_t rank) {
+  uint32_t out;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(smem_u32(p)), "r"(rank));
+  return out;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+// TMA load into this CTA's shared memory that signals an mbarrier of either CTA of the pair
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, int x, int y, uint32_t bar_cluster) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar_cluster)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_f16_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                             uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// arrive on the same barrier in both CTAs of the pair once the MMAs issued so far complete
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"((unsigned short)3)
+      : "memory");
+}
+
+// arrive on this CTA's barrier once the pair MMAs issued so far complete
+__device__ __forceinline__ void mma_commit_pair_local(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool pair_tile_coords(const TcArgs& a, int id, int& tm, int& tn) {
+  const int tiles = a.n / 256;
+  if (a.tile_list) {
+    tm = a.tile_list[2 * id];
+    tn = a.tile_list[2 * id + 1];
+  } else {
+    const int per_group = kPairGroupM * tiles;
+    const int g = id / per_group, r = id % per_group;
+    const int first = g * kPairGroupM;
+    const int gm = min(tiles - first, kPairGroupM);
+    tm = first + r % gm;
+    tn = r / gm;
+  }
+  return tm >= 0 && tm < tiles && tn >= 0 && tn < tiles;
+}
+
+__global__ void __launch_bounds__(192, 1)
+    gemm_tc_pair_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                        const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
+                        const __grid_constant__ CUtensorMap mA2hi, const __grid_constant__ CUtensorMap mA2lo,
+                        const __grid_constant__ CUtensorMap mB2hi, const __grid_constant__ CUtensorMap mB2lo,
+                        TcArgs a, int ntiles) {
+  constexpr int BN = 256;
+  constexpr uint32_t TMEM_COLS = 2 * BN;
+  constexpr int STAGE_TILE = 32 * 33 * 4;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + PSTAGES * A_BYTES;
+  uint8_t* stage = sB + PSTAGES * PB_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(stage + 4 * 2 * STAGE_TILE);
+  uint64_t* empty = full + PSTAGES;
+  uint64_t* acc_full = empty + PSTAGES;    // [2]
+  uint64_t* acc_free = acc_full + 2;       // [2], used in the leader
+  uint64_t* drain = acc_full + 4;          // leader: completion of the last MMAs before teardown
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = (rank == 0);
+  const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+  if (warp == 0 && lane == 0) {
+    for (int s = 0; s < PSTAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&acc_full[0], 1);
+    mbar_init(&acc_full[1], 1);
+    mbar_init(&acc_free[0], 8);
+    mbar_init(&acc_free[1], 8);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  cluster_sync();   // both CTAs' barriers exist before any remote signal
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  const int nk = a.K / BK;
+  const int total = a.nseg * a.pairs * nk;
+  const bool chunked = a.nseg > 1;
+  const int H = a.pairs * nk;
+  const int Cn = total - H;
+  const int Lc = (chunked && a.chunk_kb > 0 && a.chunk_kb < H) ? a.chunk_kb : H;
+  const int nchunks = (H + Lc - 1) / Lc;
+  const int nfold = chunked ? max(1, nchunks - 1) : 0;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const uint32_t full_leader0 = map_to_rank(&full[0], 0);   // leader's full[0]; stages 8 bytes apart
+      uint32_t g = 0;
+      bool ok = true;
+      for (int id = pair; id < ntiles && ok && !*abort_flag; id += npairs) {
+        int tm, tn;
+        if (!pair_tile_coords(a, id, tm, tn)) {
+          atomicExch(a.err, 4);
+          *abort_flag = 1;
+          break;
+        }
+        const int arow = tm * 256 + (int)rank * 128, brow = tn * 256 + (int)rank * 128;
+        KWalk w;
+        kwalk_begin(w);
+        for (int kb = 0; kb < total; ++kb, ++g, kwalk_next(w, nk, Lc, Cn)) {
+          const int s = g % PSTAGES;
+          const uint32_t ph = (g / PSTAGES) & 1;
+          if (g >= PSTAGES && !mbar_wait(&empty[s], ph ^ 1)) {
+            atomicExch(a.err, 1);
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          if (leader) mbar_expect_tx(&full[s], 2 * (A_BYTES + PB_BYTES));   // both CTAs' halves
+          const int kk = w.kidx * BK;
+          const CUtensorMap* ma = (w.kind == 2) ? (w.pr ? &mA2lo : &mAlo) : (w.pr ? &mA2hi : &mAhi);
+          const CUtensorMap* mb = (w.kind == 1) ? (w.pr ? &mB2lo : &mBlo) : (w.pr ? &mB2hi : &mBhi);
+          const uint32_t bar = full_leader0 + 8u * (uint32_t)s;
+          tma_load_2d_pair(sA + s * A_BYTES, ma, kk, arow, bar);
+          tma_load_2d_pair(sB + s * PB_BYTES, mb, kk, brow, bar);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && leader) {
+      constexpr uint32_t idesc_f16 = instr_desc_m(256, BN, 0);
+      constexpr uint32_t idesc_bf16 = instr_desc_m(256, BN, 1);
+      const uint32_t idesc = a.bf16 ? idesc_bf16 : idesc_f16;
+      uint32_t g = 0;
+      int it = 0;
+      int uses0 = 0, uses1 = 0;
+      int par = 0;
+      bool issued = false;
+      for (int id = pair; id < ntiles && !*abort_flag; id += npairs, ++it, par ^= (nfold & 1) ^ 1) {
+        int tm, tn;
+        if (!pair_tile_coords(a, id, tm, tn)) break;
+        bool ok = true;
+        const int buf = it & 1;
+        int cur = 0;
+        int bnd = 2 * Lc;
+        KWalk w;
+        kwalk_begin(w);
+        for (int kb = 0; kb < total; ++kb, ++g, kwalk_next(w, nk, Lc, Cn)) {
+          int fresh = -1;
+          if (!chunked) {
+            if (kb == 0) fresh = buf;
+          } else if (w.phase == 0) {
+            if (w.h == 0) fresh = par;
+          } else if (w.phase == 1) {
+            if (w.c == 0) fresh = par ^ 1;
+          } else if (w.h == bnd) {
+            mma_commit_pair(&acc_full[0]);
+            fresh = ((bnd / Lc) & 1) ^ par;
+            bnd += Lc;
+          }
+          if (fresh >= 0) {
+            const int u = chunked ? (fresh ? uses1 : uses0) : (it >> 1);
+            if (u > 0) {
+              if (!mbar_wait(&acc_free[fresh], (uint32_t)((u - 1) & 1)) || *abort_flag) {
+                ok = false;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
+            if (chunked) {
+              if (fresh)
+                ++uses1;
+              else
+                ++uses0;
+            }
+            cur = fresh;
+          }
+          const int s = g % PSTAGES;
+          const uint32_t ph = (g / PSTAGES) & 1;
+          if (!mbar_wait(&full[s], ph)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t dcol = cur ? (uint32_t)BN : 0u;
+#pragma unroll
+          for (int j = 0; j < BK / 16; ++j) {
+            const uint64_t ad = smem_desc(sA + s * A_BYTES + j * 32);
+            const uint64_t bd = smem_desc(sB + s * PB_BYTES + j * 32);
+            mma_f16_pair(tmem + dcol, ad, bd, idesc, (fresh >= 0 && j == 0) ? 0u : 1u);
+          }
+          issued = true;
+          mma_commit_pair(&empty[s]);
+        }
+        if (!ok) {
+          atomicExch(a.err, 2);
+          *abort_flag = 1;
+          break;
+        }
+        mma_commit_pair(&acc_full[chunked ? 0 : buf]);
+      }
+      // no MMA may still write either CTA's TMEM when the pair frees it
+      if (issued) {
+        mma_commit_pair_local(drain);
+        if (!mbar_wait(drain, 0)) atomicExch(a.err, 5);
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    float(*tx)[33] = reinterpret_cast<float(*)[33]>(stage + q * 2 * STAGE_TILE);
+    float(*ty)[33] = reinterpret_cast<float(*)[33]>(stage + q * 2 * STAGE_TILE + STAGE_TILE);
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const float inv = a.alpha / (__ldg(a.sa) * __ldg(a.sb));
+    const uint32_t free_leader0 = map_to_rank(&acc_free[0], 0), free_leader1 = map_to_rank(&acc_free[1], 0);
+    int it = 0;
+    uint32_t ev = 0;
+    int par = 0;
+    for (int id = pair; id < ntiles && !*abort_flag; id += npairs, ++it, par ^= (nfold & 1) ^ 1) {
+      int tm, tn;
+      if (!pair_tile_coords(a, id, tm, tn)) break;
+      const int tm128 = 2 * tm + (int)rank;          // this CTA's 128-row panel
+      prefetch_sides<BN>(a, tm128, tn, (warp - 2) * 32 + lane);
+      int src;
+      bool ok = true;
+      if (!chunked) {
+        src = it & 1;
+        ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[src], (uint32_t)((it >> 1) & 1)));
+        if (ok) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      } else {
+        src = par;
+        for (int f = 1; f <= nfold && ok; ++f, ++ev) {
+          ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[0], ev & 1));
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const int dst = (f & 1) ^ par, from = dst ^ 1;
+          for (int ch = 0; ch < BN / 64; ++ch) {
+            uint32_t v[64], u[64];
+            tmem_ld64_nowait(tmem + lane_base + (uint32_t)(from * BN + ch * 64), v);
+            tmem_ld64_nowait(tmem + lane_base + (uint32_t)(dst * BN + ch * 64), u);
+            tmem_wait_ld64(v);
+            tmem_after_wait64(u);
+#pragma unroll
+            for (int i = 0; i < 64; ++i) v[i] = __float_as_uint(__uint_as_float(v[i]) + __uint_as_float(u[i]));
+            tmem_st64(tmem + lane_base + (uint32_t)(dst * BN + ch * 64), v);
+          }
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive_cluster(from ? free_leader1 : free_leader0);
+          src = dst;
+        }
+      }
+      if (!ok || *abort_flag) {
+        if (lane == 0) atomicExch(a.err, 3);
+        *abort_flag = 1;
+        break;
+      }
+      const int row0 = tm128 * BM + q * 32;
+      const int row = row0 + lane;
+      float vmax = 0.0f;
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        float v[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)(src * BN + ch * 32), v);
+        epilogue_chunk(a, v, row, row0, tn * BN + ch * 32, lane, tx, ty, inv, vmax);
+      }
+      for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+      if (lane == 0 && a.amax) atomicMax(a.amax, __float_as_uint(vmax));
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(src ? free_leader1 : free_leader0);
+    }
+  }
+
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  cluster_sync();   // the peer is done with this CTA's shared memory and TMEM
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
 // ---- host side: tensor maps ----
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -934,13 +1279,20 @@ int smem_bytes_persistent() {
   return STAGES * (A_BYTES + BN * BK * 2) + 4 * 2 * 32 * 33 * 4 + (2 * STAGES + 4) * 8 + 16 + 1024;
 }
 
-// 1: persistent CTAs (default); 0: one CTA per output tile (XLBOMD_GEMM=classic).
+int smem_bytes_pair() {
+  return PSTAGES * (A_BYTES + PB_BYTES) + 4 * 2 * 32 * 33 * 4 + (2 * PSTAGES + 5) * 8 + 16 + 1024;
+}
+
+// 2: two-SM products where n is a multiple of 256, else one-SM persistent CTAs (default);
+// 1: one-SM persistent CTAs (XLBOMD_GEMM=persistent); 0: one CTA per output tile
+// (XLBOMD_GEMM=classic).
 int tc_variant() {
   static int v = -1;
   static std::once_flag once;
   std::call_once(once, [] {
     const char* e = std::getenv("XLBOMD_GEMM");
-    v = (e && std::string(e) == "classic") ? 0 : 1;
+    const std::string x = e ? std::string(e) : std::string();
+    v = (x == "classic") ? 0 : (x == "persistent") ? 1 : 2;
   });
   return v;
 }
@@ -950,7 +1302,8 @@ int tc_variant() {
 constexpr int kMaxDevices = 64;
 struct DeviceState {
   int sms = 0;
-  bool smem_set[4] = {false, false, false, false};
+  int pair_clusters = 0;   // co-resident clusters of the two-SM product kernel
+  bool smem_set[5] = {false, false, false, false, false};
 };
 std::mutex g_dev_mu;
 DeviceState g_dev[kMaxDevices];
@@ -974,6 +1327,35 @@ int sm_count() {
     d.sms = n;
   }
   return d.sms;
+}
+
+// How many two-SM clusters of the pair kernel fit on the current device at once (its shared
+// memory allows one CTA per SM; pairs must sit on SM pairs of one GPC).
+int pair_clusters(int smem) {
+  const int dev = current_device();
+  {
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (g_dev[dev].pair_clusters > 0) return g_dev[dev].pair_clusters;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2, 1, 1);
+  cfg.blockDim = dim3(192, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, gemm_tc_pair_kernel, &cfg) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    n = sm_count() / 2;
+  }
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  g_dev[dev].pair_clusters = n;
+  return n;
 }
 
 // Raise kernel `slot`'s dynamic shared-memory limit to `bytes` on the current device (once per
@@ -1001,20 +1383,23 @@ void tc_forget_maps(const void* base) {
 }
 
 cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* Alo, const uint16_t* Bhi,
-                    const uint16_t* Blo, TcArgs args, const int* sym_tiles_128, const int* sym_tiles_256,
-                    int n_sym_128, int n_sym_256) {
+                    const uint16_t* Blo, TcArgs args, const TcTiles& tiles) {
   if (n % 128 != 0 || n <= 0) return cudaErrorInvalidValue;
+  if (args.pairs != 1 && args.pairs != 2) return cudaErrorInvalidValue;
   const bool wide = (n % 256 == 0);
+  const int variant = tc_variant();
+  const bool two_sm = (variant == 2) && wide && tiles.pair != nullptr;
+  // B boxes: a CTA's 128-row half of the 256-row tile (two-SM), else the tile's bn rows
   const int bn = wide ? 256 : 128;
+  const int bbox = two_sm ? 128 : bn;
   CUtensorMap mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo;
   if (!make_map(&mAhi, Ahi, n, BM, args.bf16) || !make_map(&mAlo, Alo ? Alo : Ahi, n, BM, args.bf16) ||
-      !make_map(&mBhi, Bhi, n, bn, args.bf16) || !make_map(&mBlo, Blo ? Blo : Bhi, n, bn, args.bf16))
+      !make_map(&mBhi, Bhi, n, bbox, args.bf16) || !make_map(&mBlo, Blo ? Blo : Bhi, n, bbox, args.bf16))
     return cudaErrorInvalidValue;
-  if (args.pairs != 1 && args.pairs != 2) return cudaErrorInvalidValue;
   if (args.pairs == 2) {
-    // the swapped pair: B in the A role (BM-row boxes), A in the B role (bn-row boxes)
+    // the swapped pair: B in the A role (BM-row boxes), A in the B role
     if (!make_map(&mA2hi, Bhi, n, BM, args.bf16) || !make_map(&mA2lo, Blo ? Blo : Bhi, n, BM, args.bf16) ||
-        !make_map(&mB2hi, Ahi, n, bn, args.bf16) || !make_map(&mB2lo, Alo ? Alo : Ahi, n, bn, args.bf16))
+        !make_map(&mB2hi, Ahi, n, bbox, args.bf16) || !make_map(&mB2lo, Alo ? Alo : Ahi, n, bbox, args.bf16))
       return cudaErrorInvalidValue;
   } else {
     mA2hi = mAhi;
@@ -1026,15 +1411,45 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
   args.K = n;
   if (args.split_acc && n / BK < 2) return cudaErrorInvalidValue;   // both accumulators get K blocks
   args.tiles_n = n / bn;
+  if (two_sm) {
+    int ntiles;
+    if (args.sym) {
+      args.tile_list = tiles.pair;
+      ntiles = tiles.npair;
+    } else {
+      args.tile_list = nullptr;
+      ntiles = (n / 256) * (n / 256);
+    }
+    const int sb = smem_bytes_pair();
+    const cudaError_t attr = ensure_smem(4, gemm_tc_pair_kernel, sb);
+    if (attr != cudaSuccess) return attr;
+    const int npairs = std::min(ntiles, pair_clusters(sb));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * npairs, 1, 1);
+    cfg.blockDim = dim3(192, 1, 1);
+    cfg.dynamicSmemBytes = sb;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, gemm_tc_pair_kernel, mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi,
+                                             mB2lo, args, ntiles);
+    note_launch();
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
   int nblocks;
   if (args.sym) {
-    args.tile_list = wide ? sym_tiles_256 : sym_tiles_128;
-    nblocks = wide ? n_sym_256 : n_sym_128;
+    args.tile_list = wide ? tiles.sym256 : tiles.sym128;
+    nblocks = wide ? tiles.n256 : tiles.n128;
   } else {
     args.tile_list = nullptr;
     nblocks = (n / BM) * (n / bn);
   }
-  if (tc_variant() == 1) {
+  if (variant >= 1) {
     const int grid = std::min(nblocks, sm_count());
     if (wide) {
       const int sb = smem_bytes_persistent<256>();
@@ -1064,6 +1479,23 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
     note_launch();
   }
   return cudaGetLastError();
+}
+
+// Tile list of symmetric two-SM products: the 256 x 256 tiles (tm, tn) with tn >= tm, in the
+// grouped raster of the dense products.
+std::vector<int> tc_sym_tiles_pair(int n) {
+  std::vector<int> t;
+  const int tiles = n / 256;
+  for (int first = 0; first < tiles; first += kPairGroupM) {
+    const int gm = std::min(tiles - first, kPairGroupM);
+    for (int tn = 0; tn < tiles; ++tn)
+      for (int tm = first; tm < first + gm; ++tm)
+        if (tn >= tm) {
+          t.push_back(tm);
+          t.push_back(tn);
+        }
+  }
+  return t;
 }
 
 // Tile lists of symmetric products: tiles (tm, tn) of BM x bn that reach the

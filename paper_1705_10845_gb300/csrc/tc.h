@@ -42,11 +42,24 @@ struct TcArgs {
   int* err = nullptr;             // set non-zero when a bounded wait gives up
 };
 
-// n x n product (n a multiple of 128); the symmetric tile lists come from tc_sym_tiles.
+// Device tile lists of the symmetric-output products of one size n (pairs of ints (tm, tn)):
+// 128 x 128 tiles, 128 x 256 tiles (n a multiple of 256) and 256 x 256 tiles of the two-SM
+// products (n a multiple of 256; null: two-SM products are not used for this size).
+struct TcTiles {
+  const int* sym128 = nullptr;
+  int n128 = 0;
+  const int* sym256 = nullptr;
+  int n256 = 0;
+  const int* pair = nullptr;
+  int npair = 0;
+};
+
+// n x n product (n a multiple of 128); the symmetric tile lists come from tc_sym_tiles and
+// tc_sym_tiles_pair.
 cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* Alo, const uint16_t* Bhi,
-                    const uint16_t* Blo, TcArgs args, const int* sym_tiles_128, const int* sym_tiles_256,
-                    int n_sym_128, int n_sym_256);
+                    const uint16_t* Blo, TcArgs args, const TcTiles& tiles);
 std::vector<int> tc_sym_tiles(int n, int bn);
+std::vector<int> tc_sym_tiles_pair(int n);
 void tc_forget_maps(const void* base);
 
 }  // namespace xl

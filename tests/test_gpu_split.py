@@ -183,34 +183,40 @@ def test_split_exact_kernel_against_oracle(X, prec, tol):
     assert err < tol
 
 
-def test_one_cta_per_tile_variant_matches_fp64(X):
-    # the one-CTA-per-tile product kernel (XLBOMD_GEMM=classic) stays checked
-    # next to the persistent default; a fresh process reads the variant once
+@pytest.mark.parametrize("variant", ["classic", "persistent"])
+def test_other_product_variants_match_fp64(X, variant):
+    # the one-CTA-per-tile product kernel (XLBOMD_GEMM=classic) and the one-SM persistent kernel
+    # at sizes that the two-SM kernel serves by default (XLBOMD_GEMM=persistent) stay checked
+    # next to the default; a fresh process reads the variant once
     import json
     import os
     import subprocess
     import sys
     code = ("import json, paper_1705_10845_gb300 as X; X.load(); "
-            "print(json.dumps([[X.binding.selftest_gemm(n, p, s) for n in (256, 384) "
+            "print(json.dumps([[X.binding.selftest_gemm(n, p, s) for n in (256, 384, 2048) "
             "for p in ('fp16x3', 'bf16x3') for s in (False, True)], "
-            "[X.binding.selftest_gemm(8192, 'fp16x3', s) for s in (False, True, 2)]]))")
+            "[X.binding.selftest_gemm(8192, 'fp16x3', s) for s in (False, True, 2)], "
+            "[X.binding.selftest_gemm(4096, 'fp16x3', s, single=True) for s in (False, True, 2)]]))")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     out = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True,
-                         env=dict(os.environ, XLBOMD_GEMM="classic"), timeout=300)
+                         env=dict(os.environ, XLBOMD_GEMM=variant), timeout=300)
     assert out.returncode == 0, out.stderr[-2000:]
-    res, large = json.loads(out.stdout.strip().splitlines()[-1])
+    res, large, single = json.loads(out.stdout.strip().splitlines()[-1])
     k = 0
-    for n in (256, 384):
+    for n in (256, 384, 2048):
         for bound in (1e-6, 2e-5):
             for _sym in (False, True):
                 err, flag, ms = res[k]
                 k += 1
                 assert flag == 0 and err < bound * n, (n, err)
-    # n = 8192: the hi*hi sums split over both accumulators (dense, symmetric, pair), with the
-    # bounds of the persistent kernel's tests
+    # n = 8192 split products (dense, symmetric, pair) with the bounds of the default kernel's tests
     for (err, flag, ms), bound in zip(large, (1e-6, 1e-6, 2e-6)):
-        print("classic fp16x3 8192", err, ms)
+        print(variant, "fp16x3 8192", err, ms)
         assert flag == 0 and err < bound * 8192, (err, ms)
+    # single products (one 16-bit product) at n = 4096
+    for (err, flag, ms), f in zip(single, (1.0, 1.0, 2.0)):
+        bound = 8.0 * 2.0 ** -11 * np.sqrt(2.0 * 4096 / 27.0) * f
+        assert flag == 0 and err < bound, (err, bound)
 
 
 @pytest.mark.parametrize("prec", ["fp16x3", "bf16x3"])
