@@ -558,43 +558,38 @@ __global__ void __launch_bounds__(192, 1)
 //    with one barrier pair per accumulator no barrier can run two phases ahead of its waiter.
 //  - split products (three segments): the tensor core truncates as it accumulates, so the error
 //    of a K-long sum grows with K.  The hi*hi sum is therefore accumulated in chunks of
-//    chunk_kb K blocks, alternately in the two accumulators, and the epilogue warps fold each
-//    finished chunk into the running sum with round-to-nearest FP32 adds (tcgen05.ld + st).
-//    Steps of a tile with c chunks, accumulators named relative to the tile's parity p: step 0
-//    = chunk 0 into accumulator p; step 1 = the two correction segments into accumulator p ^ 1
-//    while it is small, then chunk 1 on top of them; step s >= 2 = chunk s into accumulator
-//    (s % 2) ^ p.  After step f (f = 1 .. F, F = max(1, c - 1)) the epilogue folds: accumulator
-//    (f % 2) ^ p += the other one, which it releases for step f + 1; the last fold leaves the sum
-//    in accumulator (F % 2) ^ p, which the epilogue writes out and releases.  The next tile's
-//    parity makes its step 0 use the accumulator the last fold released, so that step 0
-//    overlaps the write-out.  acc_full[0] carries one phase per fold; acc_free[b] one phase per
-//    release of accumulator b, and the MMA thread waits for release u - 1 of b before its u-th
-//    fresh write to b.  Each phase needs the previous one consumed, so no barrier runs two
-//    phases ahead.
+//    chunk_kb K blocks, and the epilogue warps fold each finished chunk into the tile's sum with
+//    round-to-nearest FP32 adds (tcgen05.ld + st).  A tile with parity p first accumulates the
+//    two correction segments into accumulator p (while it is small), then each hi*hi chunk into
+//    accumulator p ^ 1; after each chunk the epilogue folds accumulator p ^ 1 into accumulator p
+//    and releases it for the next chunk, and after the last fold writes out accumulator p and
+//    releases it.  Tiles alternate p, so a tile's long correction segments run while the
+//    previous tile is written out from the other accumulator.  acc_full[0] carries one phase per
+//    fold; acc_free[b] one phase per release of accumulator b, and the MMA thread waits for
+//    release u - 1 of b before its u-th fresh write to b.  Each phase needs the previous one
+//    consumed, so no barrier runs two phases ahead.
 // Barriers: full/empty (operand ring), acc_full[2] (MMA -> epilogue), acc_free[2] (epilogue ->
 // MMA, four warp arrivals per phase).  Every wait is bounded; a role that gives up records an
 // error and raises a shared abort flag that ends the other roles' loops.
 
-// K-block order of one tile (the producer and the MMA thread walk it alike): the first hi*hi
-// chunk (K blocks 0 .. L0 - 1 of the hi*hi sequence: pair 0's K blocks, then pair 1's), then the
-// Cn correction K blocks (hi*lo, lo*hi of pair 0, then of pair 1), then the rest of the hi*hi
-// sequence.  Counters only, no divisions.
+// K-block order of one tile (the producer and the MMA thread walk it alike): the Cn correction
+// K blocks first (hi*lo, lo*hi of pair 0, then of pair 1), then the hi*hi sequence (pair 0's K
+// blocks, then pair 1's).  Counters only, no divisions.
 struct KWalk {
-  int phase;           // 0: first hi*hi chunk, 1: corrections, 2: remaining hi*hi
+  int phase;           // 0: corrections, 1: hi*hi
   int pr, kind, kidx;  // current K block: operand pair, split part (0 hi*hi, 1 hi*lo, 2 lo*hi), index
   int h, c;            // hi*hi and correction K blocks issued before the current one
-  int sp, sk;          // hi*hi position to resume at after the corrections
 };
 
-__device__ __forceinline__ void kwalk_begin(KWalk& w) {
-  w.phase = 0;
-  w.pr = w.kind = w.kidx = 0;
+__device__ __forceinline__ void kwalk_begin(KWalk& w, int Cn) {
+  w.phase = Cn > 0 ? 0 : 1;
+  w.pr = w.kidx = 0;
+  w.kind = Cn > 0 ? 1 : 0;
   w.h = w.c = 0;
-  w.sp = w.sk = 0;
 }
 
-__device__ __forceinline__ void kwalk_next(KWalk& w, int nk, int L0, int Cn) {
-  if (w.phase == 1) {
+__device__ __forceinline__ void kwalk_next(KWalk& w, int nk, int Cn) {
+  if (w.phase == 0) {
     ++w.c;
     if (++w.kidx == nk) {
       w.kidx = 0;
@@ -606,10 +601,8 @@ __device__ __forceinline__ void kwalk_next(KWalk& w, int nk, int L0, int Cn) {
       }
     }
     if (w.c == Cn) {
-      w.phase = 2;
-      w.pr = w.sp;
-      w.kind = 0;
-      w.kidx = w.sk;
+      w.phase = 1;
+      w.pr = w.kind = w.kidx = 0;
     }
     return;
   }
@@ -617,17 +610,6 @@ __device__ __forceinline__ void kwalk_next(KWalk& w, int nk, int L0, int Cn) {
   if (++w.kidx == nk) {
     w.kidx = 0;
     ++w.pr;
-  }
-  if (w.phase == 0 && w.h == L0) {
-    w.phase = 2;
-    if (Cn > 0) {
-      w.sp = w.pr;
-      w.sk = w.kidx;
-      w.phase = 1;
-      w.pr = 0;
-      w.kind = 1;
-      w.kidx = 0;
-    }
   }
 }
 
@@ -685,7 +667,7 @@ __global__ void __launch_bounds__(192, 1)
   const int Cn = total - H;                        // correction K blocks
   const int Lc = (chunked && a.chunk_kb > 0 && a.chunk_kb < H) ? a.chunk_kb : H;   // chunk length
   const int nchunks = (H + Lc - 1) / Lc;
-  const int nfold = chunked ? max(1, nchunks - 1) : 0;   // folds per tile
+  const int nfold = chunked ? nchunks : 0;   // folds per tile
 
   if (warp == 0) {
     if (lane == 0) {
@@ -699,8 +681,8 @@ __global__ void __launch_bounds__(192, 1)
           break;
         }
         KWalk w;
-        kwalk_begin(w);
-        for (int kb = 0; kb < total; ++kb, ++g, kwalk_next(w, nk, Lc, Cn)) {
+        kwalk_begin(w, Cn);
+        for (int kb = 0; kb < total; ++kb, ++g, kwalk_next(w, nk, Cn)) {
           const int s = g % STAGES;
           const uint32_t ph = (g / STAGES) & 1;
           if (g >= STAGES && !mbar_wait(&empty[s], ph ^ 1)) {
@@ -727,27 +709,25 @@ __global__ void __launch_bounds__(192, 1)
       int it = 0;
       int uses0 = 0, uses1 = 0;      // fresh writes of each accumulator so far (split products)
       int par = 0;                   // split products: accumulator parity p of this tile
-      for (int id = blockIdx.x; id < ntiles && !*abort_flag; id += gridDim.x, ++it, par ^= (nfold & 1) ^ 1) {
+      for (int id = blockIdx.x; id < ntiles && !*abort_flag; id += gridDim.x, ++it, par ^= 1) {
         int tm, tn;
         if (!tile_coords(a, id, tm, tn)) break;
         bool ok = true;
         const int buf = it & 1;      // single products: accumulator of this tile
         int cur = 0;                 // accumulator of the current step
-        int bnd = 2 * Lc;            // first hi*hi K block of the next step s >= 2
+        int bnd = 0;                 // first hi*hi K block of the next chunk
         KWalk w;
-        kwalk_begin(w);
-        for (int kb = 0; kb < total; ++kb, ++g, kwalk_next(w, nk, Lc, Cn)) {
+        kwalk_begin(w, Cn);
+        for (int kb = 0; kb < total; ++kb, ++g, kwalk_next(w, nk, Cn)) {
           // does this K block start a step, and into which accumulator?
           int fresh = -1;            // accumulator written fresh from this K block, or -1
           if (!chunked) {
             if (kb == 0) fresh = buf;
           } else if (w.phase == 0) {
-            if (w.h == 0) fresh = par;
-          } else if (w.phase == 1) {
-            if (w.c == 0) fresh = par ^ 1;
+            if (w.c == 0) fresh = par;                     // corrections: the tile's sum accumulator
           } else if (w.h == bnd) {
-            mma_commit(&acc_full[0]);                    // the previous step is complete: fold it
-            fresh = ((bnd / Lc) & 1) ^ par;
+            if (bnd > 0) mma_commit(&acc_full[0]);                    // the previous chunk is complete: fold it
+            fresh = par ^ 1;                               // next hi*hi chunk
             bnd += Lc;
           }
           if (fresh >= 0) {
@@ -802,7 +782,7 @@ __global__ void __launch_bounds__(192, 1)
     int it = 0;
     uint32_t ev = 0;                 // acc_full[0] phases consumed (split products)
     int par = 0;                     // split products: accumulator parity p of this tile
-    for (int id = blockIdx.x; id < ntiles && !*abort_flag; id += gridDim.x, ++it, par ^= (nfold & 1) ^ 1) {
+    for (int id = blockIdx.x; id < ntiles && !*abort_flag; id += gridDim.x, ++it, par ^= 1) {
       int tm, tn;
       if (!tile_coords(a, id, tm, tn)) break;
       prefetch_sides<BN>(a, tm, tn, (warp - 2) * 32 + lane);
@@ -819,7 +799,7 @@ __global__ void __launch_bounds__(192, 1)
           ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[0], ev & 1));
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const int dst = (f & 1) ^ par, from = dst ^ 1;
+          const int dst = par, from = par ^ 1;
           // 64 columns at a time: both loads in flight before one wait
           for (int ch = 0; ch < BN / 64; ++ch) {
             uint32_t v[64], u[64];
@@ -1022,7 +1002,7 @@ __global__ void __launch_bounds__(192, 1)
   const int Cn = total - H;
   const int Lc = (chunked && a.chunk_kb > 0 && a.chunk_kb < H) ? a.chunk_kb : H;
   const int nchunks = (H + Lc - 1) / Lc;
-  const int nfold = chunked ? max(1, nchunks - 1) : 0;
+  const int nfold = chunked ? nchunks : 0;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -1038,8 +1018,8 @@ __global__ void __launch_bounds__(192, 1)
         }
         const int arow = tm * 256 + (int)rank * 128, brow = tn * 256 + (int)rank * 128;
         KWalk w;
-        kwalk_begin(w);
-        for (int kb = 0; kb < total; ++kb, ++g, kwalk_next(w, nk, Lc, Cn)) {
+        kwalk_begin(w, Cn);
+        for (int kb = 0; kb < total; ++kb, ++g, kwalk_next(w, nk, Cn)) {
           const int s = g % PSTAGES;
           const uint32_t ph = (g / PSTAGES) & 1;
           if (g >= PSTAGES && !mbar_wait(&empty[s], ph ^ 1)) {
@@ -1068,26 +1048,24 @@ __global__ void __launch_bounds__(192, 1)
       int uses0 = 0, uses1 = 0;
       int par = 0;
       bool issued = false;
-      for (int id = pair; id < ntiles && !*abort_flag; id += npairs, ++it, par ^= (nfold & 1) ^ 1) {
+      for (int id = pair; id < ntiles && !*abort_flag; id += npairs, ++it, par ^= 1) {
         int tm, tn;
         if (!pair_tile_coords(a, id, tm, tn)) break;
         bool ok = true;
         const int buf = it & 1;
         int cur = 0;
-        int bnd = 2 * Lc;
+        int bnd = 0;
         KWalk w;
-        kwalk_begin(w);
-        for (int kb = 0; kb < total; ++kb, ++g, kwalk_next(w, nk, Lc, Cn)) {
+        kwalk_begin(w, Cn);
+        for (int kb = 0; kb < total; ++kb, ++g, kwalk_next(w, nk, Cn)) {
           int fresh = -1;
           if (!chunked) {
             if (kb == 0) fresh = buf;
           } else if (w.phase == 0) {
-            if (w.h == 0) fresh = par;
-          } else if (w.phase == 1) {
-            if (w.c == 0) fresh = par ^ 1;
+            if (w.c == 0) fresh = par;                     // corrections: the tile's sum accumulator
           } else if (w.h == bnd) {
-            mma_commit_pair(&acc_full[0]);
-            fresh = ((bnd / Lc) & 1) ^ par;
+            if (bnd > 0) mma_commit_pair(&acc_full[0]);
+            fresh = par ^ 1;                               // next hi*hi chunk
             bnd += Lc;
           }
           if (fresh >= 0) {
@@ -1147,7 +1125,7 @@ __global__ void __launch_bounds__(192, 1)
     int it = 0;
     uint32_t ev = 0;
     int par = 0;
-    for (int id = pair; id < ntiles && !*abort_flag; id += npairs, ++it, par ^= (nfold & 1) ^ 1) {
+    for (int id = pair; id < ntiles && !*abort_flag; id += npairs, ++it, par ^= 1) {
       int tm, tn;
       if (!pair_tile_coords(a, id, tm, tn)) break;
       const int tm128 = 2 * tm + (int)rank;          // this CTA's 128-row panel
@@ -1164,7 +1142,7 @@ __global__ void __launch_bounds__(192, 1)
           ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[0], ev & 1));
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const int dst = (f & 1) ^ par, from = dst ^ 1;
+          const int dst = par, from = par ^ 1;
           for (int ch = 0; ch < BN / 64; ++ch) {
             uint32_t v[64], u[64];
             tmem_ld64_nowait(tmem + lane_base + (uint32_t)(from * BN + ch * 64), v);
@@ -1283,8 +1261,8 @@ int smem_bytes_pair() {
   return PSTAGES * (A_BYTES + PB_BYTES) + 4 * 2 * 32 * 33 * 4 + (2 * PSTAGES + 5) * 8 + 16 + 1024;
 }
 
-// 2: two-SM products where n is a multiple of 256, else one-SM persistent CTAs (default);
-// 1: one-SM persistent CTAs (XLBOMD_GEMM=persistent); 0: one CTA per output tile
+// 1: one-SM persistent CTAs (default); 2: two-SM products where n is a multiple of 256
+// (XLBOMD_GEMM=pair), else one-SM persistent CTAs; 0: one CTA per output tile
 // (XLBOMD_GEMM=classic).
 int tc_variant() {
   static int v = -1;
@@ -1292,7 +1270,7 @@ int tc_variant() {
   std::call_once(once, [] {
     const char* e = std::getenv("XLBOMD_GEMM");
     const std::string x = e ? std::string(e) : std::string();
-    v = (x == "classic") ? 0 : (x == "persistent") ? 1 : 2;
+    v = (x == "classic") ? 0 : (x == "pair") ? 2 : 1;
   });
   return v;
 }
@@ -1424,6 +1402,10 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
     const cudaError_t attr = ensure_smem(4, gemm_tc_pair_kernel, sb);
     if (attr != cudaSuccess) return attr;
     const int npairs = std::min(ntiles, pair_clusters(sb));
+    if (const char* dbg = std::getenv("XLBOMD_DEBUG"))
+      if (dbg[0] && dbg[0] != '0')
+        std::fprintf(stderr, "[xlbomd] two-SM product n %d: %d tiles on %d CTA pairs (%d co-resident)\n", n, ntiles,
+                     npairs, pair_clusters(sb));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * npairs, 1, 1);
     cfg.blockDim = dim3(192, 1, 1);

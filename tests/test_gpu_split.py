@@ -183,11 +183,11 @@ def test_split_exact_kernel_against_oracle(X, prec, tol):
     assert err < tol
 
 
-@pytest.mark.parametrize("variant", ["classic", "persistent"])
+@pytest.mark.parametrize("variant", ["classic", "pair"])
 def test_other_product_variants_match_fp64(X, variant):
-    # the one-CTA-per-tile product kernel (XLBOMD_GEMM=classic) and the one-SM persistent kernel
-    # at sizes that the two-SM kernel serves by default (XLBOMD_GEMM=persistent) stay checked
-    # next to the default; a fresh process reads the variant once
+    # the one-CTA-per-tile product kernel (XLBOMD_GEMM=classic) and the two-SM (cta_group::2)
+    # kernel (XLBOMD_GEMM=pair, sizes that are multiples of 256) stay checked next to the default
+    # one-SM persistent kernel; a fresh process reads the variant once
     import json
     import os
     import subprocess
