@@ -177,8 +177,9 @@ def test_trajectory_matches_oracle(X):
             assert E[0] == pytest.approx(ev.Omega, rel=1e-8), k
 
 
-@pytest.mark.parametrize("prec,tol_q", [("fp64", 1e-9), ("fp16x3", 1e-5), ("bf16x3", 1e-4)])
+@pytest.mark.parametrize("prec,tol_q", [("fp64", 1e-9), ("fp16x3", 1e-5), ("bf16x3", 3e-5)])
 def test_mu_search_through_flat_occupation(X, prec, tol_q):
+    # (BF16x3 is held to its measured level, 3e-5 e, outside the 1e-5 e bound of FP16x3)
     # 33 atoms at n = 0, Te = 1000 K, 12 squarings: from the first guess (the
     # middle of the Gershgorin interval) the safeguarded Newton search bisects
     # to a mu above every level, where Tr D = N and dTr D/dmu = 0; it must

@@ -92,8 +92,12 @@ def test_split_density_against_oracle(X, prec, case, mu_prec):
         ctx.energy(0)
         q, F, Kr = ctx.get(0, X.Q), ctx.get(0, X.F), ctx.get(0, X.KR)
         E = ctx.get(0, X.ENERGY)
-    tol_q = 1e-5 if prec == "fp16x3" else 1e-4
-    tol_f = 1e-4 if prec == "fp16x3" else 1e-3
+    # FP16x3 meets the mixed-precision bounds (1e-5 e, 1e-4 eV/A).  BF16x3 does not: its hi/lo
+    # pair keeps 16 significant bits against FP16's 22, and its charges measure 1.1-1.4e-5 e here
+    # (2-3e-5 e at 1536-2048 atoms), so it is held to its own measured level (3e-5 e) and is not
+    # used by the bench, batch or serving workloads
+    tol_q = 1e-5 if prec == "fp16x3" else 3e-5
+    tol_f = 1e-4
     print(prec, case, "mu_prec", mu_prec, "dq", np.abs(q - ref.q).max(), "dF", np.abs(F - ref.F).max(), "dKr",
           np.abs(Kr - ref.Kr).max())
     assert np.max(np.abs(q - ref.q)) < tol_q
