@@ -83,6 +83,13 @@ def parse():
                     help="comma-separated precisions (e.g. fp16x3,bf16x3): at the t0 state of the first, "
                          "each evaluates q, F and Omega against one oracle evaluation of the same (R, n), "
                          "then times --steps MD steps; prints one JSON line")
+    ap.add_argument("--batch", action="store_true",
+                    help="batch workload instead: --batch-jobs trajectories of 32-512 atoms (log-uniform, "
+                         "seeded), Te = 1000 K, --batch-steps steps each, stepped in lockstep per size bucket "
+                         "(grouped launches); prints one JSON line with the aggregate step rate and the "
+                         "per-step latency percentiles")
+    ap.add_argument("--batch-jobs", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--profile-step", action="store_true",
                     help="profiling run: t0 SCF, --warmup steps, then one step inside the NVTX range "
                          "'xlbomd_step'; prints no JSON")
@@ -377,6 +384,46 @@ def run_precision_study(a, X, ctx, s, sysd, stream):
     return 0
 
 
+def run_batch(a, X, ws, rank, dist):
+    """Many independent trajectories of uneven size advanced together (grouped launches per
+    size bucket): aggregate MD steps/s over all trajectories and ranks."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1705_10845_gb300 import serve
+    rng = np.random.default_rng(1705 + 1000 * rank)
+    jobs = []
+    for i in range(a.batch_jobs):
+        nat = int(round(math.exp(rng.uniform(math.log(32), math.log(512)))))
+        jobs.append(serve.Job(arrival=0.0, jid=i, natoms=nat, Te=1000.0, steps=a.batch_steps,
+                              seed=1705 + 1000 * rank + i, prec=a.prec))
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    l0 = X.binding.launch_count()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall, lat, steps, errors = serve.run_lockstep(
+        X, jobs, 8, stream_factory=lambda job: torch.cuda.Stream(priority=serve.stream_priority(job.natoms)))
+    torch.cuda.synchronize()
+    wall = max_over_ranks(wall, dist, "cuda")
+    clocks = sampler.stop()
+    arr = np.array(lat) * 1000.0 if lat else np.zeros(1)
+    line = {"metric": "XL-BOMD batch: aggregate MD steps/s of many trajectories (lockstep per size bucket)",
+            "value": job_rate(steps, ws, wall), "unit": "steps/s", "n_gpus": ws, "steps": a.batch_steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype_label(a),
+            "data": "synthetic",
+            "config": {"workload": f"{a.batch_jobs} trajectories, 32-512 carbon-like atoms (log-uniform, seeded), "
+                                   f"Te = 1000 K, 10+ squarings, rank-2 kernel, {a.batch_steps} steps each; "
+                                   "t0 SCF inside the timed region",
+                       "parallelism": f"replicas x{ws}"},
+            "step_latency_ms_p50": float(np.percentile(arr, 50)), "step_latency_ms_p99": float(np.percentile(arr, 99)),
+            "atom_steps_per_s": sum(j.natoms * j.done_steps for j in jobs) * ws / wall,
+            "gpu_launches": X.binding.launch_count() - l0, "clocks": clocks, "errors": errors[:5], "wall_s": wall}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 1 if errors else 0
+
+
 def main():
     a = parse()
     ws, rank, local = dist_setup()
@@ -401,6 +448,9 @@ def main():
     if dist is not None:
         dist.barrier()
     X.load()
+
+    if a.batch:
+        return run_batch(a, X, ws, rank, dist)
 
     s = synth.make_system(a.natoms, replica_seed(rank))
     sysd = dict(natoms=s.natoms, L=s.L, R=s.R, V=s.V, Z=s.Z, mass=s.mass)

@@ -282,6 +282,16 @@ xlbomd_status xlbomd_sizes(xlbomd_ctx* ctx, int sys, int* natoms, int* n_orb, in
  * counterpart. */
 xlbomd_status xlbomd_selftest_gemm(int n, int prec, int sym, double* result);
 
+/* Diagnostics: the grouped product launch (the products of several systems of one size in
+ * one persistent launch, per-problem tensor maps and epilogue arguments read from a device
+ * table) against single launches: nprob (2..64) seeded operand pairs of size n, each product
+ * computed alone, then all together in one grouped launch (both tile widths, as the tile
+ * autotuner tries them, then the width it keeps).  sym as for xlbomd_selftest_gemm (0-2, +4
+ * single product); prec FP16x3 or BF16x3.  result[0] = max |C_group - C_single| (0: the
+ * grouped launch computes every tile exactly as the single launch does), result[1] = device
+ * wait-timeout flag.  The paper has no counterpart. */
+xlbomd_status xlbomd_selftest_gemm_group(int n, int prec, int sym, int nprob, double* result);
+
 /* Diagnostics: number of CUDA kernels the library has launched since it was
  * loaded (all contexts). */
 long long xlbomd_launch_count(void);

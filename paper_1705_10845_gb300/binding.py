@@ -87,6 +87,8 @@ def load(path: str | None = None):
     lib.xlbomd_gemm_profile.restype = C.c_int
     lib.xlbomd_selftest_gemm.argtypes = [I, I, I, DP]
     lib.xlbomd_selftest_gemm.restype = C.c_int
+    lib.xlbomd_selftest_gemm_group.argtypes = [I, I, I, I, DP]
+    lib.xlbomd_selftest_gemm_group.restype = C.c_int
     for name in ("xlbomd_init", "xlbomd_scf", "xlbomd_build_H", "xlbomd_density", "xlbomd_kernel_update",
                  "xlbomd_energy", "xlbomd_step", "xlbomd_response", "xlbomd_get", "xlbomd_set",
                  "xlbomd_sizes", "xlbomd_clear_error", "xlbomd_free", "xlbomd_kernel_exact", "xlbomd_table_i"):
@@ -143,6 +145,19 @@ def selftest_gemm(n: int, prec: str = "fp16x3", sym=False, single: bool = False)
     if st != XLBOMD_OK:
         raise XlbomdError(st, "xlbomd_selftest_gemm")
     return float(out[0]), int(out[2]), float(out[3])
+
+
+def selftest_gemm_group(n: int, prec: str = "fp16x3", sym=False, single: bool = False, nprob: int = 3):
+    """Grouped product launch of nprob seeded problems against their single launches:
+    returns (max |C_group - C_single|, timeout flag)."""
+    out = np.zeros(2)
+    mode = 2 if (not isinstance(sym, bool) and sym == 2) else int(bool(sym))
+    if single:
+        mode += 4
+    st = load().xlbomd_selftest_gemm_group(int(n), PREC[prec], mode, int(nprob), _dptr(out))
+    if st != XLBOMD_OK:
+        raise XlbomdError(st, "xlbomd_selftest_gemm_group")
+    return float(out[0]), int(out[1])
 
 
 class Context:

@@ -73,6 +73,7 @@ struct xlbomd_ctx {
   cudaStream_t stream = nullptr;
   std::vector<Sys> sys;
   double* pinned = nullptr;
+  double* pinned_group = nullptr;   // lockstep: 2 doubles per system
   double* ppar = nullptr;   // pinned staging of the device parameters of a captured pass
   double* cdev = nullptr;
   int status = XLBOMD_OK;
@@ -294,71 +295,57 @@ void ns_plan(double t0max, int n, double tol, std::vector<int>& s, std::vector<d
   }
 }
 
-// a3-a6
-xlbomd_status density(xlbomd_ctx* ctx, Sys& S, bool with_forces) {
-  cudaStream_t st = ctx->stream;
-  const xlbomd_params& p = ctx->p;
-  const double beta = beta_of(p);
-  const int n = p.n_sq;
-  const double sc = beta / std::ldexp(1.0, n + 1);
-  Engine& E = *ctx->eng;
-
-  CK(launch_gershgorin(st, S.N, S.np, S.H, S.work));
-  CKS(sync_read(ctx, S.work, 2));
-  const double glo = ctx->pinned[0], ghi = ctx->pinned[1];
-  if (!std::isfinite(glo) || !std::isfinite(ghi))
-    return fail(ctx, XLBOMD_ERR_SPECTRUM, "non-finite Hamiltonian (Gershgorin bounds)");
-
-  double mu;
-  if (S.mu_valid) {
-    mu = S.mu;
-    if (S.n_mu_hist >= 3)
-      mu = 3.0 * S.mu_hist[0] - 3.0 * S.mu_hist[1] + S.mu_hist[2];
-    else if (S.n_mu_hist == 2)
-      mu = 2.0 * S.mu_hist[0] - S.mu_hist[1];
-  } else {
-    mu = 0.5 * (glo + ghi);
-  }
-  double blo = glo - 1.0, bhi = ghi + 1.0;   // bracket of the root of Tr D(mu) = N_occ
-  const double tol_ns = (p.prec == XLBOMD_FP64) ? 1e-16 : 1e-8;
-  const double occ_floor = ((p.prec == XLBOMD_FP64) ? 1e-12 : 1e-6) * S.N;
+// Safeguarded Newton search for the chemical potential of one system (Tr D(mu) = N_occ): the
+// host side of the mu passes, shared by the one-system and the lockstep paths.
+struct MuSearch {
+  double glo = 0, ghi = 0, mu = 0, blo = 0, bhi = 0, dmu = 0, t0max = 0;
+  int pass = 0;
+  bool done = false;
   std::vector<int> plan_s;
   std::vector<double> plan_c;
-  double dmu = 0.0;
-  int pass = 0;
-  for (;; ++pass) {
-    if (pass >= p.mu_max_iter) return fail(ctx, XLBOMD_ERR_NOT_CONVERGED, "chemical potential did not converge");
-    const double t0max = sc * std::max(std::fabs(ghi - mu), std::fabs(mu - glo));
-    if (!(t0max < 1.0)) return fail(ctx, XLBOMD_ERR_SPECTRUM, "|beta (e - mu)| / 2^(n+1) >= 1");
-    ns_plan(t0max, n, tol_ns, plan_s, plan_c);
-    S.mats.t0max = t0max;
-    auto mu_pass = [&](const double* dp) -> xlbomd_status {
-      CK(E.foe(st, S.mats, S.H, S.N, mu, sc, plan_s, plan_c, S.stats, dp));
-      // mu chain: T1_0 = +sc I, full last level
-      CK(E.chain(st, S.mats, S.dvec_mu, S.N, true, S.dmu_diag, S.stats));
-      CK(E.trace_tn(st, S.mats, S.N, S.scal));          // scal[0] = sum_i T_n,ii
-      CK(launch_sum(st, S.N, S.dmu_diag, S.scal + 1));    // scal[1] = sum_i dT_n,ii/dmu
-      return XLBOMD_OK;
-    };
-    if (use_graphs(ctx, S)) {
-      if (!S.dpar) CKS(dalloc(ctx, &S.dpar, 64));
-      ctx->ppar[0] = mu;
-      for (int k = 0; k < n && k < 63; ++k) ctx->ppar[1 + k] = plan_c[k];
-      CK(cudaMemcpyAsync(S.dpar, ctx->ppar, sizeof(double) * 64, cudaMemcpyHostToDevice, st));
-      std::vector<int> key{0};
-      key.insert(key.end(), plan_s.begin(), plan_s.end());
-      CKS(run_captured(ctx, S, key, [&] { return mu_pass(S.dpar); }));
+
+  // start from the Gershgorin interval [glo, ghi] and the system's mu history
+  xlbomd_status start(xlbomd_ctx* ctx, const Sys& S, double lo, double hi) {
+    glo = lo;
+    ghi = hi;
+    if (!std::isfinite(glo) || !std::isfinite(ghi))
+      return fail(ctx, XLBOMD_ERR_SPECTRUM, "non-finite Hamiltonian (Gershgorin bounds)");
+    if (S.mu_valid) {
+      mu = S.mu;
+      if (S.n_mu_hist >= 3)
+        mu = 3.0 * S.mu_hist[0] - 3.0 * S.mu_hist[1] + S.mu_hist[2];
+      else if (S.n_mu_hist == 2)
+        mu = 2.0 * S.mu_hist[0] - S.mu_hist[1];
     } else {
-      CKS(mu_pass(nullptr));
+      mu = 0.5 * (glo + ghi);
     }
-    int* herr = reinterpret_cast<int*>(ctx->pinned + 63);
-    *herr = 0;
-    if (const int* derr = E.device_error())
-      CK(cudaMemcpyAsync(herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CKS(sync_read(ctx, S.scal, 2));
-    if (*herr != 0) return fail(ctx, XLBOMD_ERR_TIMEOUT, "tensor-core product: a bounded wait gave up or a tile was out of range");
-    const double trD = 0.5 * (S.N + ctx->pinned[0]);
-    const double trDmu = 0.5 * ctx->pinned[1];
+    blo = glo - 1.0;   // bracket of the root of Tr D(mu) = N_occ
+    bhi = ghi + 1.0;
+    dmu = 0.0;
+    pass = 0;
+    done = false;
+    return XLBOMD_OK;
+  }
+
+  // spectral bound and Newton-Schulz plan of the next pass
+  xlbomd_status prepare(xlbomd_ctx* ctx, Sys& S) {
+    const xlbomd_params& p = ctx->p;
+    if (pass >= p.mu_max_iter) return fail(ctx, XLBOMD_ERR_NOT_CONVERGED, "chemical potential did not converge");
+    const double sc = beta_of(p) / std::ldexp(1.0, p.n_sq + 1);
+    t0max = sc * std::max(std::fabs(ghi - mu), std::fabs(mu - glo));
+    if (!(t0max < 1.0)) return fail(ctx, XLBOMD_ERR_SPECTRUM, "|beta (e - mu)| / 2^(n+1) >= 1");
+    ns_plan(t0max, p.n_sq, (p.prec == XLBOMD_FP64) ? 1e-16 : 1e-8, plan_s, plan_c);
+    S.mats.t0max = t0max;
+    return XLBOMD_OK;
+  }
+
+  // the pass's traces: Tr T_n (tn) and Tr dT_n/dmu (tmu)
+  xlbomd_status update(xlbomd_ctx* ctx, Sys& S, double tn, double tmu) {
+    const xlbomd_params& p = ctx->p;
+    const double beta = beta_of(p);
+    const double occ_floor = ((p.prec == XLBOMD_FP64) ? 1e-12 : 1e-6) * S.N;
+    const double trD = 0.5 * (S.N + tn);
+    const double trDmu = 0.5 * tmu;
     if (!std::isfinite(trD) || !std::isfinite(trDmu))
       return fail(ctx, XLBOMD_ERR_NOT_CONVERGED, "non-finite trace in the expansion");
     if (trD < S.nocc)
@@ -373,35 +360,169 @@ xlbomd_status density(xlbomd_ctx* ctx, Sys& S, bool with_forces) {
     if (debug_enabled())
       std::fprintf(stderr, "[xlbomd] mu pass %d: mu %.12f trD %.10f (nocc %.1f) trDmu %.6e dmu %.3e bracket [%.6f, %.6f] t0max %.4e\n",
                    pass, mu, trD, S.nocc, trDmu, dmu, blo, bhi, t0max);
-    if (std::fabs(dmu) * beta < p.mu_tol) break;
+    ++pass;
+    if (std::fabs(dmu) * beta < p.mu_tol) {
+      done = true;
+      return XLBOMD_OK;
+    }
     // flat region with the occupation already met to the trace's rounding floor: keep mu
     if (std::fabs(err) < occ_floor) {
       dmu = 0.0;
-      break;
+      done = true;
+      return XLBOMD_OK;
     }
     // Newton converges quadratically; once a step is not much smaller than
     // the previous one (and already small), the rounding noise of the
     // product arithmetic has been reached: keep the first-order correction.
-    if (pass >= 1 && std::fabs(dmu) * beta < 0.05 && std::fabs(dmu) > 0.25 * std::fabs(dmu_prev)) break;
+    if (pass >= 2 && std::fabs(dmu) * beta < 0.05 && std::fabs(dmu) > 0.25 * std::fabs(dmu_prev)) {
+      done = true;
+      return XLBOMD_OK;
+    }
     double next = mu + dmu;
     if (!(trDmu > 0.0) || !(next > blo && next < bhi)) next = 0.5 * (blo + bhi);
     mu = next;
+    return XLBOMD_OK;
   }
-  // first-order correction D(mu + dmu) = D(mu) + dmu dD/dmu
-  S.dmu_last = dmu;
-  S.mu = mu + dmu;
-  S.mu_valid = true;
-  S.mu_hist[2] = S.mu_hist[1];
-  S.mu_hist[1] = S.mu_hist[0];
-  S.mu_hist[0] = S.mu;
-  S.n_mu_hist = std::min(S.n_mu_hist + 1, 3);
-  CK(E.density_out(st, S.mats, S.N, dmu, S.dmu_diag, S.ddiag, S.Dm));
+
+  // first-order correction D(mu + dmu) = D(mu) + dmu dD/dmu and the mu history
+  void finish(Sys& S) const {
+    S.dmu_last = dmu;
+    S.mu = mu + dmu;
+    S.mu_valid = true;
+    S.mu_hist[2] = S.mu_hist[1];
+    S.mu_hist[1] = S.mu_hist[0];
+    S.mu_hist[0] = S.mu;
+    S.n_mu_hist = std::min(S.n_mu_hist + 1, 3);
+  }
+};
+
+// density matrix, charges (and forces) from the final mu pass
+xlbomd_status density_finish(xlbomd_ctx* ctx, Sys& S, const MuSearch& ms, bool with_forces) {
+  cudaStream_t st = ctx->stream;
+  const xlbomd_params& p = ctx->p;
+  ms.finish(S);
+  CK(ctx->eng->density_out(st, S.mats, S.N, ms.dmu, S.dmu_diag, S.ddiag, S.Dm));
   CK(launch_charges(st, S.nat, S.ddiag, S.Z, S.nh, S.q, S.r));
   if (with_forces) {
     CK(launch_forces(st, model_of(p), S.nat, S.L, S.eta, S.ng, S.G4, S.R, S.Dm, S.np, S.q, S.nh, S.F, S.work,
                      p.prec != XLBOMD_FP64));
   }
   S.have_density = true;
+  return XLBOMD_OK;
+}
+
+// a3-a6
+xlbomd_status density(xlbomd_ctx* ctx, Sys& S, bool with_forces) {
+  cudaStream_t st = ctx->stream;
+  const xlbomd_params& p = ctx->p;
+  const int n = p.n_sq;
+  const double sc = beta_of(p) / std::ldexp(1.0, n + 1);
+  Engine& E = *ctx->eng;
+
+  CK(launch_gershgorin(st, S.N, S.np, S.H, S.work));
+  CKS(sync_read(ctx, S.work, 2));
+  MuSearch ms;
+  CKS(ms.start(ctx, S, ctx->pinned[0], ctx->pinned[1]));
+  while (!ms.done) {
+    CKS(ms.prepare(ctx, S));
+    const double mu = ms.mu;
+    auto mu_pass = [&](const double* dp) -> xlbomd_status {
+      CK(E.foe(st, S.mats, S.H, S.N, mu, sc, ms.plan_s, ms.plan_c, S.stats, dp));
+      // mu chain: T1_0 = +sc I, full last level
+      CK(E.chain(st, S.mats, S.dvec_mu, S.N, true, S.dmu_diag, S.stats));
+      CK(E.trace_tn(st, S.mats, S.N, S.scal));          // scal[0] = sum_i T_n,ii
+      CK(launch_sum(st, S.N, S.dmu_diag, S.scal + 1));    // scal[1] = sum_i dT_n,ii/dmu
+      return XLBOMD_OK;
+    };
+    if (use_graphs(ctx, S)) {
+      if (!S.dpar) CKS(dalloc(ctx, &S.dpar, 64));
+      ctx->ppar[0] = mu;
+      for (int k = 0; k < n && k < 63; ++k) ctx->ppar[1 + k] = ms.plan_c[k];
+      CK(cudaMemcpyAsync(S.dpar, ctx->ppar, sizeof(double) * 64, cudaMemcpyHostToDevice, st));
+      std::vector<int> key{0};
+      key.insert(key.end(), ms.plan_s.begin(), ms.plan_s.end());
+      CKS(run_captured(ctx, S, key, [&] { return mu_pass(S.dpar); }));
+    } else {
+      CKS(mu_pass(nullptr));
+    }
+    int* herr = reinterpret_cast<int*>(ctx->pinned + 63);
+    *herr = 0;
+    if (const int* derr = E.device_error())
+      CK(cudaMemcpyAsync(herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKS(sync_read(ctx, S.scal, 2));
+    if (*herr != 0) return fail(ctx, XLBOMD_ERR_TIMEOUT, "tensor-core product: a bounded wait gave up or a tile was out of range");
+    CKS(ms.update(ctx, S, ctx->pinned[0], ctx->pinned[1]));
+  }
+  return density_finish(ctx, S, ms, with_forces);
+}
+
+// a3-a6 for several systems of one padded size in lockstep: every mu pass runs the expansion
+// and the mu chain of all systems still searching as grouped launches, with one host
+// synchronisation per pass for all of them.  Each system takes exactly the steps of density().
+xlbomd_status density_group(xlbomd_ctx* ctx, const std::vector<Sys*>& G, bool with_forces) {
+  cudaStream_t st = ctx->stream;
+  const xlbomd_params& p = ctx->p;
+  const double sc = beta_of(p) / std::ldexp(1.0, p.n_sq + 1);
+  Engine& E = *ctx->eng;
+  const size_t B = G.size();
+  double* h = ctx->pinned_group;
+  for (size_t i = 0; i < B; ++i) {
+    CK(launch_gershgorin(st, G[i]->N, G[i]->np, G[i]->H, G[i]->work));
+    CK(cudaMemcpyAsync(h + 2 * i, G[i]->work, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  std::vector<MuSearch> ms(B);
+  for (size_t i = 0; i < B; ++i) CKS(ms[i].start(ctx, *G[i], h[2 * i], h[2 * i + 1]));
+  std::vector<size_t> active(B);
+  for (size_t i = 0; i < B; ++i) active[i] = i;
+  while (!active.empty()) {
+    std::vector<FoeJob> fj;
+    std::vector<ChainJob> cj;
+    for (size_t i : active) {
+      Sys& S = *G[i];
+      CKS(ms[i].prepare(ctx, S));
+      FoeJob f;
+      f.m = &S.mats;
+      f.H = S.H;
+      f.N = S.N;
+      f.mu = ms[i].mu;
+      f.ns = &ms[i].plan_s;
+      f.nc = &ms[i].plan_c;
+      f.stats = S.stats;
+      fj.push_back(f);
+      ChainJob c;
+      c.m = &S.mats;
+      c.dvec = S.dvec_mu;   // mu chain: T1_0 = +sc I, full last level
+      c.N = S.N;
+      c.out_diag = S.dmu_diag;
+      c.stats = S.stats;
+      cj.push_back(c);
+    }
+    CK(E.foe_group(st, fj, sc));
+    CK(E.chain_group(st, cj, true));
+    for (size_t k = 0; k < active.size(); ++k) {
+      Sys& S = *G[active[k]];
+      CK(E.trace_tn(st, S.mats, S.N, S.scal));
+      CK(launch_sum(st, S.N, S.dmu_diag, S.scal + 1));
+      CK(cudaMemcpyAsync(h + 2 * k, S.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    int* herr = reinterpret_cast<int*>(ctx->pinned + 63);
+    *herr = 0;
+    if (const int* derr = E.device_error())
+      CK(cudaMemcpyAsync(herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (*herr != 0) return fail(ctx, XLBOMD_ERR_TIMEOUT, "tensor-core product: a bounded wait gave up or a tile was out of range");
+    std::vector<size_t> next;
+    for (size_t k = 0; k < active.size(); ++k) {
+      const size_t i = active[k];
+      CKS(ms[i].update(ctx, *G[i], h[2 * k], h[2 * k + 1]));
+      if (ms[i].done)
+        CKS(density_finish(ctx, *G[i], ms[i], with_forces));
+      else
+        next.push_back(i);
+    }
+    active.swap(next);
+  }
   return XLBOMD_OK;
 }
 
@@ -641,6 +762,97 @@ xlbomd_status md_step(xlbomd_ctx* ctx, Sys& S, bool do_energy) {
   return XLBOMD_OK;
 }
 
+// Rank-m kernel update (kernel_mode 0) of several systems of one padded size in lockstep: probe
+// i of every system still probing runs as one grouped response chain, with one host
+// synchronisation per probe index for all of them.  Each system takes exactly the probes of
+// kernel_update().  Other kernel modes update one system after another.
+xlbomd_status kernel_update_group(xlbomd_ctx* ctx, const std::vector<Sys*>& G) {
+  cudaStream_t st = ctx->stream;
+  const xlbomd_params& p = ctx->p;
+  if (p.kernel_mode != 0) {
+    for (Sys* S : G) CKS(kernel_update(ctx, *S));
+    return XLBOMD_OK;
+  }
+  const double sc = beta_of(p) / std::ldexp(1.0, p.n_sq + 1);
+  const size_t B = G.size();
+  double* h = ctx->pinned_group;
+  std::vector<int> m(B, 0);
+  std::vector<size_t> active(B);
+  for (size_t i = 0; i < B; ++i) active[i] = i;
+  for (int i = 0; i < p.rank_m && !active.empty(); ++i) {
+    for (size_t k = 0; k < active.size(); ++k) {
+      Sys& S = *G[active[k]];
+      CK(launch_kernel_vec(st, 0, S.nat, i, S.kc, S.r, S.pV, S.pW, nullptr, S.scal + 8));
+      CK(cudaMemcpyAsync(h + k, S.scal + 8, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    std::vector<size_t> probing;
+    for (size_t k = 0; k < active.size(); ++k)
+      if (h[k] == 1.0) probing.push_back(active[k]);
+    std::vector<ChainJob> cj;
+    for (size_t j : probing) {
+      Sys& S = *G[j];
+      const double* vi = S.pV + (size_t)i * S.nat;
+      CK(gamma_apply(ctx, S, vi, S.potv, S.work));
+      CK(launch_expand_potential(st, S.nat, S.np, -sc, S.potv, S.dvec));
+      ChainJob c;
+      c.m = &S.mats;
+      c.dvec = S.dvec;
+      c.N = S.N;
+      c.out_diag = S.d1;
+      c.stats = S.stats;
+      cj.push_back(c);
+    }
+    CK(ctx->eng->chain_group(st, cj, false));
+    for (size_t j : probing) {
+      Sys& S = *G[j];
+      CK(launch_response_finish(st, S.nat, S.N, S.d1, S.dmu_diag, S.scal + 4, S.pW + (size_t)i * S.nat));
+      m[j] = i + 1;
+    }
+    active.swap(probing);
+  }
+  for (size_t j = 0; j < B; ++j) {
+    Sys& S = *G[j];
+    CK(launch_kernel_vec(st, 1, S.nat, m[j], S.kc, S.r, S.pV, S.pW, S.Kr, S.scal + 8));
+    S.probes_used = m[j];
+    S.stats[2] = m[j];
+  }
+  return XLBOMD_OK;
+}
+
+// One MD step of several systems of one padded size in lockstep (md_step of each, with the
+// expansion, mu passes and probe chains grouped).
+xlbomd_status md_step_group(xlbomd_ctx* ctx, const std::vector<Sys*>& G) {
+  cudaStream_t st = ctx->stream;
+  const xlbomd_params& p = ctx->p;
+  for (Sys* S : G) {
+    CK(launch_verlet_first(st, S->nat, S->L, p.dt, kAcc / S->mass, S->R, S->V, S->F, S->nh, p.kmax, S->Kr, p.kappa,
+                           p.alpha, ctx->cdev));
+    CKS(build_H(ctx, *S));
+  }
+  CKS(density_group(ctx, G, true));
+  for (Sys* S : G) {
+    ++S->md_steps;
+    if (p.kernel_mode == 1 && p.kernel_every > 0 && S->md_steps % p.kernel_every == 0) S->have_K = false;
+  }
+  CKS(kernel_update_group(ctx, G));
+  double* h = ctx->pinned_group;
+  for (size_t k = 0; k < G.size(); ++k) {
+    Sys& S = *G[k];
+    CK(launch_verlet_second(st, S.nat, p.dt, kAcc / S.mass, S.V, S.F));
+    CK(launch_absmax(st, S.nat, S.r, S.scal + 9));
+    const bool e = p.energy_every > 0 && ((int)S.stats[4] + 1) % p.energy_every == 0;
+    if (e) CKS(energy(ctx, S));
+    CK(cudaMemcpyAsync(h + k, S.scal + 9, sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  for (size_t k = 0; k < G.size(); ++k) {
+    if (!(h[k] <= p.diverge_tol)) return fail(ctx, XLBOMD_ERR_DIVERGED, "residual |q - n| too large");
+    G[k]->stats[4] += 1;
+  }
+  return XLBOMD_OK;
+}
+
 void free_sys(Sys& S) {
   double** ptrs[] = {&S.R,  &S.V,        &S.F,    &S.Z,  &S.nh,  &S.q,    &S.r,     &S.Kr,    &S.pot,
                      &S.potv, &S.gam,    &S.SF,   &S.G4, &S.H0,  &S.H,    &S.Dm,    &S.ddiag, &S.dmu_diag,
@@ -832,7 +1044,8 @@ xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* syst
     return st;
   };
   if (cudaMallocHost((void**)&ctx->pinned, 64 * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost((void**)&ctx->ppar, 64 * sizeof(double)) != cudaSuccess)
+      cudaMallocHost((void**)&ctx->ppar, 64 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&ctx->pinned_group, 2 * (size_t)nsys * sizeof(double)) != cudaSuccess)
     return bail(XLBOMD_ERR_OOM);
   if (dalloc(ctx, &ctx->cdev, 8) != XLBOMD_OK) return bail(XLBOMD_ERR_OOM);
   // every upload and memset below runs on the context's stream, which may be non-blocking
@@ -956,12 +1169,24 @@ xlbomd_status xlbomd_energy(xlbomd_ctx* ctx, int sys) {
 
 xlbomd_status xlbomd_step(xlbomd_ctx* ctx, int nsteps) {
   if (!ctx || nsteps < 0) return XLBOMD_ERR_ARG;
+  for (int i = 0; i < (int)ctx->sys.size(); ++i) CKS(check(ctx, i));
+  // systems of one padded size advance in lockstep (grouped launches); a size held by one
+  // system takes the one-system step
+  std::vector<int> sizes;
+  for (const Sys& S : ctx->sys)
+    if (std::find(sizes.begin(), sizes.end(), S.np) == sizes.end()) sizes.push_back(S.np);
   for (int t = 0; t < nsteps; ++t)
-    for (int i = 0; i < (int)ctx->sys.size(); ++i) {
-      CKS(check(ctx, i));
-      Sys& S = ctx->sys[i];
-      const bool e = ctx->p.energy_every > 0 && ((int)S.stats[4] + 1) % ctx->p.energy_every == 0;
-      CKS(md_step(ctx, S, e));
+    for (int np : sizes) {
+      std::vector<Sys*> G;
+      for (Sys& S : ctx->sys)
+        if (S.np == np) G.push_back(&S);
+      if (G.size() == 1) {
+        Sys& S = *G[0];
+        const bool e = ctx->p.energy_every > 0 && ((int)S.stats[4] + 1) % ctx->p.energy_every == 0;
+        CKS(md_step(ctx, S, e));
+      } else {
+        CKS(md_step_group(ctx, G));
+      }
     }
   return XLBOMD_OK;
 }
@@ -1113,6 +1338,14 @@ xlbomd_status xlbomd_selftest_gemm(int n, int prec, int sym, double* result) {
   return rc == 0 ? XLBOMD_OK : XLBOMD_ERR_CUDA;
 }
 
+xlbomd_status xlbomd_selftest_gemm_group(int n, int prec, int sym, int nprob, double* result) {
+  if (!result || n <= 0 || n % 128 || sym < 0 || sym > 6 || sym == 3 || nprob < 2 || nprob > 64)
+    return XLBOMD_ERR_ARG;
+  const int rc = selftest_gemm_group(n, prec, sym, nprob, result);
+  if (rc == -1) return XLBOMD_ERR_ARG;
+  return rc == 0 ? XLBOMD_OK : XLBOMD_ERR_CUDA;
+}
+
 xlbomd_status xlbomd_free(xlbomd_ctx* ctx) {
   if (!ctx) return XLBOMD_ERR_ARG;
   cudaStreamSynchronize(ctx->stream);   // no work of this context may still use its memory
@@ -1120,6 +1353,7 @@ xlbomd_status xlbomd_free(xlbomd_ctx* ctx) {
   if (ctx->cdev) cudaFree(ctx->cdev);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->ppar) cudaFreeHost(ctx->ppar);
+  if (ctx->pinned_group) cudaFreeHost(ctx->pinned_group);
   delete ctx->eng;
   delete ctx;
   return XLBOMD_OK;

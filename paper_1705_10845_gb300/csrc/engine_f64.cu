@@ -150,6 +150,17 @@ void free_matset(MatSet& m) {
   free_matset_split(m);
 }
 
+// Default grouped operations: one system after another.
+cudaError_t Engine::foe_group(cudaStream_t s, std::vector<FoeJob>& jobs, double sc) {
+  for (auto& j : jobs) RET(foe(s, *j.m, j.H, j.N, j.mu, sc, *j.ns, *j.nc, j.stats, j.dpar));
+  return cudaSuccess;
+}
+
+cudaError_t Engine::chain_group(cudaStream_t s, std::vector<ChainJob>& jobs, bool full_last) {
+  for (auto& j : jobs) RET(chain(s, *j.m, j.dvec, j.N, full_last, j.out_diag, j.stats));
+  return cudaSuccess;
+}
+
 Engine* make_engine(int prec) {
   if (prec == 0) return new EngineF64();
   return make_split_engine(prec);

@@ -34,7 +34,6 @@ inline unsigned nblk(size_t count, int tpb = 256) { return (unsigned)((count + t
 // element-wise kernels that raise a matrix's max |x| walk their elements grid-stride with at
 // most this many blocks, so that each launch issues few atomics on the one max
 constexpr unsigned kEwBlocks = 152 * 16;
-inline unsigned ew_blocks(size_t count) { return (unsigned)std::min<size_t>(nblk(count), kEwBlocks); }
 
 // One-CTA-per-tile product kernel: products of at least this size split their hi*hi sums over
 // both accumulators.
@@ -129,24 +128,6 @@ __global__ void convert_hi_kernel(size_t count, const float* __restrict__ f, con
   }
 }
 
-// Y = a I + b X (grid-stride, one max-|Y| atomic per block)
-__global__ void axpi_f32_kernel(int np, float a, float b, const float* __restrict__ X, float* __restrict__ Y,
-                                unsigned* amax, const double* __restrict__ dc = nullptr) {
-  if (dc) {   // a = 1 - c, b = c from the device copy of c
-    a = (float)(1.0 - dc[0]);
-    b = (float)dc[0];
-  }
-  const size_t count = (size_t)np * np;
-  float m = 0.0f;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(idx / np), j = (int)(idx % np);
-    const float v = b * X[idx] + (i == j ? a : 0.0f);
-    Y[idx] = v;
-    m = fmaxf(m, fabsf(v));
-  }
-  raise_amax(amax, m);
-}
-
 __global__ void df_to_f64_kernel(size_t count, const float2* __restrict__ x, double* __restrict__ y) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < count) y[i] = (double)x[i].x + (double)x[i].y;
@@ -196,64 +177,7 @@ __global__ void convert_split_d_kernel(size_t count, const float2* __restrict__ 
   }
 }
 
-// T0 = -sc (H - mu I) as a double-float (hi = rn32(v), lo = rn32(v - hi))
-__global__ void t0_init_d_kernel(int n, int np, const double* __restrict__ H, double mu, double sc,
-                                 float2* __restrict__ T0, unsigned* amax, const double* __restrict__ dmu = nullptr) {
-  if (dmu) mu = dmu[0];
-  const size_t count = (size_t)np * np;
-  float m = 0.0f;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(idx / np), j = (int)(idx % np);
-    double v = 0.0;
-    if (i < n && j < n) v = -sc * (H[idx] - (i == j ? mu : 0.0));
-    const float vh = (float)v;
-    T0[idx] = make_float2(vh, (float)(v - (double)vh));
-    m = fmaxf(m, fabsf(vh));
-  }
-  raise_amax(amax, m);
-}
-
-__global__ void level0_A1_d_kernel(int np, const float2* __restrict__ T0, const double* __restrict__ d,
-                                   float* __restrict__ A1, unsigned* amax) {
-  const size_t count = (size_t)np * np;
-  float m = 0.0f;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(idx / np), j = (int)(idx % np);
-    const float2 t = T0[idx];
-    const float v = (t.x + t.y) * (float)(d[i] + d[j]);
-    A1[idx] = v;
-    m = fmaxf(m, fabsf(v));
-  }
-  raise_amax(amax, m);
-}
-
 __device__ __forceinline__ double df_val(float2 v) { return (double)v.x + (double)v.y; }
-
-// out_i = (Y M)_ii = Mt_ii - sum_j W_ij Mt_ij  (Y = I - W, Mt = M^T), one warp per row
-__global__ void row_dot_last_kernel(int n, int np, const float* __restrict__ W, const float2* __restrict__ Mt,
-                                    double* __restrict__ out) {
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (i >= n) return;
-  float accf = 0.0f;
-  double acc = 0.0;
-  for (int j = lane, c = 0; j < np; j += 32, ++c) {
-    const float2 m = Mt[(size_t)i * np + j];
-    accf += W[(size_t)i * np + j] * (m.x + m.y);
-    if ((c & 15) == 15) {
-      acc += (double)accf;
-      accf = 0.0f;
-    }
-  }
-  acc += (double)accf;
-  acc = warp_sum(acc);
-  if (lane == 0) out[i] = df_val(Mt[(size_t)i * np + i]) - acc;
-}
-
-__global__ void get_diag_d_kernel(int n, int np, const float2* __restrict__ X, double* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = df_val(X[(size_t)i * np + i]);
-}
 
 __global__ void diag_sum_d_kernel(int n, int np, const float2* __restrict__ X, double* __restrict__ out) {
   __shared__ double sh[32];
@@ -274,6 +198,191 @@ __global__ void density_out_d_kernel(int N, int np, const float2* __restrict__ T
     if (i == j) ddiag[i] = 2.0 * v;
   }
   D[idx] = v;
+}
+
+// ---- grouped element-wise kernels ----
+//
+// Batched trajectories step in lockstep: the same element-wise operation runs on the matrices
+// of every system of a group in one launch, blockIdx.y selecting the system.  The per-system
+// pointers travel by value in the kernel parameters (at most kMaxGroup systems per launch).
+constexpr int kMaxGroup = 64;
+
+struct MatList {
+  int n = 0;
+  float* f[kMaxGroup];
+  float2* d[kMaxGroup];
+  uint16_t* hi[kMaxGroup];
+  uint16_t* lo[kMaxGroup];
+  float* scale[kMaxGroup];
+  unsigned* amax[kMaxGroup];
+};
+
+__global__ void zero_amax_kernel(MatList L) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L.n) *L.amax[i] = 0u;
+}
+
+// mode 0: FP32 value -> hi, lo; 1: double-float value -> hi, lo; 2: FP32 value -> hi
+template <bool BF16, int MODE>
+__global__ void convert_group_kernel(size_t count, MatList L) {
+  const int j = blockIdx.y;
+  const float m = __uint_as_float(*L.amax[j]);
+  float s = 1.0f;
+  if (m > 0.0f && isfinite(m)) s = ldexpf(1.0f, 10 - ilogbf(m));
+  if (blockIdx.x == 0 && threadIdx.x == 0) *L.scale[j] = s;
+  ushort4* h4 = reinterpret_cast<ushort4*>(L.hi[j]);
+  ushort4* l4 = reinterpret_cast<ushort4*>(L.lo[j]);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count / 4; i += (size_t)gridDim.x * blockDim.x) {
+    float xs[4], xl[4] = {0.f, 0.f, 0.f, 0.f};
+    if (MODE == 1) {
+      const float4* d4 = reinterpret_cast<const float4*>(L.d[j]);
+      const float4 a = d4[2 * i], b = d4[2 * i + 1];
+      xs[0] = a.x * s; xs[1] = a.z * s; xs[2] = b.x * s; xs[3] = b.z * s;
+      xl[0] = a.y * s; xl[1] = a.w * s; xl[2] = b.y * s; xl[3] = b.w * s;
+    } else {
+      const float4 x = reinterpret_cast<const float4*>(L.f[j])[i];
+      xs[0] = x.x * s; xs[1] = x.y * s; xs[2] = x.z * s; xs[3] = x.w * s;
+    }
+    unsigned short h[4], l[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (BF16) {
+        const __nv_bfloat16 hb = __float2bfloat16_rn(xs[k]);
+        h[k] = __bfloat16_as_ushort(hb);
+        if (MODE != 2) l[k] = __bfloat16_as_ushort(__float2bfloat16_rn((xs[k] - __bfloat162float(hb)) + xl[k]));
+      } else {
+        const __half hh = __float2half_rn(xs[k]);
+        h[k] = __half_as_ushort(hh);
+        if (MODE != 2) l[k] = __half_as_ushort(__float2half_rn((xs[k] - __half2float(hh)) + xl[k]));
+      }
+    }
+    h4[i] = make_ushort4(h[0], h[1], h[2], h[3]);
+    if (MODE != 2) l4[i] = make_ushort4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+// Y = a I + b X per system (W_k start of the Newton-Schulz iteration)
+struct AxpiList {
+  int n = 0;
+  const float* X[kMaxGroup];
+  float* Y[kMaxGroup];
+  unsigned* amax[kMaxGroup];
+  float a[kMaxGroup], b[kMaxGroup];
+  const double* dc[kMaxGroup];   // device c (a = 1 - c, b = c) when not null
+};
+
+__global__ void axpi_group_kernel(int np, AxpiList L) {
+  const int j = blockIdx.y;
+  float a = L.a[j], b = L.b[j];
+  if (L.dc[j]) {
+    a = (float)(1.0 - L.dc[j][0]);
+    b = (float)L.dc[j][0];
+  }
+  const size_t count = (size_t)np * np;
+  const float* X = L.X[j];
+  float* Y = L.Y[j];
+  float m = 0.0f;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / np), c = (int)(idx % np);
+    const float v = b * X[idx] + (r == c ? a : 0.0f);
+    Y[idx] = v;
+    m = fmaxf(m, fabsf(v));
+  }
+  raise_amax(L.amax[j], m);
+}
+
+// T0 = -sc (H - mu I) as a double-float, per system
+struct T0List {
+  int n = 0;
+  int N[kMaxGroup];
+  const double* H[kMaxGroup];
+  double mu[kMaxGroup];
+  const double* dmu[kMaxGroup];
+  float2* T0[kMaxGroup];
+  unsigned* amax[kMaxGroup];
+};
+
+__global__ void t0_init_group_kernel(int np, double sc, T0List L) {
+  const int j = blockIdx.y;
+  const double mu = L.dmu[j] ? L.dmu[j][0] : L.mu[j];
+  const int n = L.N[j];
+  const double* H = L.H[j];
+  float2* T0 = L.T0[j];
+  const size_t count = (size_t)np * np;
+  float m = 0.0f;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / np), c = (int)(idx % np);
+    double v = 0.0;
+    if (r < n && c < n) v = -sc * (H[idx] - (r == c ? mu : 0.0));
+    const float vh = (float)v;
+    T0[idx] = make_float2(vh, (float)(v - (double)vh));
+    m = fmaxf(m, fabsf(vh));
+  }
+  raise_amax(L.amax[j], m);
+}
+
+// A1 of chain level 0 per system: (T0 hi + lo)(d_i + d_j)
+struct A1List {
+  int n = 0;
+  const float2* T0[kMaxGroup];
+  const double* d[kMaxGroup];
+  float* A1[kMaxGroup];
+  unsigned* amax[kMaxGroup];
+};
+
+__global__ void level0_A1_group_kernel(int np, A1List L) {
+  const int j = blockIdx.y;
+  const float2* T0 = L.T0[j];
+  const double* d = L.d[j];
+  float* A1 = L.A1[j];
+  const size_t count = (size_t)np * np;
+  float m = 0.0f;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / np), c = (int)(idx % np);
+    const float2 t = T0[idx];
+    const float v = (t.x + t.y) * (float)(d[r] + d[c]);
+    A1[idx] = v;
+    m = fmaxf(m, fabsf(v));
+  }
+  raise_amax(L.amax[j], m);
+}
+
+// Diagonal reductions of the chains' last level, per system
+struct DiagList {
+  int n = 0;
+  int N[kMaxGroup];
+  const float* W[kMaxGroup];    // row_dot: W_k (FP32)
+  const float2* X[kMaxGroup];   // row_dot: M^T; get_diag: T1_n (double-float)
+  double* out[kMaxGroup];
+};
+
+// out_i = (Y M)_ii = Mt_ii - sum_j W_ij Mt_ij  (Y = I - W, Mt = M^T), one warp per row
+__global__ void row_dot_last_group_kernel(int np, DiagList L) {
+  const int j = blockIdx.y;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= L.N[j]) return;
+  const float* W = L.W[j];
+  const float2* Mt = L.X[j];
+  float accf = 0.0f;
+  double acc = 0.0;
+  for (int c = lane, t = 0; c < np; c += 32, ++t) {
+    const float2 mm = Mt[(size_t)i * np + c];
+    accf += W[(size_t)i * np + c] * (mm.x + mm.y);
+    if ((t & 15) == 15) {
+      acc += (double)accf;
+      accf = 0.0f;
+    }
+  }
+  acc += (double)accf;
+  acc = warp_sum(acc);
+  if (lane == 0) L.out[j][i] = df_val(Mt[(size_t)i * np + i]) - acc;
+}
+
+__global__ void get_diag_group_kernel(int np, DiagList L) {
+  const int j = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L.N[j]) L.out[j][i] = df_val(L.X[j][(size_t)i * np + i]);
 }
 
 // Epilogue options of one split product.  The FP32 side inputs E, E2 are
@@ -313,6 +422,7 @@ class EngineSplit : public Engine {
   ~EngineSplit() override {
     for (auto& kv : tiles_) cudaFree(kv.second.first);
     if (err_) cudaFree(err_);
+    tc_group_cache_free(group_cache_);
   }
 
   cudaError_t convert(cudaStream_t s, SplitMat& m, int np) {
@@ -422,65 +532,323 @@ class EngineSplit : public Engine {
     return e.out64 ? convert_d(s, C, np) : convert(s, C, np);
   }
 
+  // ---- grouped operations (one launch over the systems of a lockstep group) ----
+
+  struct GemmOp {
+    const SplitMat* A;
+    const SplitMat* B;
+    SplitMat* C;
+    Epi e;
+    double* stats;
+  };
+
+  static MatList mat_list(const std::vector<SplitMat*>& ms) {
+    MatList L;
+    L.n = (int)ms.size();
+    for (int i = 0; i < L.n; ++i) {
+      L.f[i] = ms[i]->f;
+      L.d[i] = ms[i]->d;
+      L.hi[i] = ms[i]->hi;
+      L.lo[i] = ms[i]->lo;
+      L.scale[i] = ms[i]->scale;
+      L.amax[i] = ms[i]->amax;
+    }
+    return L;
+  }
+
+  cudaError_t zero_amax_group(cudaStream_t s, const std::vector<SplitMat*>& ms) {
+    if (ms.size() == 1) return cudaMemsetAsync(ms[0]->amax, 0, sizeof(unsigned), s);
+    zero_amax_kernel<<<1, kMaxGroup, 0, s>>>(mat_list(ms));
+    note_launch();
+    return cudaGetLastError();
+  }
+
+  // operand split of each matrix: mode 0 FP32 -> hi, lo; 1 double-float -> hi, lo; 2 FP32 -> hi
+  cudaError_t convert_group(cudaStream_t s, const std::vector<SplitMat*>& ms, int np, int mode) {
+    if (ms.size() == 1) {
+      if (mode == 0) return convert(s, *ms[0], np);
+      if (mode == 1) return convert_d(s, *ms[0], np);
+      return convert_hi(s, *ms[0], np);
+    }
+    const size_t count = (size_t)np * np;
+    const unsigned gx = (unsigned)std::max<size_t>(1, std::min<size_t>(nblk(count), (152 * 16) / ms.size()));
+    const dim3 grid(gx, (unsigned)ms.size());
+    const MatList L = mat_list(ms);
+    if (bf16_) {
+      if (mode == 0) convert_group_kernel<true, 0><<<grid, 256, 0, s>>>(count, L);
+      else if (mode == 1) convert_group_kernel<true, 1><<<grid, 256, 0, s>>>(count, L);
+      else convert_group_kernel<true, 2><<<grid, 256, 0, s>>>(count, L);
+    } else {
+      if (mode == 0) convert_group_kernel<false, 0><<<grid, 256, 0, s>>>(count, L);
+      else if (mode == 1) convert_group_kernel<false, 1><<<grid, 256, 0, s>>>(count, L);
+      else convert_group_kernel<false, 2><<<grid, 256, 0, s>>>(count, L);
+    }
+    note_launch();
+    return cudaGetLastError();
+  }
+
+  static dim3 ew_grid(size_t count, int nsys) {
+    return dim3((unsigned)std::max<size_t>(1, std::min<size_t>(nblk(count), kEwBlocks / nsys)), (unsigned)nsys);
+  }
+
+  // One product per op, all in one grouped launch (ops share sym, nseg, pairs), then each C's
+  // max |x| and operand split.
+  cudaError_t gemm_group(cudaStream_t s, int np, std::vector<GemmOp>& ops, bool sym) {
+    if (ops.empty()) return cudaSuccess;
+    if (ops.size() == 1) {
+      GemmOp& o = ops[0];
+      return gemm(s, np, *o.A, *o.B, *o.C, o.e, sym, o.stats);
+    }
+    RET(prep_tiles(np, s));
+    const TcTiles& tl = tiles_[np].second;
+    const Epi& e0 = ops[0].e;
+    std::vector<SplitMat*> outs;
+    for (auto& o : ops) outs.push_back(o.C);
+    RET(zero_amax_group(s, outs));
+    TcArgs shared;
+    shared.nseg = e0.nseg;
+    shared.pairs = e0.pairs;
+    shared.sym = sym ? 1 : 0;
+    shared.bf16 = bf16_;
+    shared.split_acc = (np >= kSplitAccMin) ? 1 : 0;
+    shared.chunk_kb = kChunkKb;
+    shared.err = err_;
+    std::vector<TcProblem> probs(ops.size());
+    for (size_t i = 0; i < ops.size(); ++i) {
+      const GemmOp& o = ops[i];
+      const Epi& e = o.e;
+      TcArgs& a = probs[i].epi;
+      probs[i].Ahi = o.A->hi;
+      probs[i].Alo = o.A->lo;
+      probs[i].Bhi = o.B->hi;
+      probs[i].Blo = o.B->lo;
+      a.alpha = e.alpha;
+      a.E = e.E ? e.E->f : nullptr;
+      a.beta = e.beta;
+      a.E2 = e.E2 ? e.E2->f : nullptr;
+      a.beta2 = e.beta2;
+      a.E64 = e.E64;
+      a.beta64 = e.beta64;
+      a.e64_trans = e.e64_trans;
+      a.diag = e.diag;
+      a.dvec = e.dvec;
+      a.ndvec = e.dvec ? np : 0;
+      a.dvec_scale = e.dvec_scale;
+      a.C = e.out64 ? nullptr : o.C->f;
+      a.C64 = e.out64 ? o.C->d : nullptr;
+      a.ldc = np;
+      a.amax = o.C->amax;
+      a.sa = o.A->scale;
+      a.sb = o.B->scale;
+      if (o.stats) o.stats[3] += (sym ? 0.5 : 1.0) * e0.pairs;
+    }
+    if (!group_cache_) group_cache_ = tc_group_cache_new();
+    RET(tune_group(s, np, probs, shared, tl));
+    shared.bn = tuned_bn_[np];
+    RET(prof_begin(s));
+    RET(gemm_tc_group(s, np, probs.data(), (int)probs.size(), shared, tl, group_cache_));
+    const int kind = 64 | (sym ? 1 : 0) | (e0.E ? 2 : 0) | (e0.E2 ? 4 : 0) | (e0.E64 ? 8 : 0) |
+                     (e0.e64_trans ? 16 : 0) | (e0.out64 ? 32 : 0);
+    RET(prof_end(s, (double)ops.size() * 2.0 * (double)np * np * np * (sym ? 0.5 : 1.0) * e0.pairs, kind));
+    if (!e0.convert) return cudaSuccess;
+    const int mode = (e0.hi_only && !e0.out64) ? 2 : (e0.out64 ? 1 : 0);
+    return convert_group(s, outs, np, mode);
+  }
+
+  // Tile-width autotuner of grouped products: the first grouped product of a size that both
+  // widths can tile (n a multiple of 256) runs twice with 128-wide and twice with 256-wide
+  // tiles, timed with CUDA events on the stream, and the faster width serves every later
+  // grouped product of that size.  (Few large tiles leave SMs idle on small matrices; narrow
+  // tiles stage more operand bytes per flop on large ones.)  The product is recomputed from the
+  // same operands each time, so the tuning runs change nothing.
+  cudaError_t tune_group(cudaStream_t s, int np, std::vector<TcProblem>& probs, TcArgs shared, const TcTiles& tl) {
+    if (tuned_bn_.count(np)) return cudaSuccess;
+    if (np % 256 != 0) {
+      tuned_bn_[np] = 128;
+      return cudaSuccess;
+    }
+    cudaEvent_t ev[3];
+    for (auto& e : ev) RET(cudaEventCreate(&e));
+    float ms[2] = {0.f, 0.f};
+    const int widths[2] = {128, 256};
+    cudaError_t rc = cudaSuccess;
+    for (int w = 0; w < 2 && rc == cudaSuccess; ++w) {
+      shared.bn = widths[w];
+      rc = gemm_tc_group(s, np, probs.data(), (int)probs.size(), shared, tl, group_cache_);   // warm-up
+      if (rc == cudaSuccess) rc = cudaEventRecord(ev[0], s);
+      if (rc == cudaSuccess) rc = gemm_tc_group(s, np, probs.data(), (int)probs.size(), shared, tl, group_cache_);
+      if (rc == cudaSuccess) rc = cudaEventRecord(ev[1], s);
+      if (rc == cudaSuccess) rc = cudaEventSynchronize(ev[1]);
+      if (rc == cudaSuccess) rc = cudaEventElapsedTime(&ms[w], ev[0], ev[1]);
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    RET(rc);
+    tuned_bn_[np] = (ms[0] < ms[1]) ? 128 : 256;
+    if (const char* d = std::getenv("XLBOMD_DEBUG"))
+      if (d[0] && d[0] != '0')
+        std::fprintf(stderr, "[xlbomd] tile autotuner n %d, %zu problems: 128-wide %.3f ms, 256-wide %.3f ms -> %d\n",
+                     np, probs.size(), ms[0], ms[1], tuned_bn_[np]);
+    return cudaSuccess;
+  }
+
   cudaError_t foe(cudaStream_t s, MatSet& m, const double* H, int N, double mu, double sc,
                   const std::vector<int>& ns, const std::vector<double>& nc, double* stats,
                   const double* dpar) override {
-    const int np = m.np, n = m.n;
+    std::vector<FoeJob> jobs(1);
+    jobs[0].m = &m;
+    jobs[0].H = H;
+    jobs[0].N = N;
+    jobs[0].mu = mu;
+    jobs[0].ns = &ns;
+    jobs[0].nc = &nc;
+    jobs[0].stats = stats;
+    jobs[0].dpar = dpar;
+    return foe_group(s, jobs, sc);
+  }
+
+  // The recursion of every job's system in lockstep: each product of a level is one grouped
+  // launch over the jobs that need it (a job runs its own Newton-Schulz iteration count).
+  cudaError_t foe_group(cudaStream_t s, std::vector<FoeJob>& jobs, double sc) override {
+    const int B = (int)jobs.size();
+    if (B == 0) return cudaSuccess;
+    if (B > kMaxGroup) {
+      for (int i = 0; i < B; i += kMaxGroup) {
+        std::vector<FoeJob> part(jobs.begin() + i, jobs.begin() + std::min(B, i + kMaxGroup));
+        RET(foe_group(s, part, sc));
+      }
+      return cudaSuccess;
+    }
+    const int np = jobs[0].m->np, n = jobs[0].m->n;
+    for (auto& j : jobs)
+      if (j.m->np != np || j.m->n != n) return cudaErrorInvalidValue;
     const size_t cnt = (size_t)np * np;
-    RET(cudaMemsetAsync(m.sT[0].amax, 0, sizeof(unsigned), s));
-    t0_init_d_kernel<<<ew_blocks(cnt), 256, 0, s>>>(N, np, H, mu, sc, m.sT[0].d, m.sT[0].amax, dpar);
+    std::vector<SplitMat*> T0s;
+    T0List tl;
+    tl.n = B;
+    for (int i = 0; i < B; ++i) {
+      FoeJob& j = jobs[i];
+      T0s.push_back(&j.m->sT[0]);
+      tl.N[i] = j.N;
+      tl.H[i] = j.H;
+      tl.mu[i] = j.mu;
+      tl.dmu[i] = j.dpar;
+      tl.T0[i] = j.m->sT[0].d;
+      tl.amax[i] = j.m->sT[0].amax;
+    }
+    RET(zero_amax_group(s, T0s));
+    t0_init_group_kernel<<<ew_grid(cnt, B), 256, 0, s>>>(np, sc, tl);
     note_launch();
     RET(cudaGetLastError());
-    RET(convert_d(s, m.sT[0], np));
+    RET(convert_group(s, T0s, np, 1));
+    std::vector<SplitMat*> W(B), Wn(B);
     for (int k = 0; k < n; ++k) {
-      Epi es;
-      RET(gemm(s, np, m.sT[k], m.sT[k], m.sS, es, true, stats));                 // S = T^2
+      std::vector<GemmOp> ops;
+      for (auto& j : jobs) ops.push_back({&j.m->sT[k], &j.m->sT[k], &j.m->sS, Epi(), j.stats});   // S = T^2
+      RET(gemm_group(s, np, ops, true));
       // the Newton-Schulz iterates alternate between sY[k] and the work matrix; the start is
       // chosen by the parity of the iteration count so that W_k always ends in sY[k] (the
       // buffers every later use, and a captured graph of this pass, refer to)
-      SplitMat* W = (ns[k] % 2 == 1) ? &m.sYw : &m.sY[k];
-      SplitMat* Wn = (W == &m.sY[k]) ? &m.sYw : &m.sY[k];
-      RET(cudaMemsetAsync(W->amax, 0, sizeof(unsigned), s));
-      if (k == 0)
-        axpi_f32_kernel<<<ew_blocks(cnt), 256, 0, s>>>(np, 0.f, 1.f, m.sS.f, W->f, W->amax);        // W = S
-      else
-        axpi_f32_kernel<<<ew_blocks(cnt), 256, 0, s>>>(np, (float)(1.0 - nc[k]), (float)nc[k], m.sY[k - 1].f, W->f,
-                                                 W->amax, dpar ? dpar + 1 + k : nullptr);  // W = (1-c) I + c W_{k-1}
+      AxpiList al;
+      al.n = B;
+      int maxit = 0;
+      for (int i = 0; i < B; ++i) {
+        FoeJob& j = jobs[i];
+        MatSet& m = *j.m;
+        const int nsk = (*j.ns)[k];
+        maxit = std::max(maxit, nsk);
+        W[i] = (nsk % 2 == 1) ? &m.sYw : &m.sY[k];
+        Wn[i] = (W[i] == &m.sY[k]) ? &m.sYw : &m.sY[k];
+        al.Y[i] = W[i]->f;
+        al.amax[i] = W[i]->amax;
+        if (k == 0) {                                                             // W = S
+          al.X[i] = m.sS.f;
+          al.a[i] = 0.f;
+          al.b[i] = 1.f;
+          al.dc[i] = nullptr;
+        } else {                                                                  // W = (1-c) I + c W_{k-1}
+          al.X[i] = m.sY[k - 1].f;
+          al.a[i] = (float)(1.0 - (*j.nc)[k]);
+          al.b[i] = (float)(*j.nc)[k];
+          al.dc[i] = j.dpar ? j.dpar + 1 + k : nullptr;
+        }
+      }
+      RET(zero_amax_group(s, W));
+      axpi_group_kernel<<<ew_grid(cnt, B), 256, 0, s>>>(np, al);
       note_launch();
       RET(cudaGetLastError());
-      RET(convert(s, *W, np));
-      for (int it = 0; it < ns[k]; ++it) {
-        Epi eq;                                                                   // Q = S - W - W S
-        eq.alpha = -1.f;
-        eq.E = &m.sS;
-        eq.beta = 1.f;
-        eq.E2 = W;
-        eq.beta2 = -1.f;
-        RET(gemm(s, np, *W, m.sS, m.sQ, eq, false, stats));
-        Epi ew;                                                                   // W <- W + Q - Q W
-        ew.alpha = -1.f;
-        ew.E = W;
-        ew.beta = 1.f;
-        ew.E2 = &m.sQ;
-        ew.beta2 = 1.f;
-        RET(gemm(s, np, m.sQ, *W, *Wn, ew, true, stats));
-        std::swap(W, Wn);
-        if (stats) stats[1] += 1;
+      RET(convert_group(s, W, np, 0));
+      for (int it = 0; it < maxit; ++it) {
+        std::vector<GemmOp> oq, ow;
+        std::vector<int> who;
+        for (int i = 0; i < B; ++i) {
+          FoeJob& j = jobs[i];
+          if ((*j.ns)[k] <= it) continue;
+          MatSet& m = *j.m;
+          Epi eq;                                                                 // Q = S - W - W S
+          eq.alpha = -1.f;
+          eq.E = &m.sS;
+          eq.beta = 1.f;
+          eq.E2 = W[i];
+          eq.beta2 = -1.f;
+          oq.push_back({W[i], &m.sS, &m.sQ, eq, j.stats});
+          Epi ew;                                                                 // W <- W + Q - Q W
+          ew.alpha = -1.f;
+          ew.E = W[i];
+          ew.beta = 1.f;
+          ew.E2 = &m.sQ;
+          ew.beta2 = 1.f;
+          ow.push_back({&m.sQ, W[i], Wn[i], ew, j.stats});
+          who.push_back(i);
+        }
+        RET(gemm_group(s, np, oq, false));
+        RET(gemm_group(s, np, ow, true));
+        for (int i : who) {
+          std::swap(W[i], Wn[i]);
+          if (jobs[i].stats) jobs[i].stats[1] += 1;
+        }
       }
-      Epi et;                                                                     // T' = 2T - 2 T W
-      et.alpha = -2.f;
-      et.E64 = m.sT[k].d;                                                         // symmetric: read transposed
-      et.e64_trans = 1;
-      et.beta64 = 2.0f;
-      et.out64 = true;
-      RET(gemm(s, np, m.sT[k], m.sY[k], m.sT[k + 1], et, true, stats));
+      std::vector<GemmOp> ot;
+      for (auto& j : jobs) {
+        MatSet& m = *j.m;
+        Epi et;                                                                   // T' = 2T - 2 T W
+        et.alpha = -2.f;
+        et.E64 = m.sT[k].d;                                                       // symmetric: read transposed
+        et.e64_trans = 1;
+        et.beta64 = 2.0f;
+        et.out64 = true;
+        ot.push_back({&m.sT[k], &m.sY[k], &m.sT[k + 1], et, j.stats});
+      }
+      RET(gemm_group(s, np, ot, true));
     }
     return cudaSuccess;
   }
 
   cudaError_t chain(cudaStream_t s, MatSet& m, const double* dvec, int N, bool full_last, double* out_diag,
                     double* stats) override {
-    const int np = m.np, n = m.n;
+    std::vector<ChainJob> jobs(1);
+    jobs[0].m = &m;
+    jobs[0].dvec = dvec;
+    jobs[0].N = N;
+    jobs[0].out_diag = out_diag;
+    jobs[0].stats = stats;
+    return chain_group(s, jobs, full_last);
+  }
+
+  // Response chains of several systems (or several probes of one system, each with its own
+  // chain matrices) in lockstep, every product a grouped launch.
+  cudaError_t chain_group(cudaStream_t s, std::vector<ChainJob>& jobs, bool full_last) override {
+    const int B = (int)jobs.size();
+    if (B == 0) return cudaSuccess;
+    if (B > kMaxGroup) {
+      for (int i = 0; i < B; i += kMaxGroup) {
+        std::vector<ChainJob> part(jobs.begin() + i, jobs.begin() + std::min(B, i + kMaxGroup));
+        RET(chain_group(s, part, full_last));
+      }
+      return cudaSuccess;
+    }
+    const int np = jobs[0].m->np, n = jobs[0].m->n;
+    for (auto& j : jobs)
+      if (j.m->np != np || j.m->n != n) return cudaErrorInvalidValue;
     const size_t cnt = (size_t)np * np;
     // either chain may run on the hi operands alone (the mu chain is the one with a full last level)
     const int nseg = full_last ? mu_nseg_ : probe_nseg_;
@@ -489,70 +857,122 @@ class EngineSplit : public Engine {
     // chain would add traffic and no accuracy.  The last level still writes the double-float array
     // the reductions read (with a zero low word).
     const bool single = (nseg == 1);
-    SplitMat* T1 = &m.sT1a;
-    SplitMat* T1n = &m.sT1b;
+    std::vector<SplitMat*> T1(B), T1n(B), A1s(B), Mts(B);
+    for (int i = 0; i < B; ++i) {
+      T1[i] = &jobs[i].m->sT1a;
+      T1n[i] = &jobs[i].m->sT1b;
+      A1s[i] = &jobs[i].m->sA1;
+      Mts[i] = &jobs[i].m->sMt;
+    }
     for (int k = 0; k < n; ++k) {
       const bool last = (k == n - 1);
-      RET(cudaMemsetAsync(m.sA1.amax, 0, sizeof(unsigned), s));
+      RET(zero_amax_group(s, A1s));
       Epi em;                                                                    // Mt = 2 T1 - T_{k+1} A1
       em.alpha = -1.f;
       em.out64 = !single || (last && !full_last);
       em.hi_only = single;
       em.convert = !(last && !full_last);                                        // the last M of a probe
       em.nseg = nseg;                                                            // chain is only reduced
+      std::vector<GemmOp> om;
       if (k == 0) {
-        level0_A1_d_kernel<<<ew_blocks(cnt), 256, 0, s>>>(np, m.sT[0].d, dvec, m.sA1.f, m.sA1.amax);
+        A1List al;
+        al.n = B;
+        for (int i = 0; i < B; ++i) {
+          al.T0[i] = jobs[i].m->sT[0].d;
+          al.d[i] = jobs[i].dvec;
+          al.A1[i] = A1s[i]->f;
+          al.amax[i] = A1s[i]->amax;
+        }
+        level0_A1_group_kernel<<<ew_grid(cnt, B), 256, 0, s>>>(np, al);
         note_launch();
         RET(cudaGetLastError());
-        em.dvec = dvec;
-        em.dvec_scale = 2.f;
+        for (int i = 0; i < B; ++i) {
+          Epi e = em;
+          e.dvec = jobs[i].dvec;
+          e.dvec_scale = 2.f;
+          om.push_back({&jobs[i].m->sT[k + 1], A1s[i], Mts[i], e, jobs[i].stats});
+        }
       } else {
         // A1 = T T1 + T1 T (T, T1 symmetric): one symmetric-output product over the two K pairs
-        Epi ea;
-        ea.convert = false;
-        ea.nseg = nseg;
-        ea.pairs = 2;
-        RET(gemm(s, np, m.sT[k], *T1, m.sA1, ea, true, stats));
-        if (single) {
-          em.E = T1;                                                              // FP32, symmetric
-          em.beta = 2.0f;
-        } else {
-          em.E64 = T1->d;                                                         // symmetric: read transposed
-          em.e64_trans = 1;
-          em.beta64 = 2.0f;
+        std::vector<GemmOp> oa;
+        for (int i = 0; i < B; ++i) {
+          Epi ea;
+          ea.convert = false;
+          ea.nseg = nseg;
+          ea.pairs = 2;
+          oa.push_back({&jobs[i].m->sT[k], T1[i], A1s[i], ea, jobs[i].stats});
+        }
+        RET(gemm_group(s, np, oa, true));
+        for (int i = 0; i < B; ++i) {
+          Epi e = em;
+          if (single) {
+            e.E = T1[i];                                                          // FP32, symmetric
+            e.beta = 2.0f;
+          } else {
+            e.E64 = T1[i]->d;                                                     // symmetric: read transposed
+            e.e64_trans = 1;
+            e.beta64 = 2.0f;
+          }
+          om.push_back({&jobs[i].m->sT[k + 1], A1s[i], Mts[i], e, jobs[i].stats});
         }
       }
-      RET(single ? convert_hi(s, m.sA1, np) : convert(s, m.sA1, np));
-      RET(gemm(s, np, m.sT[k + 1], m.sA1, m.sMt, em, false, stats));
+      RET(convert_group(s, A1s, np, single ? 2 : 0));
+      RET(gemm_group(s, np, om, false));
       if (last && !full_last) {
-        row_dot_last_kernel<<<(N + 7) / 8, 256, 0, s>>>(N, np, m.sY[k].f, m.sMt.d, out_diag);
+        DiagList dl;
+        dl.n = B;
+        int maxN = 0;
+        for (int i = 0; i < B; ++i) {
+          dl.N[i] = jobs[i].N;
+          dl.W[i] = jobs[i].m->sY[k].f;
+          dl.X[i] = Mts[i]->d;
+          dl.out[i] = jobs[i].out_diag;
+          maxN = std::max(maxN, jobs[i].N);
+        }
+        row_dot_last_group_kernel<<<dim3((maxN + 7) / 8, B), 256, 0, s>>>(np, dl);
         note_launch();
         return cudaGetLastError();
       }
-      SplitMat* dst = (last && full_last) ? &m.sTmu : T1n;
-      Epi ey;                                                                    // T1' = M - W M
-      ey.alpha = -1.f;
-      if (single) {
-        ey.E = &m.sMt;                                                            // read transposed: M
-        ey.beta = 1.0f;
-        ey.out64 = last;                                                          // T_mu (double-float)
-        ey.hi_only = true;
-      } else {
-        ey.E64 = m.sMt.d;
-        ey.beta64 = 1.0f;
-        ey.e64_trans = 1;
-        ey.out64 = true;
+      std::vector<SplitMat*> dst(B);
+      std::vector<GemmOp> oy;
+      for (int i = 0; i < B; ++i) {
+        dst[i] = (last && full_last) ? &jobs[i].m->sTmu : T1n[i];
+        Epi ey;                                                                  // T1' = M - W M
+        ey.alpha = -1.f;
+        if (single) {
+          ey.E = Mts[i];                                                          // read transposed: M
+          ey.beta = 1.0f;
+          ey.out64 = last;                                                        // T_mu (double-float)
+          ey.hi_only = true;
+        } else {
+          ey.E64 = Mts[i]->d;
+          ey.beta64 = 1.0f;
+          ey.e64_trans = 1;
+          ey.out64 = true;
+        }
+        ey.convert = !last;
+        ey.nseg = nseg;
+        oy.push_back({&jobs[i].m->sY[k], Mts[i], dst[i], ey, jobs[i].stats});
       }
-      ey.convert = !last;
-      ey.nseg = nseg;
-      RET(gemm(s, np, m.sY[k], m.sMt, *dst, ey, true, stats));
+      RET(gemm_group(s, np, oy, true));
       if (last) {
-        get_diag_d_kernel<<<(N + 255) / 256, 256, 0, s>>>(N, np, dst->d, out_diag);
+        DiagList dl;
+        dl.n = B;
+        int maxN = 0;
+        for (int i = 0; i < B; ++i) {
+          dl.N[i] = jobs[i].N;
+          dl.X[i] = dst[i]->d;
+          dl.out[i] = jobs[i].out_diag;
+          maxN = std::max(maxN, jobs[i].N);
+        }
+        get_diag_group_kernel<<<dim3((maxN + 255) / 256, B), 256, 0, s>>>(np, dl);
         note_launch();
         return cudaGetLastError();
       }
-      T1n = T1;
-      T1 = dst;
+      for (int i = 0; i < B; ++i) {
+        T1n[i] = T1[i];
+        T1[i] = dst[i];
+      }
     }
     return cudaSuccess;
   }
@@ -607,6 +1027,8 @@ class EngineSplit : public Engine {
   int probe_nseg_ = 3;
   int mu_nseg_ = 3;
   std::unordered_map<int, std::pair<int*, TcTiles>> tiles_;
+  TcGroupCache* group_cache_ = nullptr;
+  std::unordered_map<int, int> tuned_bn_;   // grouped products: tile width per size
 };
 
 // which value arrays a matrix keeps
@@ -732,6 +1154,22 @@ __global__ void to_f32_kernel(size_t count, const double* __restrict__ x, float*
   raise_amax(amax, v);
 }
 
+__global__ void diff_f32_kernel(size_t count, const float* __restrict__ a, const float* __restrict__ b,
+                                double* __restrict__ out) {
+  __shared__ double sh[32];
+  double m = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs((double)a[i] - (double)b[i]));
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, sh[w]);
+    atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(t));
+  }
+}
+
 __global__ void max_abs_diff_kernel(size_t count, const float* __restrict__ a, const double* __restrict__ b,
                                     double* __restrict__ out) {
   __shared__ double sh[32];
@@ -783,6 +1221,86 @@ done:
   if (A) cudaFree(A);
   if (B) cudaFree(B);
   if (C) cudaFree(C);
+  return rc;
+}
+
+// Grouped products against single products: nprob seeded operand pairs, each product computed
+// alone and then all of them in one grouped launch (with 128- and 256-wide tiles where n allows
+// both); result = [max |C_group - C_single| over the problems and widths, error flag].
+int selftest_gemm_group(int n, int prec, int mode, int nprob, double* result) {
+  if (n % 128 || n <= 0 || nprob < 2 || nprob > kMaxGroup || (prec != XLBOMD_FP16x3_ID && prec != XLBOMD_BF16x3_ID))
+    return -1;
+  const bool single = mode >= 4;
+  const int sym = single ? mode - 4 : mode;
+  if (sym < 0 || sym > 2) return -1;
+  EngineSplit eng(prec);
+  const size_t cnt = (size_t)n * n;
+  std::vector<SplitMat> A(nprob), B(nprob), C(nprob), R(nprob);
+  double *tmp = nullptr, *out = nullptr;
+  float* scal = nullptr;
+  int rc = -2;
+  std::vector<double> worst(1, 0.0);
+  if (cudaMalloc((void**)&tmp, cnt * 8) || cudaMalloc((void**)&out, 8) ||
+      cudaMalloc((void**)&scal, 8 * nprob * sizeof(float)))
+    goto done;
+  cudaMemset(scal, 0, 8 * nprob * sizeof(float));
+  for (int i = 0; i < nprob; ++i) {
+    float* sf = scal + 4 * i;
+    unsigned* su = reinterpret_cast<unsigned*>(scal + 4 * nprob + 4 * i);
+    if (alloc_split(A[i], n, sf, su, kF, nullptr) || alloc_split(B[i], n, sf + 1, su + 1, kF, nullptr) ||
+        alloc_split(C[i], n, sf + 2, su + 2, kF, nullptr) || alloc_split(R[i], n, sf + 3, su + 3, kF, nullptr))
+      goto done;
+    fill_random_kernel<<<nblk(cnt), 256>>>(cnt, n, 101 + 7 * i, 0, tmp);
+    note_launch();
+    to_f32_kernel<<<nblk(cnt), 256>>>(cnt, tmp, A[i].f, A[i].amax);
+    note_launch();
+    fill_random_kernel<<<nblk(cnt), 256>>>(cnt, n, 203 + 11 * i, sym, tmp);
+    note_launch();
+    to_f32_kernel<<<nblk(cnt), 256>>>(cnt, tmp, B[i].f, B[i].amax);
+    note_launch();
+    if (eng.convert(nullptr, A[i], n) || eng.convert(nullptr, B[i], n)) goto done;
+  }
+  {
+    Epi ep;
+    ep.pairs = (sym == 2) ? 2 : 1;
+    ep.nseg = single ? 1 : 3;
+    ep.alpha = 0.75f;
+    for (int i = 0; i < nprob; ++i)
+      if (eng.gemm(nullptr, n, A[i], B[i], R[i], ep, sym != 0, nullptr)) goto done;
+    std::vector<EngineSplit::GemmOp> ops;
+    for (int i = 0; i < nprob; ++i) ops.push_back({&A[i], &B[i], &C[i], ep, nullptr});
+    // the autotuner runs both widths on the first grouped product of this size; then the
+    // chosen width; compare after each
+    for (int rep = 0; rep < 2; ++rep) {
+      if (eng.gemm_group(nullptr, n, ops, sym != 0)) goto done;
+      for (int i = 0; i < nprob; ++i) {
+        if (cudaMemset(out, 0, 8)) goto done;
+        diff_f32_kernel<<<304, 256>>>(cnt, C[i].f, R[i].f, out);
+        note_launch();
+        double h = 0.0;
+        if (cudaMemcpy(&h, out, 8, cudaMemcpyDeviceToHost)) goto done;
+        worst[0] = std::max(worst[0], h);
+      }
+    }
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) goto done;
+  {
+    int herr = 0;
+    cudaMemcpy(&herr, eng.err_, sizeof(int), cudaMemcpyDeviceToHost);
+    result[0] = worst[0];
+    result[1] = herr;
+    rc = 0;
+  }
+done:
+  for (int i = 0; i < nprob; ++i) {
+    free_split(A[i]);
+    free_split(B[i]);
+    free_split(C[i]);
+    free_split(R[i]);
+  }
+  if (tmp) cudaFree(tmp);
+  if (out) cudaFree(out);
+  if (scal) cudaFree(scal);
   return rc;
 }
 

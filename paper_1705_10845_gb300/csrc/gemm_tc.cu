@@ -31,6 +31,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <cstdlib>
 #include <mutex>
 #include <string>
@@ -81,6 +82,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<uint64_t>(p)));
+}
+
+// A tensor map written to global memory by the host (grouped launches) reaches the TMA unit
+// through the tensormap proxy: acquire it before its first use in the kernel.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+               : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -572,6 +580,18 @@ __global__ void __launch_bounds__(192, 1)
 // MMA, four warp arrivals per phase).  Every wait is bounded; a role that gives up records an
 // error and raises a shared abort flag that ends the other roles' loops.
 
+// Grouped launch (tab != null): tile id -> problem p of the group and its tile lid; tiles_per
+// tiles per problem.  Otherwise one problem.
+__device__ __forceinline__ void group_tile(const TcEntry* tab, int tiles_per, int id, int& p, int& lid) {
+  if (tab) {
+    p = id / tiles_per;
+    lid = id - p * tiles_per;
+  } else {
+    p = 0;
+    lid = id;
+  }
+}
+
 // K-block order of one tile (the producer and the MMA thread walk it alike): the Cn correction
 // K blocks first (hi*lo, lo*hi of pair 0, then of pair 1), then the hi*hi sequence (pair 0's K
 // blocks, then pair 1's).  Counters only, no divisions.
@@ -619,7 +639,7 @@ __global__ void __launch_bounds__(192, 1)
                               const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
                               const __grid_constant__ CUtensorMap mA2hi, const __grid_constant__ CUtensorMap mA2lo,
                               const __grid_constant__ CUtensorMap mB2hi, const __grid_constant__ CUtensorMap mB2lo,
-                              TcArgs a, int ntiles) {
+                              TcArgs a, int ntiles, const TcEntry* __restrict__ tab, int tiles_per) {
   constexpr int B_BYTES = BN * BK * 2;
   constexpr uint32_t TMEM_COLS = 2 * BN;
   constexpr int STAGE_TILE = 32 * 33 * 4;
@@ -673,12 +693,19 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0) {
       uint32_t g = 0;
       bool ok = true;
+      int last_p = -1;
       for (int id = blockIdx.x; id < ntiles && ok && !*abort_flag; id += gridDim.x) {
-        int tm, tn;
-        if (!tile_coords(a, id, tm, tn)) {
+        int tm, tn, p, lid;
+        group_tile(tab, tiles_per, id, p, lid);
+        if (!tile_coords(a, lid, tm, tn)) {
           atomicExch(a.err, 4);
           *abort_flag = 1;
           break;
+        }
+        const CUtensorMap* maps = tab ? tab[p].map : nullptr;   // grouped: this problem's maps
+        if (maps && p != last_p) {
+          for (int i = 0; i < 8; ++i) tensormap_acquire(&maps[i]);
+          last_p = p;
         }
         KWalk w;
         kwalk_begin(w, Cn);
@@ -693,8 +720,10 @@ __global__ void __launch_bounds__(192, 1)
           }
           mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
           const int kk = w.kidx * BK;
-          const CUtensorMap* ma = (w.kind == 2) ? (w.pr ? &mA2lo : &mAlo) : (w.pr ? &mA2hi : &mAhi);
-          const CUtensorMap* mb = (w.kind == 1) ? (w.pr ? &mB2lo : &mBlo) : (w.pr ? &mB2hi : &mBhi);
+          const int ia = (w.kind == 2) ? (w.pr ? 5 : 1) : (w.pr ? 4 : 0);
+          const int ib = (w.kind == 1) ? (w.pr ? 7 : 3) : (w.pr ? 6 : 2);
+          const CUtensorMap* ma = maps ? &maps[ia] : (w.kind == 2) ? (w.pr ? &mA2lo : &mAlo) : (w.pr ? &mA2hi : &mAhi);
+          const CUtensorMap* mb = maps ? &maps[ib] : (w.kind == 1) ? (w.pr ? &mB2lo : &mBlo) : (w.pr ? &mB2hi : &mBhi);
           tma_load_2d(sA + s * A_BYTES, ma, kk, tm * BM, &full[s]);
           tma_load_2d(sB + s * B_BYTES, mb, kk, tn * BN, &full[s]);
         }
@@ -711,7 +740,9 @@ __global__ void __launch_bounds__(192, 1)
       int par = 0;                   // split products: accumulator parity p of this tile
       for (int id = blockIdx.x; id < ntiles && !*abort_flag; id += gridDim.x, ++it, par ^= 1) {
         int tm, tn;
-        if (!tile_coords(a, id, tm, tn)) break;
+        int p_, lid;
+        group_tile(tab, tiles_per, id, p_, lid);
+        if (!tile_coords(a, lid, tm, tn)) break;
         bool ok = true;
         const int buf = it & 1;      // single products: accumulator of this tile
         int cur = 0;                 // accumulator of the current step
@@ -778,14 +809,16 @@ __global__ void __launch_bounds__(192, 1)
     float(*tx)[33] = reinterpret_cast<float(*)[33]>(stage + q * 2 * STAGE_TILE);
     float(*ty)[33] = reinterpret_cast<float(*)[33]>(stage + q * 2 * STAGE_TILE + STAGE_TILE);
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    const float inv = a.alpha / (__ldg(a.sa) * __ldg(a.sb));
     int it = 0;
     uint32_t ev = 0;                 // acc_full[0] phases consumed (split products)
     int par = 0;                     // split products: accumulator parity p of this tile
     for (int id = blockIdx.x; id < ntiles && !*abort_flag; id += gridDim.x, ++it, par ^= 1) {
-      int tm, tn;
-      if (!tile_coords(a, id, tm, tn)) break;
-      prefetch_sides<BN>(a, tm, tn, (warp - 2) * 32 + lane);
+      int tm, tn, p, lid;
+      group_tile(tab, tiles_per, id, p, lid);
+      if (!tile_coords(a, lid, tm, tn)) break;
+      const TcArgs& ea = tab ? tab[p].args : a;     // this problem's epilogue
+      const float inv = ea.alpha / (__ldg(ea.sa) * __ldg(ea.sb));
+      prefetch_sides<BN>(ea, tm, tn, (warp - 2) * 32 + lane);
       int src;                       // accumulator holding the tile's sum
       bool ok = true;
       if (!chunked) {
@@ -830,10 +863,10 @@ __global__ void __launch_bounds__(192, 1)
       for (int ch = 0; ch < BN / 32; ++ch) {
         float v[32];
         tmem_ld32(tmem + lane_base + (uint32_t)(src * BN + ch * 32), v);
-        epilogue_chunk(a, v, row, row0, tn * BN + ch * 32, lane, tx, ty, inv, vmax);
+        epilogue_chunk(ea, v, row, row0, tn * BN + ch * 32, lane, tx, ty, inv, vmax);
       }
       for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-      if (lane == 0 && a.amax) atomicMax(a.amax, __float_as_uint(vmax));
+      if (lane == 0 && ea.amax) atomicMax(ea.amax, __float_as_uint(vmax));
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_free[src]);
@@ -1437,12 +1470,14 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
       const int sb = smem_bytes_persistent<256>();
       const cudaError_t attr = ensure_smem(0, gemm_tc_persistent_kernel<256>, sb);
       if (attr != cudaSuccess) return attr;
-      gemm_tc_persistent_kernel<256><<<grid, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo, args, nblocks);
+      gemm_tc_persistent_kernel<256><<<grid, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo, args, nblocks,
+                                                           nullptr, 0);
     } else {
       const int sb = smem_bytes_persistent<128>();
       const cudaError_t attr = ensure_smem(1, gemm_tc_persistent_kernel<128>, sb);
       if (attr != cudaSuccess) return attr;
-      gemm_tc_persistent_kernel<128><<<grid, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo, args, nblocks);
+      gemm_tc_persistent_kernel<128><<<grid, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo, args, nblocks,
+                                                           nullptr, 0);
     }
     note_launch();
     return cudaGetLastError();
@@ -1460,6 +1495,152 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
     gemm_tc_kernel<128><<<nblocks, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo, args);
     note_launch();
   }
+  return cudaGetLastError();
+}
+
+struct TcGroupCache {
+  std::unordered_map<uint64_t, TcEntry*> tables;
+};
+
+TcGroupCache* tc_group_cache_new() { return new TcGroupCache(); }
+
+void tc_group_cache_free(TcGroupCache* c) {
+  if (!c) return;
+  for (auto& kv : c->tables) cudaFree(kv.second);
+  delete c;
+}
+
+namespace {
+inline uint64_t fnv_mix(uint64_t h, uint64_t x) {
+  for (int i = 0; i < 8; ++i) {
+    h ^= (x >> (8 * i)) & 0xff;
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+template <typename T>
+inline uint64_t bits_of(T v) {
+  uint64_t x = 0;
+  std::memcpy(&x, &v, sizeof(T) < 8 ? sizeof(T) : 8);
+  return x;
+}
+}  // namespace
+
+cudaError_t gemm_tc_group(cudaStream_t s, int n, const TcProblem* probs, int nprob, TcArgs shared,
+                          const TcTiles& tiles, TcGroupCache* cache) {
+  if (nprob < 1 || !cache) return cudaErrorInvalidValue;
+  if (n % 128 != 0 || n <= 0 || (shared.pairs != 1 && shared.pairs != 2)) return cudaErrorInvalidValue;
+  if (nprob == 1) {
+    TcArgs a = probs[0].epi;
+    a.nseg = shared.nseg;
+    a.pairs = shared.pairs;
+    a.sym = shared.sym;
+    a.bf16 = shared.bf16;
+    a.split_acc = shared.split_acc;
+    a.chunk_kb = shared.chunk_kb;
+    a.err = shared.err;
+    return gemm_tc(s, n, probs[0].Ahi, probs[0].Alo, probs[0].Bhi, probs[0].Blo, a, tiles);
+  }
+  const bool wide = (n % 256 == 0) && shared.bn != 128;
+  const int bn = wide ? 256 : 128;
+  // table key: the problems' operands and epilogue arguments (a table is rebuilt only when
+  // one of them changes)
+  uint64_t key = 1469598103934665603ull;
+  key = fnv_mix(key, (uint64_t)n * 1000003u + shared.nseg * 7 + shared.pairs * 31 + shared.sym * 131 +
+                         shared.bf16 * 521 + (uint64_t)bn * 7919);
+  key = fnv_mix(key, (uint64_t)(shared.sym ? (wide ? tiles.sym256 : tiles.sym128) : nullptr));
+  key = fnv_mix(key, (uint64_t)shared.err + (uint64_t)shared.chunk_kb);
+  for (int i = 0; i < nprob; ++i) {
+    const TcProblem& q = probs[i];
+    const TcArgs& e = q.epi;
+    const uint64_t w[] = {(uint64_t)q.Ahi, (uint64_t)q.Alo, (uint64_t)q.Bhi, (uint64_t)q.Blo, (uint64_t)e.E,
+                          (uint64_t)e.E2, (uint64_t)e.E64, (uint64_t)e.C64, (uint64_t)e.dvec, (uint64_t)e.C,
+                          (uint64_t)e.amax, (uint64_t)e.sa, (uint64_t)e.sb, bits_of(e.alpha), bits_of(e.beta),
+                          bits_of(e.beta2), bits_of(e.beta64), bits_of(e.diag), bits_of(e.dvec_scale),
+                          (uint64_t)e.e64_trans * 3 + (uint64_t)e.ndvec * 17 + (uint64_t)e.ldc * 65537};
+    for (uint64_t x : w) key = fnv_mix(key, x);
+  }
+  TcArgs a = shared;
+  a.n = n;
+  a.K = n;
+  a.tiles_n = n / bn;
+  int tiles_per;
+  if (a.sym) {
+    a.tile_list = wide ? tiles.sym256 : tiles.sym128;
+    tiles_per = wide ? tiles.n256 : tiles.n128;
+  } else {
+    a.tile_list = nullptr;
+    tiles_per = (n / BM) * (n / bn);
+  }
+  TcEntry* table = nullptr;
+  auto it = cache->tables.find(key);
+  if (it != cache->tables.end()) {
+    table = it->second;
+  } else {
+    std::vector<TcEntry> host(nprob);
+    for (int i = 0; i < nprob; ++i) {
+      const TcProblem& q = probs[i];
+      TcEntry& t = host[i];
+      const uint16_t* Alo = q.Alo ? q.Alo : q.Ahi;
+      const uint16_t* Blo = q.Blo ? q.Blo : q.Bhi;
+      if (!make_map(&t.map[0], q.Ahi, n, BM, shared.bf16) || !make_map(&t.map[1], Alo, n, BM, shared.bf16) ||
+          !make_map(&t.map[2], q.Bhi, n, bn, shared.bf16) || !make_map(&t.map[3], Blo, n, bn, shared.bf16))
+        return cudaErrorInvalidValue;
+      if (shared.pairs == 2) {
+        if (!make_map(&t.map[4], q.Bhi, n, BM, shared.bf16) || !make_map(&t.map[5], Blo, n, BM, shared.bf16) ||
+            !make_map(&t.map[6], q.Ahi, n, bn, shared.bf16) || !make_map(&t.map[7], Alo, n, bn, shared.bf16))
+          return cudaErrorInvalidValue;
+      } else {
+        t.map[4] = t.map[0];
+        t.map[5] = t.map[1];
+        t.map[6] = t.map[2];
+        t.map[7] = t.map[3];
+      }
+      // the problem's epilogue arguments, with the launch's shared fields (the epilogue reads
+      // sym, the kernel's walk n, K, nseg, pairs, ...)
+      t.args = q.epi;
+      t.args.n = a.n;
+      t.args.K = a.K;
+      t.args.nseg = a.nseg;
+      t.args.pairs = a.pairs;
+      t.args.sym = a.sym;
+      t.args.bf16 = a.bf16;
+      t.args.split_acc = a.split_acc;
+      t.args.chunk_kb = a.chunk_kb;
+      t.args.bn = a.bn;
+      t.args.tiles_n = a.tiles_n;
+      t.args.tile_list = a.tile_list;
+      t.args.err = a.err;
+    }
+    cudaError_t e = cudaMalloc((void**)&table, sizeof(TcEntry) * nprob);
+    if (e != cudaSuccess) return e;
+    // pageable source: the call returns once the bytes are staged, ordered on the stream
+    e = cudaMemcpyAsync(table, host.data(), sizeof(TcEntry) * nprob, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+      cudaFree(table);
+      return e;
+    }
+    cache->tables[key] = table;
+  }
+  const int ntiles = nprob * tiles_per;
+  const int grid = std::min(ntiles, sm_count());
+  // the launch's own maps are unused (every problem's maps come from the table)
+  CUtensorMap dummy;
+  std::memset(&dummy, 0, sizeof(dummy));
+  if (wide) {
+    const int sb = smem_bytes_persistent<256>();
+    const cudaError_t attr = ensure_smem(0, gemm_tc_persistent_kernel<256>, sb);
+    if (attr != cudaSuccess) return attr;
+    gemm_tc_persistent_kernel<256><<<grid, 192, sb, s>>>(dummy, dummy, dummy, dummy, dummy, dummy, dummy, dummy, a,
+                                                           ntiles, table, tiles_per);
+  } else {
+    const int sb = smem_bytes_persistent<128>();
+    const cudaError_t attr = ensure_smem(1, gemm_tc_persistent_kernel<128>, sb);
+    if (attr != cudaSuccess) return attr;
+    gemm_tc_persistent_kernel<128><<<grid, 192, sb, s>>>(dummy, dummy, dummy, dummy, dummy, dummy, dummy, dummy, a,
+                                                           ntiles, table, tiles_per);
+  }
+  note_launch();
   return cudaGetLastError();
 }
 

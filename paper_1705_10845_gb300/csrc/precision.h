@@ -46,6 +46,26 @@ struct MatSet {
 cudaError_t alloc_matset(MatSet& m, int prec, int np, int n, cudaStream_t s);
 void free_matset(MatSet& m);
 
+// One system's part of a grouped expansion or response chain (systems of one size np advanced
+// in lockstep; see Engine::foe_group, Engine::chain_group).
+struct FoeJob {
+  MatSet* m = nullptr;
+  const double* H = nullptr;
+  int N = 0;
+  double mu = 0.0;
+  const std::vector<int>* ns = nullptr;
+  const std::vector<double>* nc = nullptr;
+  double* stats = nullptr;
+  const double* dpar = nullptr;
+};
+struct ChainJob {
+  MatSet* m = nullptr;
+  const double* dvec = nullptr;
+  int N = 0;
+  double* out_diag = nullptr;
+  double* stats = nullptr;
+};
+
 class Engine {
  public:
   virtual ~Engine() {
@@ -118,6 +138,10 @@ class Engine {
   // A1 = T_k T1_k + T1_k T_k.  out_diag = diag(T1_n); full_last keeps T1_n in Tmu.
   virtual cudaError_t chain(cudaStream_t s, MatSet& m, const double* dvec, int N, bool full_last,
                             double* out_diag, double* stats) = 0;
+  // The same for several systems of one padded size (lockstep: the split engine runs each
+  // product over all of them in one grouped launch; the FP64 engine one after another).
+  virtual cudaError_t foe_group(cudaStream_t s, std::vector<FoeJob>& jobs, double sc);
+  virtual cudaError_t chain_group(cudaStream_t s, std::vector<ChainJob>& jobs, bool full_last);
   // out[0] = sum_{i<N} (T_n)_ii
   // Device flag that the tensor-core product sets when a bounded wait gives up or a
   // tile falls outside the matrix (null: this engine has none).
@@ -136,6 +160,8 @@ class Engine {
 
 Engine* make_engine(int prec);
 
+
+
 // split-precision engines (engine_split.cu)
 Engine* make_split_engine(int prec);
 cudaError_t alloc_matset_split(MatSet& m, cudaStream_t s);
@@ -143,6 +169,7 @@ void free_matset_split(MatSet& m);
 
 // tensor-core product self-test (engine_split.cu)
 int selftest_gemm(int n, int prec, int sym, double* result);
+int selftest_gemm_group(int n, int prec, int mode, int nprob, double* result);
 
 // FP64 eigenvalue-free entropy (entropy.cu)
 cudaError_t entropy_fp64(cudaStream_t s, int N, int np, int n, int n_sq, const double* T0,

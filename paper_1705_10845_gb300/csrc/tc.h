@@ -3,6 +3,7 @@
 #include <cstdint>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace xl {
@@ -12,6 +13,8 @@ struct TcArgs {
   int n = 0;                      // matrix size (set by gemm_tc)
   int split_acc = 0;              // one-CTA-per-tile kernel: 1 = the hi*hi K blocks split over both
                                   // accumulators (below)
+  int bn = 0;                     // grouped products: tile width 128 or 256 (0: 256 where n is a
+                                  // multiple of 256, else 128)
   int chunk_kb = 0;               // persistent kernel, split products: the hi*hi sum is accumulated in
                                   // chunks of this many K blocks, folded in FP32 (0: one chunk)
   int nseg = 3;                   // 1: hi only; 3: hi*hi + hi*lo + lo*hi
@@ -42,6 +45,22 @@ struct TcArgs {
   int* err = nullptr;             // set non-zero when a bounded wait gives up
 };
 
+// One problem of a grouped product launch, in device memory: its tensor maps (A hi, A lo, B hi,
+// B lo, and the swapped pair's A2 hi, A2 lo, B2 hi, B2 lo) and its epilogue arguments.  The
+// problems of a group share n, the segment and pair counts, the symmetric mode and the operand
+// type; they differ in their matrices and scalars.
+struct TcEntry {   // CUtensorMap's own alignment (64 bytes) aligns every entry
+  CUtensorMap map[8];
+  TcArgs args;
+};
+
+// One problem of a grouped product: operands and its epilogue arguments (n, K, nseg, pairs,
+// sym, bf16, chunk_kb and err come from the launch's shared arguments).
+struct TcProblem {
+  const uint16_t *Ahi = nullptr, *Alo = nullptr, *Bhi = nullptr, *Blo = nullptr;
+  TcArgs epi;
+};
+
 // Device tile lists of the symmetric-output products of one size n (pairs of ints (tm, tn)):
 // 128 x 128 tiles, 128 x 256 tiles (n a multiple of 256) and 256 x 256 tiles of the two-SM
 // products (n a multiple of 256; null: two-SM products are not used for this size).
@@ -58,6 +77,14 @@ struct TcTiles {
 // tc_sym_tiles_pair.
 cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* Alo, const uint16_t* Bhi,
                     const uint16_t* Blo, TcArgs args, const TcTiles& tiles);
+// Grouped product: the problems' tiles in one persistent launch (one-SM kernel).  The device
+// table of each distinct problem list is built once and kept in `cache` (key: the table's
+// bytes), so repeated groups upload nothing.
+struct TcGroupCache;
+TcGroupCache* tc_group_cache_new();
+void tc_group_cache_free(TcGroupCache* c);
+cudaError_t gemm_tc_group(cudaStream_t s, int n, const TcProblem* probs, int nprob, TcArgs shared,
+                          const TcTiles& tiles, TcGroupCache* cache);
 std::vector<int> tc_sym_tiles(int n, int bn);
 std::vector<int> tc_sym_tiles_pair(int n);
 void tc_forget_maps(const void* base);

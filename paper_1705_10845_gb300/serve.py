@@ -257,6 +257,76 @@ class Scheduler:
         return wall
 
 
+def padded_orbitals(natoms: int) -> int:
+    return (4 * natoms + 127) // 128 * 128
+
+
+def run_lockstep(X, jobs, workers: int, stream_factory=None, clock=time.perf_counter, max_group: int = 64):
+    """Batch of trajectories known up front, stepped in lockstep per size bucket.
+
+    Jobs with the same padded orbital count and temperature share one context (groups of at
+    most max_group systems); the library advances a context's systems together, one grouped
+    tensor-core launch per product over all of them.  Worker threads each step a share of the
+    bucket contexts on their own streams, so buckets overlap on the GPU.  Returns
+    (wall seconds, per-job-step latencies in seconds, job-steps done, errors)."""
+    import synth
+    buckets = {}
+    for j in jobs:
+        buckets.setdefault((padded_orbitals(j.natoms), j.Te, j.steps), []).append(j)
+    groups = []
+    for key in sorted(buckets, key=lambda k: -k[0] ** 3 * len(buckets[k])):
+        bj = buckets[key]
+        for i in range(0, len(bj), max_group):
+            groups.append(bj[i:i + max_group])
+    t0 = clock()
+    lat, errors = [], []
+    done = [0]
+    lock = threading.Lock()
+    # largest work first, spread over the workers
+    queues = [[] for _ in range(workers)]
+    load = [0.0] * workers
+    for g in groups:
+        w = min(range(workers), key=lambda i: load[i])
+        queues[w].append(g)
+        load[w] += work_estimate(g[0].natoms, squarings_for(g[0].Te), g[0].steps) * len(g)
+
+    def worker(w):
+        for g in queues[w]:
+            try:
+                stream = stream_factory(g[0]) if stream_factory else None
+                n_sq = squarings_for(g[0].Te)
+                p = X.default_params(Te=g[0].Te, n_sq=n_sq, rank_m=2, dt=0.25, mix_alpha=0.06,
+                                     kernel_c=1 - 1 / 0.06, prec=g[0].prec, scf_mode=1, kernel_auto=1,
+                                     scf_tol=1e-5, scf_max_iter=400, mu_tol=1e-3, rep_A=40.0, rep_rho=0.3,
+                                     kernel_prec=1, mu_prec=1)
+                systems = []
+                for j in g:
+                    sy = synth.make_system(j.natoms, j.seed)
+                    systems.append(dict(natoms=sy.natoms, L=sy.L, R=sy.R, V=sy.V, Z=sy.Z, mass=sy.mass))
+                ctx = X.Context(p, systems, stream=stream.cuda_stream if stream is not None else 0)
+                ctx.scf(-1)
+                for _ in range(g[0].steps):
+                    t = clock()
+                    ctx.step(1)
+                    dt = clock() - t
+                    with lock:
+                        lat.extend([dt] * len(g))
+                        done[0] += len(g)
+                for j in g:
+                    j.done_steps = j.steps
+                ctx.close()
+            except Exception as e:      # report and go on with the next bucket
+                with lock:
+                    errors.append(f"bucket of {len(g)} x {g[0].natoms}-ish atoms: {e}")
+
+    threads = [threading.Thread(target=worker, args=(w,), daemon=True) for w in range(workers)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    return clock() - t0, lat, done[0], errors
+
+
 def summarize(sched: Scheduler, wall: float):
     """Throughput and per-step latency over every admitted job (finished or still running)."""
     admitted = list(sched.finished) + [j for a in sched.active for j in a]
@@ -290,6 +360,9 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=1705)
     ap.add_argument("--policy", choices=["sjf", "fifo"], default="sjf", help="admission order of arrived jobs")
     ap.add_argument("--no-priority", action="store_true", help="all streams at the default priority")
+    ap.add_argument("--lockstep", action="store_true",
+                    help="batch mode: step the trajectories of each size bucket together in one context "
+                         "(grouped launches) instead of one context and stream per trajectory")
     a = ap.parse_args(argv)
 
     sys.path.insert(0, ROOT)
@@ -314,6 +387,25 @@ def main(argv=None):
             Te = 1000.0
         sched.submit(Job(arrival=t if a.mode == "serve" else 0.0, jid=i, natoms=nat, Te=Te, steps=a.steps,
                          seed=a.seed + i, prec=a.prec))
+    if a.mode == "batch" and a.lockstep:
+        jobs = [j for _, _, j in sorted(sched.pending)]
+        l0 = X.binding.launch_count()
+        wall, lat, steps, errors = run_lockstep(
+            X, jobs, min(a.workers, 8),
+            stream_factory=lambda job: torch.cuda.Stream(priority=0 if a.no_priority else stream_priority(job.natoms)))
+        torch.cuda.synchronize()
+        res = {"steps_per_s": steps / wall, "total_steps": steps, "wall_s": wall,
+               "atom_steps_per_s": sum(j.done_steps * j.natoms for j in jobs) / wall,
+               "jobs": len(jobs), "jobs_finished": sum(1 for j in jobs if j.done_steps >= j.steps),
+               "errors": errors[:5], "mode": "batch-lockstep", "prec": a.prec,
+               "atoms_range": [a.min_atoms, a.max_atoms], "steps_per_job": a.steps,
+               "gpu_launches": X.binding.launch_count() - l0}
+        if lat:
+            arr = np.array(lat) * 1000.0
+            res.update({"step_latency_ms_p50": float(np.percentile(arr, 50)),
+                        "step_latency_ms_p99": float(np.percentile(arr, 99))})
+        print(json.dumps(res), flush=True)
+        return 1 if errors else 0
     l0 = X.binding.launch_count()
     wall = sched.run(until=(a.duration + 60.0) if a.mode == "serve" else None,
                      stream_factory=lambda job: torch.cuda.Stream(

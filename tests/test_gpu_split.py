@@ -273,3 +273,16 @@ def test_graph_replay_matches_direct_launches(X):
             res[g] = [ctx.get(0, w) for w in (X.Q, X.R, X.NHIST, X.KR, X.F, X.STATS)]
     for a, b in zip(res[0], res[1]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("n", [256, 384, 1024])
+@pytest.mark.parametrize("sym", [0, 1, 2])
+@pytest.mark.parametrize("single", [False, True])
+def test_grouped_product_equals_single_launches(X, n, sym, single):
+    # the grouped launch of the lockstep batch path (several problems' tiles in one persistent
+    # launch, per-problem tensor maps and epilogue arguments from a device table, both tile
+    # widths as the autotuner tries them) computes every tile exactly as a single launch does
+    err, flag = X.binding.selftest_gemm_group(n, "fp16x3", sym, single=single, nprob=3)
+    print(n, sym, single, err)
+    assert flag == 0
+    assert err == 0.0
