@@ -762,6 +762,33 @@ xlbomd_status md_step(xlbomd_ctx* ctx, Sys& S, bool do_energy) {
   return XLBOMD_OK;
 }
 
+// The responses w_j = d q/d lambda along v_j of several systems of one padded size, their
+// chains as one grouped launch per product (v, w: one device vector per system).
+xlbomd_status response_group(xlbomd_ctx* ctx, const std::vector<Sys*>& G, const std::vector<const double*>& v,
+                             const std::vector<double*>& w) {
+  cudaStream_t st = ctx->stream;
+  const double sc = beta_of(ctx->p) / std::ldexp(1.0, ctx->p.n_sq + 1);
+  std::vector<ChainJob> cj;
+  for (size_t k = 0; k < G.size(); ++k) {
+    Sys& S = *G[k];
+    CK(gamma_apply(ctx, S, v[k], S.potv, S.work));
+    CK(launch_expand_potential(st, S.nat, S.np, -sc, S.potv, S.dvec));
+    ChainJob c;
+    c.m = &S.mats;
+    c.dvec = S.dvec;
+    c.N = S.N;
+    c.out_diag = S.d1;
+    c.stats = S.stats;
+    cj.push_back(c);
+  }
+  CK(ctx->eng->chain_group(st, cj, false));
+  for (size_t k = 0; k < G.size(); ++k) {
+    Sys& S = *G[k];
+    CK(launch_response_finish(st, S.nat, S.N, S.d1, S.dmu_diag, S.scal + 4, w[k]));
+  }
+  return XLBOMD_OK;
+}
+
 // Rank-m kernel update (kernel_mode 0) of several systems of one padded size in lockstep: probe
 // i of every system still probing runs as one grouped response chain, with one host
 // synchronisation per probe index for all of them.  Each system takes exactly the probes of
@@ -773,7 +800,6 @@ xlbomd_status kernel_update_group(xlbomd_ctx* ctx, const std::vector<Sys*>& G) {
     for (Sys* S : G) CKS(kernel_update(ctx, *S));
     return XLBOMD_OK;
   }
-  const double sc = beta_of(p) / std::ldexp(1.0, p.n_sq + 1);
   const size_t B = G.size();
   double* h = ctx->pinned_group;
   std::vector<int> m(B, 0);
@@ -789,26 +815,17 @@ xlbomd_status kernel_update_group(xlbomd_ctx* ctx, const std::vector<Sys*>& G) {
     std::vector<size_t> probing;
     for (size_t k = 0; k < active.size(); ++k)
       if (h[k] == 1.0) probing.push_back(active[k]);
-    std::vector<ChainJob> cj;
+    std::vector<Sys*> g;
+    std::vector<const double*> dv;
+    std::vector<double*> dw;
     for (size_t j : probing) {
       Sys& S = *G[j];
-      const double* vi = S.pV + (size_t)i * S.nat;
-      CK(gamma_apply(ctx, S, vi, S.potv, S.work));
-      CK(launch_expand_potential(st, S.nat, S.np, -sc, S.potv, S.dvec));
-      ChainJob c;
-      c.m = &S.mats;
-      c.dvec = S.dvec;
-      c.N = S.N;
-      c.out_diag = S.d1;
-      c.stats = S.stats;
-      cj.push_back(c);
-    }
-    CK(ctx->eng->chain_group(st, cj, false));
-    for (size_t j : probing) {
-      Sys& S = *G[j];
-      CK(launch_response_finish(st, S.nat, S.N, S.d1, S.dmu_diag, S.scal + 4, S.pW + (size_t)i * S.nat));
+      g.push_back(&S);
+      dv.push_back(S.pV + (size_t)i * S.nat);
+      dw.push_back(S.pW + (size_t)i * S.nat);
       m[j] = i + 1;
     }
+    if (!g.empty()) CKS(response_group(ctx, g, dv, dw));
     active.swap(probing);
   }
   for (size_t j = 0; j < B; ++j) {
@@ -817,6 +834,138 @@ xlbomd_status kernel_update_group(xlbomd_ctx* ctx, const std::vector<Sys*>& G) {
     S.probes_used = m[j];
     S.stats[2] = m[j];
   }
+  return XLBOMD_OK;
+}
+
+// stiffest_mode() of several systems in lockstep (one grouped response per power iteration)
+xlbomd_status stiffest_mode_group(xlbomd_ctx* ctx, const std::vector<Sys*>& G) {
+  cudaStream_t st = ctx->stream;
+  const size_t B = G.size();
+  std::vector<std::vector<double>> v(B), w(B);
+  std::vector<double> lam(B, 0.0);
+  std::vector<size_t> active;
+  for (size_t k = 0; k < B; ++k) {
+    Sys& S = *G[k];
+    v[k].resize(S.nat);
+    w[k].resize(S.nat);
+    for (int I = 0; I < S.nat; ++I) v[k][I] = ((I * 7919) % 17) - 8.0;
+    double mean = 0.0;
+    for (double x : v[k]) mean += x;
+    mean /= S.nat;
+    double nv = 0.0;
+    for (double& x : v[k]) {
+      x -= mean;
+      nv += x * x;
+    }
+    nv = std::sqrt(nv);
+    if (nv == 0.0) continue;
+    for (double& x : v[k]) x /= nv;
+    active.push_back(k);
+  }
+  for (int it = 0; it < 12 && !active.empty(); ++it) {
+    std::vector<Sys*> g;
+    std::vector<const double*> dv;
+    std::vector<double*> dw;
+    for (size_t k : active) {
+      Sys& S = *G[k];
+      double* pv = S.pV + (size_t)kMaxRank * S.nat;   // spare probe rows
+      double* pw = S.pW + (size_t)kMaxRank * S.nat;
+      CK(cudaMemcpyAsync(pv, v[k].data(), sizeof(double) * S.nat, cudaMemcpyHostToDevice, st));
+      g.push_back(&S);
+      dv.push_back(pv);
+      dw.push_back(pw);
+    }
+    CKS(response_group(ctx, g, dv, dw));
+    for (size_t j = 0; j < active.size(); ++j)
+      CK(cudaMemcpyAsync(w[active[j]].data(), dw[j], sizeof(double) * g[j]->nat, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<size_t> next;
+    for (size_t k : active) {
+      const int nat = G[k]->nat;
+      double dot = 0.0, nw = 0.0;
+      for (int I = 0; I < nat; ++I) {
+        dot += v[k][I] * w[k][I];
+        nw += w[k][I] * w[k][I];
+      }
+      nw = std::sqrt(nw);
+      lam[k] = dot;
+      if (!(nw > 0.0) || !std::isfinite(nw)) continue;
+      for (int I = 0; I < nat; ++I) v[k][I] = w[k][I] / nw;
+      next.push_back(k);
+    }
+    active.swap(next);
+  }
+  for (size_t k = 0; k < B; ++k) {
+    if (lam[k] < 0.0) G[k]->kc = 1.2 * lam[k];
+    if (debug_enabled()) std::fprintf(stderr, "[xlbomd] stiffest mode %.4f -> c = %.4f\n", lam[k], G[k]->kc);
+  }
+  return XLBOMD_OK;
+}
+
+// t0 SCF of several systems of one padded size in lockstep: each takes exactly the iterations
+// of scf(), with the densities, the stiffest-mode search and the kernel updates grouped.
+xlbomd_status scf_group(xlbomd_ctx* ctx, const std::vector<Sys*>& G) {
+  cudaStream_t st = ctx->stream;
+  const xlbomd_params& p = ctx->p;
+  const size_t B = G.size();
+  std::vector<double> best(B, HUGE_VAL);
+  std::vector<int> since_best(B, 0);
+  std::vector<size_t> active(B);
+  for (size_t k = 0; k < B; ++k) active[k] = k;
+  double* h = ctx->pinned_group;
+  for (int it = 0; it < p.scf_max_iter && !active.empty(); ++it) {
+    std::vector<Sys*> g;
+    for (size_t k : active) {
+      Sys& S = *G[k];
+      CK(gamma_apply(ctx, S, S.nh, S.pot, S.work));
+      CK(launch_apply_potential(st, S.nat, S.np, S.H0, S.pot, S.H));
+      g.push_back(&S);
+    }
+    CKS(density_group(ctx, g, false));
+    if (it == 0 && p.kernel_auto) CKS(stiffest_mode_group(ctx, g));
+    for (size_t j = 0; j < g.size(); ++j) {
+      CK(launch_absmax(st, g[j]->nat, g[j]->r, g[j]->scal + 9));
+      CK(cudaMemcpyAsync(h + j, g[j]->scal + 9, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    std::vector<size_t> next;
+    std::vector<Sys*> converged, going;
+    for (size_t j = 0; j < g.size(); ++j) {
+      const size_t k = active[j];
+      Sys& S = *G[k];
+      const double res = h[j];
+      if (debug_enabled()) std::fprintf(stderr, "[xlbomd] scf it %d system %zu max|q - n| %.3e mu %.8f\n", it, k, res, S.mu);
+      if (!std::isfinite(res) || res > 1e3) return fail(ctx, XLBOMD_ERR_DIVERGED, "t0 SCF diverged");
+      if (res < 0.9 * best[k]) {
+        best[k] = res;
+        since_best[k] = 0;
+      } else {
+        ++since_best[k];
+      }
+      const bool floor = p.prec != XLBOMD_FP64 && since_best[k] >= 4 && res < 100.0 * p.scf_tol;
+      if (res < p.scf_tol || floor) {
+        CK(launch_fill_history(st, S.nat, p.kmax, S.nh));
+        CK(launch_forces(st, model_of(p), S.nat, S.L, S.eta, S.ng, S.G4, S.R, S.Dm, S.np, S.q, S.nh, S.F, S.work,
+                         p.prec != XLBOMD_FP64));
+        S.have_K = false;   // exact or accumulated kernel: start again at the t0 state
+        converged.push_back(&S);
+      } else {
+        going.push_back(&S);
+        next.push_back(k);
+      }
+    }
+    if (!converged.empty()) CKS(kernel_update_group(ctx, converged));
+    if (!going.empty()) {
+      if (p.scf_mode == 1 && p.rank_m > 0) {
+        CKS(kernel_update_group(ctx, going));            // n <- n - K_m r (Eq. SCF_K)
+        for (Sys* S : going) CK(launch_axpy(st, S->nat, -1.0, S->Kr, S->nh));
+      } else {
+        for (Sys* S : going) CK(launch_axpy(st, S->nat, p.mix_alpha, S->r, S->nh));
+      }
+    }
+    active.swap(next);
+  }
+  if (!active.empty()) return fail(ctx, XLBOMD_ERR_NOT_CONVERGED, "t0 SCF did not converge");
   return XLBOMD_OK;
 }
 
@@ -1126,9 +1275,20 @@ xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* syst
 xlbomd_status xlbomd_scf(xlbomd_ctx* ctx, int sys) {
   if (!ctx) return XLBOMD_ERR_ARG;
   const int lo = sys < 0 ? 0 : sys, hi = sys < 0 ? (int)ctx->sys.size() : sys + 1;
-  for (int i = lo; i < hi; ++i) {
-    CKS(check(ctx, i));
-    CKS(scf(ctx, ctx->sys[i]));
+  for (int i = lo; i < hi; ++i) CKS(check(ctx, i));
+  if (hi - lo == 1) return scf(ctx, ctx->sys[lo]);
+  // every system: those of one padded size in lockstep
+  std::vector<int> sizes;
+  for (const Sys& S : ctx->sys)
+    if (std::find(sizes.begin(), sizes.end(), S.np) == sizes.end()) sizes.push_back(S.np);
+  for (int np : sizes) {
+    std::vector<Sys*> G;
+    for (Sys& S : ctx->sys)
+      if (S.np == np) G.push_back(&S);
+    if (G.size() == 1)
+      CKS(scf(ctx, *G[0]));
+    else
+      CKS(scf_group(ctx, G));
   }
   return XLBOMD_OK;
 }

@@ -266,9 +266,11 @@ def run_lockstep(X, jobs, workers: int, stream_factory=None, clock=time.perf_cou
 
     Jobs with the same padded orbital count and temperature share one context (groups of at
     most max_group systems); the library advances a context's systems together, one grouped
-    tensor-core launch per product over all of them.  Worker threads each step a share of the
-    bucket contexts on their own streams, so buckets overlap on the GPU.  Returns
-    (wall seconds, per-job-step latencies in seconds, job-steps done, errors)."""
+    tensor-core launch per product over all of them.  Two phases: every worker first builds
+    its bucket contexts and their t0 ground states (SCF), then all workers step their buckets
+    round-robin, one MD step per bucket in turn, each worker on its own streams, so buckets
+    overlap on the GPU.  Returns a dict: setup and MD wall seconds, job-steps done, per-job-step
+    latencies (seconds) and errors."""
     import synth
     buckets = {}
     for j in jobs:
@@ -278,7 +280,6 @@ def run_lockstep(X, jobs, workers: int, stream_factory=None, clock=time.perf_cou
         bj = buckets[key]
         for i in range(0, len(bj), max_group):
             groups.append(bj[i:i + max_group])
-    t0 = clock()
     lat, errors = [], []
     done = [0]
     lock = threading.Lock()
@@ -289,6 +290,8 @@ def run_lockstep(X, jobs, workers: int, stream_factory=None, clock=time.perf_cou
         w = min(range(workers), key=lambda i: load[i])
         queues[w].append(g)
         load[w] += work_estimate(g[0].natoms, squarings_for(g[0].Te), g[0].steps) * len(g)
+    ctxs = [[] for _ in range(workers)]
+    barrier = threading.Barrier(workers + 1)
 
     def worker(w):
         for g in queues[w]:
@@ -305,26 +308,46 @@ def run_lockstep(X, jobs, workers: int, stream_factory=None, clock=time.perf_cou
                     systems.append(dict(natoms=sy.natoms, L=sy.L, R=sy.R, V=sy.V, Z=sy.Z, mass=sy.mass))
                 ctx = X.Context(p, systems, stream=stream.cuda_stream if stream is not None else 0)
                 ctx.scf(-1)
-                for _ in range(g[0].steps):
+                ctxs[w].append((g, ctx, stream))
+            except Exception as e:      # report and go on with the next bucket
+                with lock:
+                    errors.append(f"bucket of {len(g)} x {g[0].natoms}-ish atoms (set-up): {e}")
+        barrier.wait()                  # every context built: the MD phase starts together
+        barrier.wait()
+        live = list(ctxs[w])
+        while live:
+            for item in list(live):
+                g, ctx, _ = item
+                try:
                     t = clock()
                     ctx.step(1)
                     dt = clock() - t
                     with lock:
                         lat.extend([dt] * len(g))
                         done[0] += len(g)
-                for j in g:
-                    j.done_steps = j.steps
-                ctx.close()
-            except Exception as e:      # report and go on with the next bucket
-                with lock:
-                    errors.append(f"bucket of {len(g)} x {g[0].natoms}-ish atoms: {e}")
+                    for j in g:
+                        j.done_steps += 1
+                    if g[0].done_steps >= g[0].steps:
+                        live.remove(item)
+                        ctx.close()
+                except Exception as e:
+                    with lock:
+                        errors.append(f"bucket of {len(g)} x {g[0].natoms}-ish atoms: {e}")
+                    live.remove(item)
+                    ctx.close()
 
     threads = [threading.Thread(target=worker, args=(w,), daemon=True) for w in range(workers)]
+    t0 = clock()
     for t in threads:
         t.start()
+    barrier.wait()
+    t1 = clock()
+    barrier.wait()
     for t in threads:
         t.join()
-    return clock() - t0, lat, done[0], errors
+    t2 = clock()
+    return {"setup_s": t1 - t0, "md_s": t2 - t1, "steps": done[0], "lat": lat, "errors": errors,
+            "contexts": len(groups)}
 
 
 def summarize(sched: Scheduler, wall: float):
@@ -390,13 +413,16 @@ def main(argv=None):
     if a.mode == "batch" and a.lockstep:
         jobs = [j for _, _, j in sorted(sched.pending)]
         l0 = X.binding.launch_count()
-        wall, lat, steps, errors = run_lockstep(
+        r = run_lockstep(
             X, jobs, min(a.workers, 8),
             stream_factory=lambda job: torch.cuda.Stream(priority=0 if a.no_priority else stream_priority(job.natoms)))
         torch.cuda.synchronize()
-        res = {"steps_per_s": steps / wall, "total_steps": steps, "wall_s": wall,
-               "atom_steps_per_s": sum(j.done_steps * j.natoms for j in jobs) / wall,
-               "jobs": len(jobs), "jobs_finished": sum(1 for j in jobs if j.done_steps >= j.steps),
+        steps, errors, lat = r["steps"], r["errors"], r["lat"]
+        res = {"steps_per_s": steps / r["md_s"], "total_steps": steps, "md_s": r["md_s"], "setup_s": r["setup_s"],
+               "steps_per_s_with_setup": steps / (r["md_s"] + r["setup_s"]),
+               "atom_steps_per_s": sum(j.done_steps * j.natoms for j in jobs) / r["md_s"],
+               "jobs": len(jobs), "contexts": r["contexts"],
+               "jobs_finished": sum(1 for j in jobs if j.done_steps >= j.steps),
                "errors": errors[:5], "mode": "batch-lockstep", "prec": a.prec,
                "atoms_range": [a.min_atoms, a.max_atoms], "steps_per_job": a.steps,
                "gpu_launches": X.binding.launch_count() - l0}
