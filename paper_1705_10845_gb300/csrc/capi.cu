@@ -38,6 +38,10 @@ struct Sys {
   double *ddiag = nullptr, *dmu_diag = nullptr, *d1 = nullptr, *dvec = nullptr, *dvec_mu = nullptr;
   double *pV = nullptr, *pW = nullptr, *scal = nullptr, *work = nullptr, *energy = nullptr;
   double *Kfull = nullptr, *Jm = nullptr;   // exact kernel (natoms x natoms) and its work matrix
+  // exact kernel, split precisions: chain slots for probes run side by side, and per slot the
+  // probe v, response w, potential, diagonal perturbation, chain diagonal and scratch
+  std::vector<MatSet> slots;
+  double* slot_vec = nullptr;
   MatSet mats;   // expansion matrices in the working precision
   // host
   double mu = 0.0;
@@ -537,6 +541,58 @@ xlbomd_status response(xlbomd_ctx* ctx, Sys& S, const double* v, double* w) {
   return XLBOMD_OK;
 }
 
+// Columns of J - I for the exact kernel with the unit-probe responses run side by side: up
+// to 64 probes at a time, each in its own chain slot, every chain product one grouped launch
+// over the probes.  The number of slots is bounded by a quarter of the free device memory.
+xlbomd_status exact_columns_grouped(xlbomd_ctx* ctx, Sys& S) {
+  cudaStream_t st = ctx->stream;
+  const double sc = beta_of(ctx->p) / std::ldexp(1.0, ctx->p.n_sq + 1);
+  const size_t per_vec = 2 * (size_t)S.nat + 3 * (size_t)S.np + (size_t)S.kp + 64;   // v, w, potv?, ...
+  if (S.slots.empty()) {
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const size_t per_slot = chain_slot_bytes(S.np) + per_vec * sizeof(double);
+    int G = (int)std::min<size_t>(64, std::max<size_t>(1, free_b / 4 / per_slot));
+    G = std::min(G, S.nat);
+    S.slots.resize(G);
+    for (int j = 0; j < G; ++j)
+      if (alloc_chain_slot(S.slots[j], S.mats, st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, XLBOMD_ERR_OOM, "exact kernel: chain slot allocation failed");
+      }
+    CKS(dalloc(ctx, &S.slot_vec, per_vec * G));
+  }
+  const int G = (int)S.slots.size();
+  auto vec = [&](int j, int what) -> double* {   // 0 v, 1 w, 2 potv, 3 dvec, 4 d1, 5 scal, 6 tmp
+    double* b = S.slot_vec + per_vec * (size_t)j;
+    const size_t off[7] = {0, (size_t)S.nat, 2 * (size_t)S.nat, 2 * (size_t)S.nat + S.np,
+                           2 * (size_t)S.nat + 2 * (size_t)S.np, 2 * (size_t)S.nat + 3 * (size_t)S.np,
+                           2 * (size_t)S.nat + 3 * (size_t)S.np + 32};
+    return b + off[what];
+  };
+  for (int I0 = 0; I0 < S.nat; I0 += G) {
+    const int g = std::min(G, S.nat - I0);
+    std::vector<ChainJob> cj(g);
+    for (int j = 0; j < g; ++j) {
+      CK(launch_unit_vector(st, S.nat, I0 + j, vec(j, 0)));
+      CK(launch_gamma_apply(st, S.nat, S.gam, S.natp, S.SF, S.kp, ctx->p.coulomb_k, vec(j, 0), vec(j, 2),
+                            vec(j, 6)));
+      CK(launch_expand_potential(st, S.nat, S.np, -sc, vec(j, 2), vec(j, 3)));
+      cj[j].m = &S.slots[j];
+      cj[j].dvec = vec(j, 3);
+      cj[j].N = S.N;
+      cj[j].out_diag = vec(j, 4);
+      cj[j].stats = S.stats;
+    }
+    CK(ctx->eng->chain_group(st, cj, false));
+    for (int j = 0; j < g; ++j) {
+      CK(launch_response_finish(st, S.nat, S.N, vec(j, 4), S.dmu_diag, vec(j, 5), vec(j, 1)));
+      CK(launch_jacobian_column(st, S.nat, I0 + j, vec(j, 1), S.Jm, S.Kfull));
+    }
+  }
+  return XLBOMD_OK;
+}
+
 // a7-a8
 // Exact kernel K = (J - I)^-1 (Eq. KK): J column by column from the responses to the
 // unit directions e_I, then Gauss-Jordan with partial pivoting in FP64.
@@ -546,12 +602,16 @@ xlbomd_status kernel_exact(xlbomd_ctx* ctx, Sys& S) {
   const size_t nn = (size_t)S.nat * S.nat;
   if (!S.Kfull) CKS(dalloc(ctx, &S.Kfull, nn));
   if (!S.Jm) CKS(dalloc(ctx, &S.Jm, nn));
-  double* v = S.pV + (size_t)kMaxRank * S.nat;   // spare probe rows
-  double* w = S.pW + (size_t)kMaxRank * S.nat;
-  for (int I = 0; I < S.nat; ++I) {
-    CK(launch_unit_vector(st, S.nat, I, v));
-    CKS(response(ctx, S, v, w));
-    CK(launch_jacobian_column(st, S.nat, I, w, S.Jm, S.Kfull));
+  if (ctx->p.prec != XLBOMD_FP64 && S.nat > 1) {
+    CKS(exact_columns_grouped(ctx, S));
+  } else {
+    double* v = S.pV + (size_t)kMaxRank * S.nat;   // spare probe rows
+    double* w = S.pW + (size_t)kMaxRank * S.nat;
+    for (int I = 0; I < S.nat; ++I) {
+      CK(launch_unit_vector(st, S.nat, I, v));
+      CKS(response(ctx, S, v, w));
+      CK(launch_jacobian_column(st, S.nat, I, w, S.Jm, S.Kfull));
+    }
   }
   CK(cudaMemsetAsync(S.scal + 10, 0, sizeof(double), st));
   CK(launch_gauss_jordan(st, S.nat, S.Jm, S.Kfull, S.work, S.scal + 10));
@@ -1014,6 +1074,10 @@ void free_sys(Sys& S) {
   for (auto& g : S.graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   S.graphs.clear();
+  for (MatSet& m : S.slots) free_chain_slot(m);
+  S.slots.clear();
+  if (S.slot_vec) cudaFree(S.slot_vec);
+  S.slot_vec = nullptr;
   free_matset(S.mats);
 }
 

@@ -1109,6 +1109,43 @@ cudaError_t alloc_matset_split(MatSet& m, cudaStream_t s) {
   return cudaSuccess;
 }
 
+// A chain slot: a view of a system's expansion matrices (T_k, W_k shared) with its own
+// response-chain matrices (A1, M, T1 twice, T_mu) and their scalars, so that several probes of
+// one system can run their chains side by side (grouped launches).
+cudaError_t alloc_chain_slot(MatSet& slot, const MatSet& base, cudaStream_t s) {
+  slot = base;
+  slot.e64[0] = slot.e64[1] = slot.e64[2] = slot.e64[3] = slot.e64[4] = slot.e64[5] = slot.e64[6] = nullptr;
+  const int np = base.np;
+  float* scal = nullptr;
+  RET(cudaMalloc((void**)&scal, sizeof(float) * 2 * 5));
+  RET(cudaMemsetAsync(scal, 0, sizeof(float) * 2 * 5, s));
+  slot.tc_plan = scal;
+  slot.sA1 = SplitMat();
+  slot.sMt = SplitMat();
+  slot.sT1a = SplitMat();
+  slot.sT1b = SplitMat();
+  slot.sTmu = SplitMat();
+  unsigned* su = reinterpret_cast<unsigned*>(scal + 5);
+  RET(alloc_split(slot.sA1, np, scal + 0, su + 0, kF, s));
+  RET(alloc_split(slot.sMt, np, scal + 1, su + 1, kD | kF, s));
+  RET(alloc_split(slot.sT1a, np, scal + 2, su + 2, kD | kF, s));
+  RET(alloc_split(slot.sT1b, np, scal + 3, su + 3, kD | kF, s));
+  RET(alloc_split(slot.sTmu, np, scal + 4, su + 4, kD, s));
+  return cudaSuccess;
+}
+
+void free_chain_slot(MatSet& slot) {
+  SplitMat* w[] = {&slot.sA1, &slot.sMt, &slot.sT1a, &slot.sT1b, &slot.sTmu};
+  for (SplitMat* x : w) free_split(*x);
+  if (slot.tc_plan) cudaFree(slot.tc_plan);
+  slot.tc_plan = nullptr;
+  slot.sT.clear();
+  slot.sY.clear();
+}
+
+// bytes of one chain slot of size np
+size_t chain_slot_bytes(int np) { return (size_t)np * np * (8 + 3 * 16 + 12); }
+
 void free_matset_split(MatSet& m) {
   for (auto& x : m.sT) free_split(x);
   for (auto& x : m.sY) free_split(x);

@@ -165,6 +165,10 @@ Engine* make_engine(int prec);
 // split-precision engines (engine_split.cu)
 Engine* make_split_engine(int prec);
 cudaError_t alloc_matset_split(MatSet& m, cudaStream_t s);
+// response-chain slots of a split-precision system (grouped probes of one system)
+cudaError_t alloc_chain_slot(MatSet& slot, const MatSet& base, cudaStream_t s);
+void free_chain_slot(MatSet& slot);
+size_t chain_slot_bytes(int np);
 void free_matset_split(MatSet& m);
 
 // tensor-core product self-test (engine_split.cu)

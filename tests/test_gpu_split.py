@@ -286,3 +286,34 @@ def test_grouped_product_equals_single_launches(X, n, sym, single):
     print(n, sym, single, err)
     assert flag == 0
     assert err == 0.0
+
+
+@pytest.mark.parametrize("kernel_prec,tol", [(0, 1e-4), (1, 2e-3)])
+def test_grouped_exact_kernel_256_atoms(X, kernel_prec, tol):
+    # the exact kernel K = (J - I)^-1 (Eq. KK) of a 256-atom system: its 256 unit-probe response
+    # chains run up to 64 at a time in chain slots of their own, every chain product one grouped
+    # launch; K against the oracle's eigenbasis kernel, and the cost of one recompute
+    import time
+    s = synth.make_system(256, 31)
+    p = X.default_params(mix_alpha=ALPHA_MIX, kernel_c=1 - 1 / ALPHA_MIX, prec="fp16x3", mu_tol=1e-3,
+                         kernel_mode=1, kernel_prec=kernel_prec)
+    m = O.Model(Te=p.Te, n_sq=p.n_sq)
+    rng = np.random.default_rng(9)
+    n = rng.normal(scale=0.01, size=s.natoms)
+    n -= n.mean()
+    ev = O.evaluate(s.R, s.L, s.Z, n, m, None, with_kernel=False, with_forces=False)
+    Kref = O.kernel_exact(ev.dens, ev.gamma)
+    with X.Context(p, [sysdict(s)]) as ctx:
+        ctx.set(0, X.N, n)
+        ctx.set(0, X.MU, [ev.dens.mu])
+        ctx.build_H(0)
+        ctx.density(0)
+        ctx.kernel_exact(0)           # allocates the chain slots
+        ctx.get(0, X.MU)
+        t = time.perf_counter()
+        ctx.kernel_exact(0)
+        K = ctx.get(0, X.KMAT)
+        dt = time.perf_counter() - t
+    err = np.max(np.abs(K - Kref)) / np.abs(Kref).max()
+    print("exact kernel 256 atoms, kernel_prec", kernel_prec, "rel err", err, "recompute s", dt)
+    assert err < tol
