@@ -135,3 +135,53 @@ def test_summary_counts_jobs_still_running():
     res = serve.summarize(sch, 1.0)
     assert res["total_steps"] == 4 and res["jobs_admitted"] == 1 and res["jobs_finished"] == 0
     assert res["step_latency_ms_p50"] == pytest.approx(10.0)
+
+
+class FakeLockstepX:
+    """Stand-in for the binding in run_lockstep: records each context's systems and steps."""
+
+    contexts = []
+
+    class Context:
+        def __init__(self, p, systems, stream=0):
+            self.systems = [s["natoms"] for s in systems]
+            self.steps = 0
+            self.scf_calls = []
+            self.closed = False
+            FakeLockstepX.contexts.append(self)
+
+        def scf(self, sys):
+            self.scf_calls.append(sys)
+
+        def step(self, n):
+            self.steps += n
+            time.sleep(0.0002)
+
+        def close(self):
+            self.closed = True
+
+    @staticmethod
+    def default_params(**kw):
+        return kw
+
+
+def test_lockstep_buckets_by_padded_size_and_steps_every_job():
+    # run_lockstep groups jobs by padded orbital count (and temperature), at most max_group per
+    # context, builds every context's ground state (scf over all systems) before the MD phase,
+    # and steps each context exactly its jobs' step count; every job-step is counted once
+    FakeLockstepX.contexts = []
+    sizes = [32, 33, 40, 63, 64, 65, 100, 128, 129, 200, 31, 32]
+    jobs = [serve.Job(arrival=0.0, jid=i, natoms=n, Te=1000.0, steps=7, seed=i) for i, n in enumerate(sizes)]
+    r = serve.run_lockstep(FakeLockstepX, jobs, workers=3, max_group=2)
+    assert not r["errors"]
+    assert r["steps"] == 7 * len(jobs) and len(r["lat"]) == 7 * len(jobs)
+    assert all(j.done_steps == 7 for j in jobs)
+    ctxs = FakeLockstepX.contexts
+    assert len(ctxs) == r["contexts"]
+    for c in ctxs:
+        assert c.steps == 7 and c.closed and c.scf_calls == [-1]
+        assert len(c.systems) <= 2
+        assert len({serve.padded_orbitals(n) for n in c.systems}) == 1
+    # every job in exactly one context
+    assert sorted(n for c in ctxs for n in c.systems) == sorted(sizes)
+    assert r["setup_s"] >= 0 and r["md_s"] > 0
