@@ -81,23 +81,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-// The same with each try suspending the thread for at most kSuspendNs: the waits of the
-// producer and MMA threads, which hand the operand ring's stages to each other (MMA completion
-// -> empty -> producer -> full -> MMA thread).  With the default suspension those hand-offs left
-// the tensor pipe idle a third of the time (a split product at n = 16384: 20.8 ms, 14.8 ms with
-// the hint, the same as with no waits at all).  The epilogue warps keep the default: polling
-// from them takes issue slots from the two single-thread loops on the sub-partitions they share.
-constexpr uint32_t kSuspendNs = 20;
+// The same without suspending (mbarrier.test_wait in a bounded spin): the waits of the producer
+// and MMA threads, which hand the operand ring's stages to each other (MMA completion -> empty
+// -> producer -> full -> MMA thread).  With the default suspension those hand-offs cost about
+// 20 % of a product (n = 8192 split product: 2.46 ms with the hand-off and no operand loads at
+// all, 2.01 ms with neither), and the spin closes that gap (no loads: 1.92 ms; with loads 2.21
+// against 2.26 ms with a 20 ns suspend hint).  The epilogue warps keep the suspending wait:
+// polling from them would take issue slots from the two single-thread loops on the
+// sub-partitions they share.
 __device__ __forceinline__ bool mbar_wait_fast(uint64_t* bar, uint32_t parity) {
   const uint32_t a = smem_u32(bar);
-  for (int it = 0; it < kWaitLimit; ++it) {
+  for (int it = 0; it < (kWaitLimit << 4); ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(a), "r"(parity), "r"(kSuspendNs)
+        : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
   }
