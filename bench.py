@@ -40,7 +40,7 @@ ALPHA_MIX = 0.06
 # DRAM bytes (read + write) per launch of the product kernel, averaged over the launches of one
 # MD step, keyed by (variant, padded orbital count), from the ncu captures summarised in profiles/;
 # a workload or kernel without a capture since the kernel last changed reports null
-GEMM_TRAFFIC = {("persistent", 16384): 3451.98e9 / 233}   # xlbomd_step_4096atoms_fp16x3_launches.md
+GEMM_TRAFFIC = {("persistent", 16384): 3450.66e9 / 233}   # xlbomd_step_4096atoms_fp16x3_launches.md
 
 
 def gemm_variant():
