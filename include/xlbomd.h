@@ -182,7 +182,9 @@ xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* syst
 /* t0 ground state of system sys (Eq. IBC): SCF to max|q - n| < scf_tol by
  * linear mixing n <- n + mix_alpha (q[n] - n) (Eq. SCF_K with K_0, scf_mode 0)
  * or by n <- n - K_m (q[n] - n) with the rank-m kernel (Eq. SCF_K, scf_mode 1);
- * then n-history = n(t0), forces and K r at t0.  sys = -1: every system.
+ * then n-history = n(t0), forces and K r at t0.  sys = -1: every system, those
+ * of one padded orbital count in lockstep (grouped densities, stiffest-mode
+ * search and kernel updates; each system takes its one-system iterations).
  * Split precisions also stop at the rounding floor of their products: when
  * max|q - n| is below 100 scf_tol and has not fallen by 10% in 4 iterations.
  * Errors: ERR_NOT_CONVERGED (scf_max_iter spent), ERR_DIVERGED (non-finite or
@@ -243,6 +245,10 @@ xlbomd_status xlbomd_kernel_update(xlbomd_ctx* ctx, int sys);
  * Gauss-Jordan elimination with partial pivoting.  Costs natoms responses.
  * The kernel is held in the context (XLBOMD_KMAT) and used by
  * xlbomd_kernel_update, xlbomd_scf and xlbomd_step when kernel_mode = 1.
+ * Split precisions run the unit-probe response chains up to 64 at a time, each
+ * in a chain slot of its own (response-chain matrices, allocated on the first
+ * call within a quarter of the free device memory and kept by the context),
+ * every chain product one grouped launch over the probes.
  * Requires xlbomd_density on the same state.  Errors: ERR_ARG (no density),
  * ERR_NOT_CONVERGED (J - I numerically singular), ERR_OOM. */
 xlbomd_status xlbomd_kernel_exact(xlbomd_ctx* ctx, int sys);
@@ -256,7 +262,16 @@ xlbomd_status xlbomd_kernel_exact(xlbomd_ctx* ctx, int sys);
  * stream.  Errors: ERR_ARG (no density), ERR_CUDA. */
 xlbomd_status xlbomd_energy(xlbomd_ctx* ctx, int sys);
 
-/* a1-a10 for every system, nsteps times (Eqs. Integration, VRL_Damp). */
+/* a1-a10 for every system, nsteps times (Eqs. Integration, VRL_Damp).  The
+ * systems of the context that share a padded orbital count advance in
+ * lockstep: their expansions, chemical-potential chains and probe chains run
+ * as grouped tensor-core launches over all of them (split precisions), with
+ * one stream synchronisation per chemical-potential pass and per probe index
+ * for the whole group; a padded size held by one system takes the one-system
+ * step.  Every system follows exactly its one-system trajectory (same mu
+ * search, Newton-Schulz plan and probes; bitwise the same results).  Errors:
+ * ERR_DIVERGED (max |q - n| above diverge_tol for any system), and those of
+ * xlbomd_density and xlbomd_kernel_update. */
 xlbomd_status xlbomd_step(xlbomd_ctx* ctx, int nsteps);
 
 /* Copy a quantity to host memory (synchronises the stream). */
