@@ -37,6 +37,7 @@ if ROOT not in sys.path:
 
 METRIC = "XL-BOMD steps/s and FOE TFLOP/s vs peak, mixed vs FP64 GPU at |dq|<=1e-5 e"
 ALPHA_MIX = 0.06
+TF32_PER_BF16 = 1.1 / 2.25   # nominal dense tensor rates of GB300 (PFLOP/s): tf32 1.1, bf16 2.25
 # DRAM bytes (read + write) per launch of the product kernel, averaged over the launches of one
 # MD step, keyed by (variant, padded orbital count), from the ncu captures summarised in profiles/;
 # a workload or kernel without a capture since the kernel last changed reports null
@@ -54,7 +55,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp16x3", choices=["fp16x3", "bf16x3", "fp64"])
+    ap.add_argument("--prec", default="fp16x3", choices=["fp16x3", "bf16x3", "tf32x3", "fp64"])
     ap.add_argument("--natoms", type=int, default=4096)
     ap.add_argument("--Te", type=float, default=1000.0)
     ap.add_argument("--nsq", type=int, default=10)
@@ -80,7 +81,7 @@ def parse():
                          "F and Omega at the GPU's (R, n); prints one JSON line")
     ap.add_argument("--energy-every", type=int, default=10)
     ap.add_argument("--precision-study", default="",
-                    help="comma-separated precisions (e.g. fp16x3,bf16x3): at the t0 state of the first, "
+                    help="comma-separated precisions (e.g. fp16x3,bf16x3,tf32x3): at the t0 state of the first, "
                          "each evaluates q, F and Omega against one oracle evaluation of the same (R, n), "
                          "then times --steps MD steps; prints one JSON line")
     ap.add_argument("--batch", action="store_true",
@@ -610,7 +611,9 @@ def main():
     bf, bf_sus, hbm, src = peaks()
     gemm_launches, gemm_ms, gemm_flops = prof
     achieved = gemm_flops / (gemm_ms / 1000.0) / 1e12 if gemm_ms > 0 else None
-    peak = bf_sus
+    peak, peak_of = bf_sus, f"{src} sustained bf16"
+    if a.prec == "tf32x3":   # kind::tf32 runs at the nominal dense TF32/BF16 ratio of the bf16 peak
+        peak, peak_of = bf_sus * TF32_PER_BF16, f"{src} sustained bf16 x {TF32_PER_BF16:.3f} (nominal dense tf32/bf16)"
     units = st1 - st0
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
@@ -624,9 +627,9 @@ def main():
                                      "at this size exists",
                      "kernel": f"gemm_tc {gemm_variant()} kernel (split-precision tcgen05 product)",
                      "note": f"algorithmic 2n^3 per product (n^3 when symmetric-output) over CUDA-event time of "
-                             f"{int(gemm_launches)} launches; each split product runs 3 half-precision "
+                             f"{int(gemm_launches)} launches; each split product runs 3 {a.prec[:4]} "
                              f"tensor products ({single_product_chains(a)}), "
-                             f"so tensor-pipe work is up to 3x the algorithmic flops; peak = {src} sustained bf16"},
+                             f"so tensor-pipe work is up to 3x the algorithmic flops; peak = {peak_of}"},
         "foe_tflops": (gemm_flops / sec / 1e12) if sec > 0 else None,
         "gemm_time_share": (gemm_ms / ms) if ms > 0 else None,
         "per_step": {"mu_passes": units[0] / a.steps, "products": units[3] / a.steps,

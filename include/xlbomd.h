@@ -55,7 +55,10 @@ typedef enum {
 typedef enum {
   XLBOMD_FP64 = 0,   /* plain FP64 products */
   XLBOMD_FP16x3 = 1, /* split FP16 hi/lo operands, 3 products, FP32 accumulation */
-  XLBOMD_BF16x3 = 2  /* split BF16 hi/lo operands, 3 products, FP32 accumulation */
+  XLBOMD_BF16x3 = 2, /* split BF16 hi/lo operands, 3 products, FP32 accumulation */
+  XLBOMD_TF32x3 = 3  /* split TF32 hi/lo operands (FP32 words), 3 products of tcgen05 kind::tf32,
+                        FP32 accumulation; twice the operand bytes and half the tensor rate of
+                        the 16-bit forms */
 } xlbomd_prec;
 
 /* Model and integrator constants.  xlbomd_default_params() fills the values
@@ -110,7 +113,7 @@ typedef struct {
   double rep_rho;          /* its decay length (A) */
   int kernel_prec;         /* split precisions: 0 = the kernel's response chains (probes, the
                               stiffest-mode search, exact-kernel columns) take the three products
-                              of the split; 1 = one 16-bit product (hi operands only, FP32
+                              of the split; 1 = one product of the hi operands (FP32
                               accumulation).  The kernel only preconditions the n dynamics and
                               the forces do not contain it; the expansion always takes three,
                               the chemical-potential chain follows mu_prec.  Ignored by FP64. */
@@ -123,7 +126,7 @@ typedef struct {
                               trajectories it measured slower than direct launches, so it is
                               off by default.  0: off. */
   int mu_prec;             /* split precisions: 0 = the chemical-potential chain (dD/dmu) takes the
-                              three products of the split; 1 = one 16-bit product.  dD/dmu only
+                              three products of the split; 1 = one hi*hi product.  dD/dmu only
                               sets the Newton step on mu and the first-order correction
                               D(mu + dmu) = D(mu) + dmu dD/dmu, whose trace stays exact whatever
                               its error; D's error from it is at most |dmu| times the error of
@@ -284,10 +287,10 @@ xlbomd_status xlbomd_set(xlbomd_ctx* ctx, int sys, int what, const double* host_
 xlbomd_status xlbomd_sizes(xlbomd_ctx* ctx, int sys, int* natoms, int* n_orb, int* n_pad);
 
 /* Diagnostics: one split-precision tensor-core product C = A B^T (n x n, n a
- * multiple of 128, prec FP16x3 or BF16x3; sym = 1: symmetric-output mode with
- * a symmetric B; sym = 2: the symmetric-output pair product A B^T + B A^T;
- * sym + 4: the same with one 16-bit product, hi operands only, as in the
- * single-product chains) of seeded uniform [-1, 1) matrices, compared on the
+ * multiple of 128, prec FP16x3, BF16x3 or TF32x3; sym = 1: symmetric-output
+ * mode with a symmetric B; sym = 2: the symmetric-output pair product
+ * A B^T + B A^T; sym + 4: the same with one product of the hi operands only, as
+ * in the single-product chains) of seeded uniform [-1, 1) matrices, compared on the
  * device with the FP64 product of the same FP64 inputs.  Other sym values:
  * ERR_ARG.  result[0] = max |C_tc - C_fp64|,
  * result[2] = device wait-timeout flag, result[3] = ms per product.
@@ -302,7 +305,7 @@ xlbomd_status xlbomd_selftest_gemm(int n, int prec, int sym, double* result);
  * table) against single launches: nprob (2..64) seeded operand pairs of size n, each product
  * computed alone, then all together in one grouped launch (both tile widths, as the tile
  * autotuner tries them, then the width it keeps).  sym as for xlbomd_selftest_gemm (0-2, +4
- * single product); prec FP16x3 or BF16x3.  result[0] = max |C_group - C_single| (0: the
+ * single product); prec FP16x3, BF16x3 or TF32x3.  result[0] = max |C_group - C_single| (0: the
  * grouped launch computes every tile exactly as the single launch does), result[1] = device
  * wait-timeout flag.  The paper has no counterpart. */
 xlbomd_status xlbomd_selftest_gemm_group(int n, int prec, int sym, int nprob, double* result);

@@ -15,7 +15,7 @@ from . import build as _build
 XLBOMD_OK = 0
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_NOT_CONVERGED",
           -5: "ERR_SPECTRUM", -6: "ERR_DIVERGED", -7: "ERR_TIMEOUT", -8: "ERR_UNSUPPORTED"}
-PREC = {"fp64": 0, "fp16x3": 1, "bf16x3": 2}
+PREC = {"fp64": 0, "fp16x3": 1, "bf16x3": 2, "tf32x3": 3}
 
 Q, N, NHIST, F, R, V, KR, RES, ENERGY, MU, D, H, GAMMA, STATS, PROBES, KMAT = range(16)
 

@@ -551,7 +551,7 @@ xlbomd_status exact_columns_grouped(xlbomd_ctx* ctx, Sys& S) {
   if (S.slots.empty()) {
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
-    const size_t per_slot = chain_slot_bytes(S.np) + per_vec * sizeof(double);
+    const size_t per_slot = chain_slot_bytes(S.np, ctx->p.prec) + per_vec * sizeof(double);
     int G = (int)std::min<size_t>(64, std::max<size_t>(1, free_b / 4 / per_slot));
     G = std::min(G, S.nat);
     S.slots.resize(G);
@@ -1238,7 +1238,9 @@ xlbomd_status xlbomd_init(const xlbomd_params* params, const xlbomd_system* syst
       p.kernel_mode < 0 || p.kernel_mode > 2 || p.kernel_every < 0 || p.rep_A < 0.0 || !(p.rep_rho > 0.0) ||
       p.kernel_prec < 0 || p.kernel_prec > 1 || p.graphs < 0 || p.graphs > 1 || p.mu_prec < 0 || p.mu_prec > 1)
     return XLBOMD_ERR_ARG;
-  if (p.prec != XLBOMD_FP64 && p.prec != XLBOMD_FP16x3 && p.prec != XLBOMD_BF16x3) return XLBOMD_ERR_ARG;
+  if (p.prec != XLBOMD_FP64 && p.prec != XLBOMD_FP16x3 && p.prec != XLBOMD_BF16x3 &&
+      p.prec != XLBOMD_TF32x3)
+    return XLBOMD_ERR_ARG;
   for (int i = 0; i < nsys; ++i) {
     const xlbomd_system& s = systems[i];
     if (s.natoms < 1 || !(s.box_L > p.r_cut) || !s.R || !s.V || !s.Z || !(s.mass > 0)) return XLBOMD_ERR_ARG;

@@ -1,15 +1,16 @@
 // Split-precision engine: the expansion and response chains with tensor-core
-// products on hi/lo 16-bit operands (FP16x3 or BF16x3).
+// products on hi/lo operand pairs (FP16x3, BF16x3 or TF32x3).
 //
 // Every matrix keeps a value array -- FP32, or double-float (an FP32 hi + lo
 // pair) for T_k, M and T1, whose leading terms the correction form keeps out of
-// the products -- and a split operand pair hi = rn16(x s), lo = rn16(x s - hi)
-// with a power-of-two scale s chosen from max |x| so that max |x s| lies in
-// [2^10, 2^11) (FP16 keeps full precision in both parts); producers raise
-// max |x| atomically and a conversion pass writes hi/lo.  A product takes three
-// 16-bit products (hi*hi, hi*lo, lo*hi), or one (hi*hi) in the probe chains
-// and the mu chain when the context asks for it.  Traces, charges and the
-// density matrix handed to the forces are accumulated in FP64.
+// the products -- and a split operand pair hi = rn(x s), lo = rn(x s - hi)
+// (rn: rounding to FP16, BF16 or TF32) with a power-of-two scale s chosen from
+// max |x| so that max |x s| lies in [2^10, 2^11) (FP16 keeps full precision in
+// both parts); producers raise max |x| atomically and a conversion pass writes
+// hi/lo.  A product takes three tensor-core products (hi*hi, hi*lo, lo*hi), or
+// one (hi*hi) in the probe chains and the mu chain when the context asks for
+// it.  Traces, charges and the density matrix handed to the forces are
+// accumulated in FP64.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -39,7 +40,8 @@ constexpr unsigned kEwBlocks = 152 * 16;
 // both accumulators.
 constexpr int kSplitAccMin = 8192;
 // Persistent product kernel, split products: the hi*hi sum is accumulated in chunks of this many
-// 64-wide K blocks (K = 1024), each folded into the running sum with round-to-nearest FP32 adds.
+// 64-wide K blocks of 16-bit operands (K = 1024; the same K with TF32's 32-wide blocks), each folded
+// into the running sum with round-to-nearest FP32 adds.
 // The tensor core truncates as it accumulates, so a sum's error grows with its length: at 2048
 // atoms (N = 8192) the charge error fell from 4.7e-5 e (one 8192-long sum) to 2.5e-5 e (two
 // halves), and it keeps halving with the chunk length.
@@ -62,70 +64,95 @@ __device__ __forceinline__ void raise_amax(unsigned* amax, float v) {
   }
 }
 
-// Conversion to the split operand pair: hi = rn16(x s), lo = rn16(x s - hi).
-template <bool BF16>
-__device__ __forceinline__ void split16(float x, unsigned short& h, unsigned short& l) {
-  if (BF16) {
-    const __nv_bfloat16 hb = __float2bfloat16_rn(x);
-    h = __bfloat16_as_ushort(hb);
-    l = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(hb)));
+// Operand words: FP16 or BF16 in 16 bits, TF32 in an FP32 word whose low 13 mantissa bits are
+// zero (fmt 0, 1, 2).
+template <int FMT>
+struct OpWord {
+  using T = unsigned short;
+  using V4 = ushort4;
+};
+template <>
+struct OpWord<2> {
+  using T = unsigned;
+  using V4 = uint4;
+};
+
+// Round x to the operand format; v receives the rounded value.  TF32 rounding (to 10 explicit
+// mantissa bits, nearest, ties away from zero) is the cvt.rna.tf32.f32 instruction.
+template <int FMT>
+__device__ __forceinline__ typename OpWord<FMT>::T op_round(float x, float& v) {
+  if constexpr (FMT == 2) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    v = __uint_as_float(r);
+    return r;
+  } else if constexpr (FMT == 1) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(x);
+    v = __bfloat162float(b);
+    return __bfloat16_as_ushort(b);
   } else {
-    const __half hh = __float2half_rn(x);
-    h = __half_as_ushort(hh);
-    l = __half_as_ushort(__float2half_rn(x - __half2float(hh)));
+    const __half h = __float2half_rn(x);
+    v = __half2float(h);
+    return __half_as_ushort(h);
   }
 }
 
-// All threads derive the same scale from amax; thread 0 of block 0 publishes it.  Four
-// elements per thread and step (16-byte loads, 8-byte stores; count is a multiple of 4).
-template <bool BF16>
-__global__ void convert_split_kernel(size_t count, const float* __restrict__ f, const unsigned* __restrict__ amax,
-                                     uint16_t* __restrict__ hi, uint16_t* __restrict__ lo, float* __restrict__ scale) {
-  const float m = __uint_as_float(*amax);
-  float s = 1.0f;
-  if (m > 0.0f && isfinite(m)) s = ldexpf(1.0f, 10 - ilogbf(m));
-  if (blockIdx.x == 0 && threadIdx.x == 0) *scale = s;
-  const float4* f4 = reinterpret_cast<const float4*>(f);
-  ushort4* h4 = reinterpret_cast<ushort4*>(hi);
-  ushort4* l4 = reinterpret_cast<ushort4*>(lo);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count / 4; i += (size_t)gridDim.x * blockDim.x) {
-    const float4 x = f4[i];
-    ushort4 h, l;
-    split16<BF16>(x.x * s, h.x, l.x);
-    split16<BF16>(x.y * s, h.y, l.y);
-    split16<BF16>(x.z * s, h.z, l.z);
-    split16<BF16>(x.w * s, h.w, l.w);
-    h4[i] = h;
-    l4[i] = l;
-  }
+// Four operand words at index i (16-byte groups for TF32, 8-byte for 16-bit words).
+template <int FMT>
+__device__ __forceinline__ void store4(void* base, size_t i, const typename OpWord<FMT>::T (&w)[4]) {
+  using V4 = typename OpWord<FMT>::V4;
+  V4 v;
+  v.x = w[0];
+  v.y = w[1];
+  v.z = w[2];
+  v.w = w[3];
+  reinterpret_cast<V4*>(base)[i] = v;
 }
 
-// The hi part alone, for matrices that only enter single products (hi*hi).
-template <bool BF16>
-__global__ void convert_hi_kernel(size_t count, const float* __restrict__ f, const unsigned* __restrict__ amax,
-                                  uint16_t* __restrict__ hi, float* __restrict__ scale) {
-  const float m = __uint_as_float(*amax);
-  float s = 1.0f;
-  if (m > 0.0f && isfinite(m)) s = ldexpf(1.0f, 10 - ilogbf(m));
-  if (blockIdx.x == 0 && threadIdx.x == 0) *scale = s;
-  const float4* f4 = reinterpret_cast<const float4*>(f);
-  ushort4* h4 = reinterpret_cast<ushort4*>(hi);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count / 4; i += (size_t)gridDim.x * blockDim.x) {
-    const float4 x = f4[i];
-    ushort4 h;
-    if (BF16) {
-      h.x = __bfloat16_as_ushort(__float2bfloat16_rn(x.x * s));
-      h.y = __bfloat16_as_ushort(__float2bfloat16_rn(x.y * s));
-      h.z = __bfloat16_as_ushort(__float2bfloat16_rn(x.z * s));
-      h.w = __bfloat16_as_ushort(__float2bfloat16_rn(x.w * s));
-    } else {
-      h.x = __half_as_ushort(__float2half_rn(x.x * s));
-      h.y = __half_as_ushort(__float2half_rn(x.y * s));
-      h.z = __half_as_ushort(__float2half_rn(x.z * s));
-      h.w = __half_as_ushort(__float2half_rn(x.w * s));
-    }
-    h4[i] = h;
+// Conversion of four values to the split operand pair: hi = rn(x s), lo = rn((x s - hi) + xl s)
+// (xl: the low word of a double-float value, else 0; s is a power of two, so x s is exact).
+// MODE 0: FP32 value -> hi, lo; 1: double-float value -> hi, lo; 2: FP32 value -> hi.
+template <int FMT, int MODE>
+__device__ __forceinline__ void convert4(size_t i, float s, const float* __restrict__ f, const float2* __restrict__ d,
+                                         void* hi, void* lo) {
+  float xs[4], xl[4] = {0.f, 0.f, 0.f, 0.f};
+  if (MODE == 1) {
+    const float4* d4 = reinterpret_cast<const float4*>(d);   // two double-float values per float4
+    const float4 a = d4[2 * i], b = d4[2 * i + 1];
+    xs[0] = a.x * s; xs[1] = a.z * s; xs[2] = b.x * s; xs[3] = b.z * s;
+    xl[0] = a.y * s; xl[1] = a.w * s; xl[2] = b.y * s; xl[3] = b.w * s;
+  } else {
+    const float4 x = reinterpret_cast<const float4*>(f)[i];
+    xs[0] = x.x * s; xs[1] = x.y * s; xs[2] = x.z * s; xs[3] = x.w * s;
   }
+  typename OpWord<FMT>::T h[4], l[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float hv, lv;
+    h[k] = op_round<FMT>(xs[k], hv);
+    if (MODE == 1) l[k] = op_round<FMT>((xs[k] - hv) + xl[k], lv);
+    if (MODE == 0) l[k] = op_round<FMT>(xs[k] - hv, lv);
+  }
+  store4<FMT>(hi, i, h);
+  if (MODE != 2) store4<FMT>(lo, i, l);
+}
+
+// The operand scale from max |x|: a power of two that puts max |x s| in [2^10, 2^11) (FP16
+// keeps full precision in both parts; BF16 and TF32 have FP32's range and lose nothing by it).
+__device__ __forceinline__ float operand_scale(const unsigned* amax) {
+  const float m = __uint_as_float(*amax);
+  return (m > 0.0f && isfinite(m)) ? ldexpf(1.0f, 10 - ilogbf(m)) : 1.0f;
+}
+
+// One matrix: all threads derive the same scale from amax; thread 0 of block 0 publishes it.
+// Four elements per thread and step (count is a multiple of 4).
+template <int FMT, int MODE>
+__global__ void convert_kernel(size_t count, const float* __restrict__ f, const float2* __restrict__ d,
+                               const unsigned* __restrict__ amax, void* hi, void* lo, float* __restrict__ scale) {
+  const float s = operand_scale(amax);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *scale = s;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count / 4; i += (size_t)gridDim.x * blockDim.x)
+    convert4<FMT, MODE>(i, s, f, d, hi, lo);
 }
 
 __global__ void df_to_f64_kernel(size_t count, const float2* __restrict__ x, double* __restrict__ y) {
@@ -140,41 +167,6 @@ __global__ void ident_minus_f32_to_f64_kernel(size_t count, int np, const float*
   if (i >= count) return;
   const int r = (int)(i / np), c = (int)(i % np);
   dst[i] = (r == c ? 1.0 : 0.0) - (double)W[i];
-}
-
-// The same from a double-float value hi + lo: the 16-bit pair splits (xh - hi16) + xl, so the
-// low FP32 word is not lost (s is a power of two, so x s is exact).
-template <bool BF16>
-__global__ void convert_split_d_kernel(size_t count, const float2* __restrict__ d, const unsigned* __restrict__ amax,
-                                       uint16_t* __restrict__ hi, uint16_t* __restrict__ lo,
-                                       float* __restrict__ scale) {
-  const float m = __uint_as_float(*amax);
-  float s = 1.0f;
-  if (m > 0.0f && isfinite(m)) s = ldexpf(1.0f, 10 - ilogbf(m));
-  if (blockIdx.x == 0 && threadIdx.x == 0) *scale = s;
-  const float4* d4 = reinterpret_cast<const float4*>(d);   // two double-float values per float4
-  ushort4* h4 = reinterpret_cast<ushort4*>(hi);
-  ushort4* l4 = reinterpret_cast<ushort4*>(lo);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count / 4; i += (size_t)gridDim.x * blockDim.x) {
-    const float4 a = d4[2 * i], b = d4[2 * i + 1];
-    const float xs[4] = {a.x * s, a.z * s, b.x * s, b.z * s};
-    const float xl[4] = {a.y * s, a.w * s, b.y * s, b.w * s};
-    unsigned short h[4], l[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (BF16) {
-        const __nv_bfloat16 hb = __float2bfloat16_rn(xs[k]);
-        h[k] = __bfloat16_as_ushort(hb);
-        l[k] = __bfloat16_as_ushort(__float2bfloat16_rn((xs[k] - __bfloat162float(hb)) + xl[k]));
-      } else {
-        const __half hh = __float2half_rn(xs[k]);
-        h[k] = __half_as_ushort(hh);
-        l[k] = __half_as_ushort(__float2half_rn((xs[k] - __half2float(hh)) + xl[k]));
-      }
-    }
-    h4[i] = make_ushort4(h[0], h[1], h[2], h[3]);
-    l4[i] = make_ushort4(l[0], l[1], l[2], l[3]);
-  }
 }
 
 __device__ __forceinline__ double df_val(float2 v) { return (double)v.x + (double)v.y; }
@@ -211,8 +203,8 @@ struct MatList {
   int n = 0;
   float* f[kMaxGroup];
   float2* d[kMaxGroup];
-  uint16_t* hi[kMaxGroup];
-  uint16_t* lo[kMaxGroup];
+  void* hi[kMaxGroup];
+  void* lo[kMaxGroup];
   float* scale[kMaxGroup];
   unsigned* amax[kMaxGroup];
 };
@@ -222,43 +214,14 @@ __global__ void zero_amax_kernel(MatList L) {
   if (i < L.n) *L.amax[i] = 0u;
 }
 
-// mode 0: FP32 value -> hi, lo; 1: double-float value -> hi, lo; 2: FP32 value -> hi
-template <bool BF16, int MODE>
+// convert_kernel per system (blockIdx.y)
+template <int FMT, int MODE>
 __global__ void convert_group_kernel(size_t count, MatList L) {
   const int j = blockIdx.y;
-  const float m = __uint_as_float(*L.amax[j]);
-  float s = 1.0f;
-  if (m > 0.0f && isfinite(m)) s = ldexpf(1.0f, 10 - ilogbf(m));
+  const float s = operand_scale(L.amax[j]);
   if (blockIdx.x == 0 && threadIdx.x == 0) *L.scale[j] = s;
-  ushort4* h4 = reinterpret_cast<ushort4*>(L.hi[j]);
-  ushort4* l4 = reinterpret_cast<ushort4*>(L.lo[j]);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count / 4; i += (size_t)gridDim.x * blockDim.x) {
-    float xs[4], xl[4] = {0.f, 0.f, 0.f, 0.f};
-    if (MODE == 1) {
-      const float4* d4 = reinterpret_cast<const float4*>(L.d[j]);
-      const float4 a = d4[2 * i], b = d4[2 * i + 1];
-      xs[0] = a.x * s; xs[1] = a.z * s; xs[2] = b.x * s; xs[3] = b.z * s;
-      xl[0] = a.y * s; xl[1] = a.w * s; xl[2] = b.y * s; xl[3] = b.w * s;
-    } else {
-      const float4 x = reinterpret_cast<const float4*>(L.f[j])[i];
-      xs[0] = x.x * s; xs[1] = x.y * s; xs[2] = x.z * s; xs[3] = x.w * s;
-    }
-    unsigned short h[4], l[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (BF16) {
-        const __nv_bfloat16 hb = __float2bfloat16_rn(xs[k]);
-        h[k] = __bfloat16_as_ushort(hb);
-        if (MODE != 2) l[k] = __bfloat16_as_ushort(__float2bfloat16_rn((xs[k] - __bfloat162float(hb)) + xl[k]));
-      } else {
-        const __half hh = __float2half_rn(xs[k]);
-        h[k] = __half_as_ushort(hh);
-        if (MODE != 2) l[k] = __half_as_ushort(__float2half_rn((xs[k] - __half2float(hh)) + xl[k]));
-      }
-    }
-    h4[i] = make_ushort4(h[0], h[1], h[2], h[3]);
-    if (MODE != 2) l4[i] = make_ushort4(l[0], l[1], l[2], l[3]);
-  }
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count / 4; i += (size_t)gridDim.x * blockDim.x)
+    convert4<FMT, MODE>(i, s, L.f[j], L.d[j], L.hi[j], L.lo[j]);
 }
 
 // Y = a I + b X per system (W_k start of the Newton-Schulz iteration)
@@ -409,7 +372,7 @@ struct Epi {
 };
 
 // The recursion is carried in correction form so that its exact leading
-// terms never pass through 16-bit operands:
+// terms never pass through the rounded operands:
 //   T_{k+1} = 2 T_k - 2 T_k W_k,  W_k = I - Y_k = I - (I + T_k^2)^-1,
 // W_k from the Newton-Schulz step written for W (Q = S - W - W S,
 // W <- W + Q - Q W), and the response chains as
@@ -418,45 +381,36 @@ struct Epi {
 // operand is the hi/lo split of a value.
 class EngineSplit : public Engine {
  public:
-  explicit EngineSplit(int prec) : bf16_(prec == XLBOMD_BF16x3_ID ? 1 : 0) {}
+  explicit EngineSplit(int prec) : fmt_(operand_fmt(prec)) {}
   ~EngineSplit() override {
     for (auto& kv : tiles_) cudaFree(kv.second.first);
     if (err_) cudaFree(err_);
     tc_group_cache_free(group_cache_);
   }
 
-  cudaError_t convert(cudaStream_t s, SplitMat& m, int np) {
-    const size_t count = (size_t)np * np;
-    const unsigned g = std::min<size_t>(nblk(count), 152 * 16);
-    if (bf16_)
-      convert_split_kernel<true><<<g, 256, 0, s>>>(count, m.f, m.amax, m.hi, m.lo, m.scale);
-    else
-      convert_split_kernel<false><<<g, 256, 0, s>>>(count, m.f, m.amax, m.hi, m.lo, m.scale);
-    note_launch();
-    return cudaGetLastError();
+  // operand split of one matrix: mode 0 FP32 -> hi, lo; 1 double-float -> hi, lo; 2 FP32 -> hi
+  template <int FMT>
+  void launch_convert(cudaStream_t s, SplitMat& m, size_t count, unsigned g, int mode) {
+    if (mode == 0) convert_kernel<FMT, 0><<<g, 256, 0, s>>>(count, m.f, m.d, m.amax, m.hi, m.lo, m.scale);
+    else if (mode == 1) convert_kernel<FMT, 1><<<g, 256, 0, s>>>(count, m.f, m.d, m.amax, m.hi, m.lo, m.scale);
+    else convert_kernel<FMT, 2><<<g, 256, 0, s>>>(count, m.f, m.d, m.amax, m.hi, m.lo, m.scale);
   }
 
-  cudaError_t convert_hi(cudaStream_t s, SplitMat& m, int np) {
+  cudaError_t convert_mode(cudaStream_t s, SplitMat& m, int np, int mode) {
     const size_t count = (size_t)np * np;
     const unsigned g = std::min<size_t>(nblk(count), 152 * 16);
-    if (bf16_)
-      convert_hi_kernel<true><<<g, 256, 0, s>>>(count, m.f, m.amax, m.hi, m.scale);
+    if (fmt_ == 2)
+      launch_convert<2>(s, m, count, g, mode);
+    else if (fmt_ == 1)
+      launch_convert<1>(s, m, count, g, mode);
     else
-      convert_hi_kernel<false><<<g, 256, 0, s>>>(count, m.f, m.amax, m.hi, m.scale);
+      launch_convert<0>(s, m, count, g, mode);
     note_launch();
     return cudaGetLastError();
   }
-
-  cudaError_t convert_d(cudaStream_t s, SplitMat& m, int np) {
-    const size_t count = (size_t)np * np;
-    const unsigned g = std::min<size_t>(nblk(count), 152 * 16);
-    if (bf16_)
-      convert_split_d_kernel<true><<<g, 256, 0, s>>>(count, m.d, m.amax, m.hi, m.lo, m.scale);
-    else
-      convert_split_d_kernel<false><<<g, 256, 0, s>>>(count, m.d, m.amax, m.hi, m.lo, m.scale);
-    note_launch();
-    return cudaGetLastError();
-  }
+  cudaError_t convert(cudaStream_t s, SplitMat& m, int np) { return convert_mode(s, m, np, 0); }
+  cudaError_t convert_d(cudaStream_t s, SplitMat& m, int np) { return convert_mode(s, m, np, 1); }
+  cudaError_t convert_hi(cudaStream_t s, SplitMat& m, int np) { return convert_mode(s, m, np, 2); }
 
   // Symmetric-product tile lists for size np, uploaded on the stream that uses them (the
   // context's stream may be non-blocking, so a legacy-stream copy would not be ordered
@@ -496,7 +450,7 @@ class EngineSplit : public Engine {
     a.nseg = e.nseg;
     a.pairs = e.pairs;
     a.sym = sym ? 1 : 0;
-    a.bf16 = bf16_;
+    a.fmt = fmt_;
     a.alpha = e.alpha;
     a.E = e.E ? e.E->f : nullptr;
     a.beta = e.beta;
@@ -520,7 +474,7 @@ class EngineSplit : public Engine {
     // large products: split the hi*hi sums over both accumulators (the tensor core truncates as it
     // accumulates, so a K-long sum's error grows with K)
     a.split_acc = (np >= kSplitAccMin) ? 1 : 0;
-    a.chunk_kb = kChunkKb;
+    a.chunk_kb = chunk_kb();
     RET(gemm_tc(s, np, A.hi, A.lo, B.hi, B.lo, a, tl));
     // kind bits: 1 sym, 2 E, 4 E2, 8 E64, 16 E64 transposed, 32 FP64 output
     const int kind = (sym ? 1 : 0) | (e.E ? 2 : 0) | (e.E2 ? 4 : 0) | (e.E64 ? 8 : 0) | (e.e64_trans ? 16 : 0) |
@@ -574,14 +528,18 @@ class EngineSplit : public Engine {
     const unsigned gx = (unsigned)std::max<size_t>(1, std::min<size_t>(nblk(count), (152 * 16) / ms.size()));
     const dim3 grid(gx, (unsigned)ms.size());
     const MatList L = mat_list(ms);
-    if (bf16_) {
-      if (mode == 0) convert_group_kernel<true, 0><<<grid, 256, 0, s>>>(count, L);
-      else if (mode == 1) convert_group_kernel<true, 1><<<grid, 256, 0, s>>>(count, L);
-      else convert_group_kernel<true, 2><<<grid, 256, 0, s>>>(count, L);
+    if (fmt_ == 2) {
+      if (mode == 0) convert_group_kernel<2, 0><<<grid, 256, 0, s>>>(count, L);
+      else if (mode == 1) convert_group_kernel<2, 1><<<grid, 256, 0, s>>>(count, L);
+      else convert_group_kernel<2, 2><<<grid, 256, 0, s>>>(count, L);
+    } else if (fmt_ == 1) {
+      if (mode == 0) convert_group_kernel<1, 0><<<grid, 256, 0, s>>>(count, L);
+      else if (mode == 1) convert_group_kernel<1, 1><<<grid, 256, 0, s>>>(count, L);
+      else convert_group_kernel<1, 2><<<grid, 256, 0, s>>>(count, L);
     } else {
-      if (mode == 0) convert_group_kernel<false, 0><<<grid, 256, 0, s>>>(count, L);
-      else if (mode == 1) convert_group_kernel<false, 1><<<grid, 256, 0, s>>>(count, L);
-      else convert_group_kernel<false, 2><<<grid, 256, 0, s>>>(count, L);
+      if (mode == 0) convert_group_kernel<0, 0><<<grid, 256, 0, s>>>(count, L);
+      else if (mode == 1) convert_group_kernel<0, 1><<<grid, 256, 0, s>>>(count, L);
+      else convert_group_kernel<0, 2><<<grid, 256, 0, s>>>(count, L);
     }
     note_launch();
     return cudaGetLastError();
@@ -609,9 +567,9 @@ class EngineSplit : public Engine {
     shared.nseg = e0.nseg;
     shared.pairs = e0.pairs;
     shared.sym = sym ? 1 : 0;
-    shared.bf16 = bf16_;
+    shared.fmt = fmt_;
     shared.split_acc = (np >= kSplitAccMin) ? 1 : 0;
-    shared.chunk_kb = kChunkKb;
+    shared.chunk_kb = chunk_kb();
     shared.err = err_;
     std::vector<TcProblem> probs(ops.size());
     for (size_t i = 0; i < ops.size(); ++i) {
@@ -1023,7 +981,9 @@ class EngineSplit : public Engine {
   int* err_ = nullptr;
 
  private:
-  int bf16_;
+  int chunk_kb() const { return fmt_ == 2 ? 2 * kChunkKb : kChunkKb; }   // K blocks per 1024-long chunk
+
+  int fmt_;   // operand format: 0 FP16, 1 BF16, 2 TF32
   int probe_nseg_ = 3;
   int mu_nseg_ = 3;
   std::unordered_map<int, std::pair<int*, TcTiles>> tiles_;
@@ -1035,7 +995,8 @@ class EngineSplit : public Engine {
 enum { kF = 1, kD = 2 };
 
 // Zeroing runs on the stream `s` that later uses the matrix.
-cudaError_t alloc_split(SplitMat& m, int np, float* scal_f, unsigned* scal_u, int what, cudaStream_t s) {
+// esz: bytes of one operand element (2: FP16/BF16, 4: TF32)
+cudaError_t alloc_split(SplitMat& m, int np, int esz, float* scal_f, unsigned* scal_u, int what, cudaStream_t s) {
   const size_t cnt = (size_t)np * np;
   if (what & kF) {
     RET(cudaMalloc((void**)&m.f, cnt * sizeof(float)));
@@ -1045,10 +1006,10 @@ cudaError_t alloc_split(SplitMat& m, int np, float* scal_f, unsigned* scal_u, in
     RET(cudaMalloc((void**)&m.d, cnt * sizeof(float2)));
     RET(cudaMemsetAsync(m.d, 0, cnt * sizeof(float2), s));
   }
-  RET(cudaMalloc((void**)&m.hi, cnt * sizeof(uint16_t)));
-  RET(cudaMalloc((void**)&m.lo, cnt * sizeof(uint16_t)));
-  RET(cudaMemsetAsync(m.hi, 0, cnt * sizeof(uint16_t), s));
-  RET(cudaMemsetAsync(m.lo, 0, cnt * sizeof(uint16_t), s));
+  RET(cudaMalloc((void**)&m.hi, cnt * esz));
+  RET(cudaMalloc((void**)&m.lo, cnt * esz));
+  RET(cudaMemsetAsync(m.hi, 0, cnt * esz, s));
+  RET(cudaMemsetAsync(m.lo, 0, cnt * esz, s));
   m.scale = scal_f;
   m.amax = scal_u;
   return cudaSuccess;
@@ -1073,12 +1034,12 @@ void free_split(SplitMat& m) {
 }  // namespace
 
 Engine* make_split_engine(int prec) {
-  if (prec != XLBOMD_FP16x3_ID && prec != XLBOMD_BF16x3_ID) return nullptr;
+  if (!is_split_prec(prec)) return nullptr;
   return new EngineSplit(prec);
 }
 
 cudaError_t alloc_matset_split(MatSet& m, cudaStream_t s) {
-  const int np = m.np, n = m.n;
+  const int np = m.np, n = m.n, esz = operand_bytes(m.prec);
   const int nmat = (n + 1) + n + 9;
   float* scal = nullptr;
   RET(cudaMalloc((void**)&scal, sizeof(float) * 2 * nmat));
@@ -1090,11 +1051,11 @@ cudaError_t alloc_matset_split(MatSet& m, cudaStream_t s) {
   m.sT.assign(n + 1, SplitMat());
   m.sY.assign(n, SplitMat());
   for (auto& x : m.sT) {
-    RET(alloc_split(x, np, sf + idx, su + idx, kD, s));
+    RET(alloc_split(x, np, esz, sf + idx, su + idx, kD, s));
     ++idx;
   }
   for (auto& x : m.sY) {
-    RET(alloc_split(x, np, sf + idx, su + idx, kF, s));
+    RET(alloc_split(x, np, esz, sf + idx, su + idx, kF, s));
     ++idx;
   }
   struct W {
@@ -1103,7 +1064,7 @@ cudaError_t alloc_matset_split(MatSet& m, cudaStream_t s) {
   } w[] = {{&m.sS, kF},  {&m.sQ, kF},  {&m.sYw, kF},  {&m.sA1, kF},
            {&m.sMt, kD | kF}, {&m.sT1a, kD | kF}, {&m.sT1b, kD | kF}, {&m.sTmu, kD}};
   for (auto& x : w) {
-    RET(alloc_split(*x.m, np, sf + idx, su + idx, x.what, s));
+    RET(alloc_split(*x.m, np, esz, sf + idx, su + idx, x.what, s));
     ++idx;
   }
   return cudaSuccess;
@@ -1115,7 +1076,7 @@ cudaError_t alloc_matset_split(MatSet& m, cudaStream_t s) {
 cudaError_t alloc_chain_slot(MatSet& slot, const MatSet& base, cudaStream_t s) {
   slot = base;
   slot.e64[0] = slot.e64[1] = slot.e64[2] = slot.e64[3] = slot.e64[4] = slot.e64[5] = slot.e64[6] = nullptr;
-  const int np = base.np;
+  const int np = base.np, esz = operand_bytes(base.prec);
   float* scal = nullptr;
   RET(cudaMalloc((void**)&scal, sizeof(float) * 2 * 5));
   RET(cudaMemsetAsync(scal, 0, sizeof(float) * 2 * 5, s));
@@ -1126,11 +1087,11 @@ cudaError_t alloc_chain_slot(MatSet& slot, const MatSet& base, cudaStream_t s) {
   slot.sT1b = SplitMat();
   slot.sTmu = SplitMat();
   unsigned* su = reinterpret_cast<unsigned*>(scal + 5);
-  RET(alloc_split(slot.sA1, np, scal + 0, su + 0, kF, s));
-  RET(alloc_split(slot.sMt, np, scal + 1, su + 1, kD | kF, s));
-  RET(alloc_split(slot.sT1a, np, scal + 2, su + 2, kD | kF, s));
-  RET(alloc_split(slot.sT1b, np, scal + 3, su + 3, kD | kF, s));
-  RET(alloc_split(slot.sTmu, np, scal + 4, su + 4, kD, s));
+  RET(alloc_split(slot.sA1, np, esz, scal + 0, su + 0, kF, s));
+  RET(alloc_split(slot.sMt, np, esz, scal + 1, su + 1, kD | kF, s));
+  RET(alloc_split(slot.sT1a, np, esz, scal + 2, su + 2, kD | kF, s));
+  RET(alloc_split(slot.sT1b, np, esz, scal + 3, su + 3, kD | kF, s));
+  RET(alloc_split(slot.sTmu, np, esz, scal + 4, su + 4, kD, s));
   return cudaSuccess;
 }
 
@@ -1144,7 +1105,9 @@ void free_chain_slot(MatSet& slot) {
 }
 
 // bytes of one chain slot of size np
-size_t chain_slot_bytes(int np) { return (size_t)np * np * (8 + 3 * 16 + 12); }
+size_t chain_slot_bytes(int np, int prec) {
+  return (size_t)np * np * (8 + 3 * 16 + 12 + 5 * 2 * (operand_bytes(prec) - 2));
+}
 
 void free_matset_split(MatSet& m) {
   for (auto& x : m.sT) free_split(x);
@@ -1265,8 +1228,8 @@ done:
 // alone and then all of them in one grouped launch (with 128- and 256-wide tiles where n allows
 // both); result = [max |C_group - C_single| over the problems and widths, error flag].
 int selftest_gemm_group(int n, int prec, int mode, int nprob, double* result) {
-  if (n % 128 || n <= 0 || nprob < 2 || nprob > kMaxGroup || (prec != XLBOMD_FP16x3_ID && prec != XLBOMD_BF16x3_ID))
-    return -1;
+  if (n % 128 || n <= 0 || nprob < 2 || nprob > kMaxGroup || !is_split_prec(prec)) return -1;
+  const int esz = operand_bytes(prec);
   const bool single = mode >= 4;
   const int sym = single ? mode - 4 : mode;
   if (sym < 0 || sym > 2) return -1;
@@ -1284,8 +1247,8 @@ int selftest_gemm_group(int n, int prec, int mode, int nprob, double* result) {
   for (int i = 0; i < nprob; ++i) {
     float* sf = scal + 4 * i;
     unsigned* su = reinterpret_cast<unsigned*>(scal + 4 * nprob + 4 * i);
-    if (alloc_split(A[i], n, sf, su, kF, nullptr) || alloc_split(B[i], n, sf + 1, su + 1, kF, nullptr) ||
-        alloc_split(C[i], n, sf + 2, su + 2, kF, nullptr) || alloc_split(R[i], n, sf + 3, su + 3, kF, nullptr))
+    if (alloc_split(A[i], n, esz, sf, su, kF, nullptr) || alloc_split(B[i], n, esz, sf + 1, su + 1, kF, nullptr) ||
+        alloc_split(C[i], n, esz, sf + 2, su + 2, kF, nullptr) || alloc_split(R[i], n, esz, sf + 3, su + 3, kF, nullptr))
       goto done;
     fill_random_kernel<<<nblk(cnt), 256>>>(cnt, n, 101 + 7 * i, 0, tmp);
     note_launch();
@@ -1344,8 +1307,9 @@ done:
 // Returns 0 on success and writes [max |C_tc - C_ref|, max |C_ref|, error flag, ms per product].
 int selftest_gemm(int n, int prec, int sym, double* result) {
   if (prec == 0 && n % 128 == 0 && n > 0 && sym >= 0 && sym <= 1) return selftest_gemm_f64(n, sym, result);
-  if (n % 128 || n <= 0 || (prec != XLBOMD_FP16x3_ID && prec != XLBOMD_BF16x3_ID)) return -1;
-  const bool single = sym >= 4;   // one 16-bit product (hi operands only), as in the single-product chains
+  if (n % 128 || n <= 0 || !is_split_prec(prec)) return -1;
+  const int esz = operand_bytes(prec);
+  const bool single = sym >= 4;   // one product of the hi operands only, as in the single-product chains
   if (single) sym -= 4;
   if (sym < 0 || sym > 2) return -1;
   EngineSplit eng(prec);
@@ -1363,8 +1327,8 @@ int selftest_gemm(int n, int prec, int sym, double* result) {
       (pair && cudaMalloc((void**)&Cref2, cnt * 8)))
     goto done;
   cudaMemset(scal, 0, 6 * sizeof(float));
-  if (alloc_split(sa, n, scal, (unsigned*)scal + 3, kF, s) || alloc_split(sb, n, scal + 1, (unsigned*)scal + 4, kF, s) ||
-      alloc_split(sc, n, scal + 2, (unsigned*)scal + 5, kF, s))
+  if (alloc_split(sa, n, esz, scal, (unsigned*)scal + 3, kF, s) || alloc_split(sb, n, esz, scal + 1, (unsigned*)scal + 4, kF, s) ||
+      alloc_split(sc, n, esz, scal + 2, (unsigned*)scal + 5, kF, s))
     goto done;
   fill_random_kernel<<<nblk(cnt), 256>>>(cnt, n, 11, 0, A);
   note_launch();

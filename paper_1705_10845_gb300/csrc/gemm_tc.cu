@@ -27,6 +27,13 @@
 // operands as a second K range, C = A B^T + B A^T.  Every mbarrier wait is
 // bounded: on timeout the kernel records an error code and leaves its loops,
 // and TMEM is always released.
+//
+// TF32 operands (fmt = 2, persistent kernel only) are FP32 words whose low 13
+// mantissa bits are zero.  A 128-byte swizzle row then holds 32 elements, and
+// each tcgen05.mma of kind::tf32 (K = 8) takes the same 32-byte step.  So the
+// ring's stage bytes, the shared-memory descriptors and the per-stage MMA
+// count stay as they are.  Only the K-block width (32 elements), the tensor
+// map's element type and the instruction kind change.
 #include <cuda.h>
 
 #include <algorithm>
@@ -137,7 +144,8 @@ __device__ __forceinline__ uint64_t smem_desc(const void* p) {
   return d;
 }
 
-// Instruction descriptor of kind::f16: D = F32, A/B = F16 (0) or BF16 (1), both K-major, M x N.
+// Instruction descriptor of kind::f16 / kind::tf32: D = F32, A/B = F16 (0) or BF16 (1) under
+// kind::f16, TF32 (2) under kind::tf32, both K-major, M x N.
 __host__ __device__ constexpr uint32_t instr_desc_m(int m, int bn, int ab_fmt) {
   return (1u << 4) | ((uint32_t)ab_fmt << 7) | ((uint32_t)ab_fmt << 10) | ((uint32_t)(bn >> 3) << 17) |
          ((uint32_t)(m >> 4) << 24);
@@ -150,6 +158,16 @@ __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
@@ -500,7 +518,7 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0) {
       constexpr uint32_t idesc_f16 = instr_desc(BN, 0);
       constexpr uint32_t idesc_bf16 = instr_desc(BN, 1);
-      const uint32_t idesc = a.bf16 ? idesc_bf16 : idesc_f16;
+      const uint32_t idesc = a.fmt ? idesc_bf16 : idesc_f16;
       for (int kb = 0; kb < total; ++kb) {
         const int s = kb % STAGES;
         const uint32_t ph = (kb / STAGES) & 1;
@@ -658,7 +676,8 @@ __device__ __forceinline__ void kwalk_next(KWalk& w, int nk, int Cn) {
   }
 }
 
-template <int BN>
+// TF32: operands are TF32 words (kind::tf32, 32-element K blocks); else FP16 or BF16 by a.fmt.
+template <int BN, bool TF32>
 __global__ void __launch_bounds__(192, 1)
     gemm_tc_persistent_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                               const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
@@ -705,7 +724,8 @@ __global__ void __launch_bounds__(192, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  const int nk = a.K / BK;
+  constexpr int bk = TF32 ? BK / 2 : BK;           // elements per K block (one 128-byte row)
+  const int nk = a.K / bk;
   const int total = a.nseg * a.pairs * nk;
   const bool chunked = a.nseg > 1;                 // split products; else single products alternate
   const int H = a.pairs * nk;                      // hi*hi K blocks
@@ -744,7 +764,7 @@ __global__ void __launch_bounds__(192, 1)
             break;
           }
           mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-          const int kk = w.kidx * BK;
+          const int kk = w.kidx * bk;
           const int ia = (w.kind == 2) ? (w.pr ? 5 : 1) : (w.pr ? 4 : 0);
           const int ib = (w.kind == 1) ? (w.pr ? 7 : 3) : (w.pr ? 6 : 2);
           const CUtensorMap* ma = maps ? &maps[ia] : (w.kind == 2) ? (w.pr ? &mA2lo : &mAlo) : (w.pr ? &mA2hi : &mAhi);
@@ -758,7 +778,8 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0) {
       constexpr uint32_t idesc_f16 = instr_desc(BN, 0);
       constexpr uint32_t idesc_bf16 = instr_desc(BN, 1);
-      const uint32_t idesc = a.bf16 ? idesc_bf16 : idesc_f16;
+      constexpr uint32_t idesc_tf32 = instr_desc(BN, 2);
+      const uint32_t idesc = TF32 ? idesc_tf32 : a.fmt ? idesc_bf16 : idesc_f16;
       uint32_t g = 0;
       int it = 0;
       int uses0 = 0, uses1 = 0;      // fresh writes of each accumulator so far (split products)
@@ -816,7 +837,10 @@ __global__ void __launch_bounds__(192, 1)
           for (int j = 0; j < BK / 16; ++j) {
             const uint64_t ad = smem_desc(sA + s * A_BYTES + j * 32);
             const uint64_t bd = smem_desc(sB + s * B_BYTES + j * 32);
-            mma_f16(tmem + dcol, ad, bd, idesc, (fresh >= 0 && j == 0) ? 0u : 1u);
+            if constexpr (TF32)
+              mma_tf32(tmem + dcol, ad, bd, idesc, (fresh >= 0 && j == 0) ? 0u : 1u);
+            else
+              mma_f16(tmem + dcol, ad, bd, idesc, (fresh >= 0 && j == 0) ? 0u : 1u);
           }
           mma_commit(&empty[s]);
         }
@@ -1100,7 +1124,7 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0 && leader) {
       constexpr uint32_t idesc_f16 = instr_desc_m(256, BN, 0);
       constexpr uint32_t idesc_bf16 = instr_desc_m(256, BN, 1);
-      const uint32_t idesc = a.bf16 ? idesc_bf16 : idesc_f16;
+      const uint32_t idesc = a.fmt ? idesc_bf16 : idesc_f16;
       uint32_t g = 0;
       int it = 0;
       int uses0 = 0, uses1 = 0;
@@ -1269,21 +1293,23 @@ EncodeTiledFn get_encode() {
 
 struct MapKey {
   const void* p;
-  int rows, box, bf16;
-  bool operator==(const MapKey& o) const { return p == o.p && rows == o.rows && box == o.box && bf16 == o.bf16; }
+  int rows, box, fmt;
+  bool operator==(const MapKey& o) const { return p == o.p && rows == o.rows && box == o.box && fmt == o.fmt; }
 };
 struct MapHash {
   size_t operator()(const MapKey& k) const {
-    return std::hash<const void*>()(k.p) ^ (size_t)k.rows * 1315423911u ^ (size_t)k.box * 2654435761u ^ k.bf16;
+    return std::hash<const void*>()(k.p) ^ (size_t)k.rows * 1315423911u ^ (size_t)k.box * 2654435761u ^ k.fmt;
   }
 };
 
 std::mutex g_map_mu;
 std::unordered_map<MapKey, CUtensorMap, MapHash> g_maps;
 
-bool make_map(CUtensorMap* out, const void* base, int n, int box_rows, int bf16) {
+// n x n row-major operand, boxes of one 128-byte swizzle row (64 16-bit or 32 TF32 elements) by
+// box_rows rows; fmt 0 FP16, 1 BF16, 2 TF32 (FP32 words)
+bool make_map(CUtensorMap* out, const void* base, int n, int box_rows, int fmt) {
   std::lock_guard<std::mutex> lk(g_map_mu);
-  MapKey k{base, n, box_rows, bf16};
+  MapKey k{base, n, box_rows, fmt};
   auto it = g_maps.find(k);
   if (it != g_maps.end()) {
     *out = it->second;
@@ -1292,11 +1318,15 @@ bool make_map(CUtensorMap* out, const void* base, int n, int box_rows, int bf16)
   EncodeTiledFn enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
-  cuuint64_t strides[1] = {(cuuint64_t)n * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  const int esz = fmt == 2 ? 4 : 2;
+  cuuint64_t strides[1] = {(cuuint64_t)n * esz};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUtensorMap m;
-  CUresult r = enc(&m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+  const CUtensorMapDataType dt = fmt == 2   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                            : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  CUresult r = enc(&m, dt, 2,
                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return false;
@@ -1339,7 +1369,7 @@ constexpr int kMaxDevices = 64;
 struct DeviceState {
   int sms = 0;
   int pair_clusters = 0;   // co-resident clusters of the two-SM product kernel
-  bool smem_set[5] = {false, false, false, false, false};
+  bool smem_set[7] = {false, false, false, false, false, false, false};
 };
 std::mutex g_dev_mu;
 DeviceState g_dev[kMaxDevices];
@@ -1406,6 +1436,21 @@ cudaError_t ensure_smem(int slot, Kern kern, int bytes) {
   return e;
 }
 
+// Persistent launch with tiles of width BN (grid CTAs, one per SM); TF32 operands (a.fmt = 2)
+// take their own instantiation, so the FP16/BF16 kernel keeps compile-time K blocks.
+template <int BN>
+cudaError_t launch_persistent(cudaStream_t s, int grid, const CUtensorMap (&m)[8], const TcArgs& a, int ntiles,
+                              const TcEntry* tab, int tiles_per) {
+  const int sb = smem_bytes_persistent<BN>();
+  const bool tf32 = a.fmt == 2;
+  auto kern = tf32 ? gemm_tc_persistent_kernel<BN, true> : gemm_tc_persistent_kernel<BN, false>;
+  const cudaError_t attr = ensure_smem((BN == 256 ? 0 : 1) + (tf32 ? 5 : 0), kern, sb);
+  if (attr != cudaSuccess) return attr;
+  kern<<<grid, 192, sb, s>>>(m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7], a, ntiles, tab, tiles_per);
+  note_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 void tc_forget_maps(const void* base) {
@@ -1418,24 +1463,26 @@ void tc_forget_maps(const void* base) {
   }
 }
 
-cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* Alo, const uint16_t* Bhi,
-                    const uint16_t* Blo, TcArgs args, const TcTiles& tiles) {
+cudaError_t gemm_tc(cudaStream_t s, int n, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo,
+                    TcArgs args, const TcTiles& tiles) {
   if (n % 128 != 0 || n <= 0) return cudaErrorInvalidValue;
   if (args.pairs != 1 && args.pairs != 2) return cudaErrorInvalidValue;
   const bool wide = (n % 256 == 0);
-  const int variant = tc_variant();
+  if (args.fmt < 0 || args.fmt > 2) return cudaErrorInvalidValue;
+  // TF32 operands run on the persistent kernel only
+  const int variant = args.fmt == 2 ? 1 : tc_variant();
   const bool two_sm = (variant == 2) && wide && tiles.pair != nullptr;
   // B boxes: a CTA's 128-row half of the 256-row tile (two-SM), else the tile's bn rows
   const int bn = wide ? 256 : 128;
   const int bbox = two_sm ? 128 : bn;
   CUtensorMap mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo;
-  if (!make_map(&mAhi, Ahi, n, BM, args.bf16) || !make_map(&mAlo, Alo ? Alo : Ahi, n, BM, args.bf16) ||
-      !make_map(&mBhi, Bhi, n, bbox, args.bf16) || !make_map(&mBlo, Blo ? Blo : Bhi, n, bbox, args.bf16))
+  if (!make_map(&mAhi, Ahi, n, BM, args.fmt) || !make_map(&mAlo, Alo ? Alo : Ahi, n, BM, args.fmt) ||
+      !make_map(&mBhi, Bhi, n, bbox, args.fmt) || !make_map(&mBlo, Blo ? Blo : Bhi, n, bbox, args.fmt))
     return cudaErrorInvalidValue;
   if (args.pairs == 2) {
     // the swapped pair: B in the A role (BM-row boxes), A in the B role
-    if (!make_map(&mA2hi, Bhi, n, BM, args.bf16) || !make_map(&mA2lo, Blo ? Blo : Bhi, n, BM, args.bf16) ||
-        !make_map(&mB2hi, Ahi, n, bbox, args.bf16) || !make_map(&mB2lo, Alo ? Alo : Ahi, n, bbox, args.bf16))
+    if (!make_map(&mA2hi, Bhi, n, BM, args.fmt) || !make_map(&mA2lo, Blo ? Blo : Bhi, n, BM, args.fmt) ||
+        !make_map(&mB2hi, Ahi, n, bbox, args.fmt) || !make_map(&mB2lo, Alo ? Alo : Ahi, n, bbox, args.fmt))
       return cudaErrorInvalidValue;
   } else {
     mA2hi = mAhi;
@@ -1491,21 +1538,9 @@ cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* 
   }
   if (variant >= 1) {
     const int grid = std::min(nblocks, sm_count());
-    if (wide) {
-      const int sb = smem_bytes_persistent<256>();
-      const cudaError_t attr = ensure_smem(0, gemm_tc_persistent_kernel<256>, sb);
-      if (attr != cudaSuccess) return attr;
-      gemm_tc_persistent_kernel<256><<<grid, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo, args, nblocks,
-                                                           nullptr, 0);
-    } else {
-      const int sb = smem_bytes_persistent<128>();
-      const cudaError_t attr = ensure_smem(1, gemm_tc_persistent_kernel<128>, sb);
-      if (attr != cudaSuccess) return attr;
-      gemm_tc_persistent_kernel<128><<<grid, 192, sb, s>>>(mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo, args, nblocks,
-                                                           nullptr, 0);
-    }
-    note_launch();
-    return cudaGetLastError();
+    const CUtensorMap maps[8] = {mAhi, mAlo, mBhi, mBlo, mA2hi, mA2lo, mB2hi, mB2lo};
+    return wide ? launch_persistent<256>(s, grid, maps, args, nblocks, nullptr, 0)
+                : launch_persistent<128>(s, grid, maps, args, nblocks, nullptr, 0);
   }
   if (wide) {
     const int sb = smem_bytes<256>();
@@ -1553,14 +1588,14 @@ inline uint64_t bits_of(T v) {
 
 cudaError_t gemm_tc_group(cudaStream_t s, int n, const TcProblem* probs, int nprob, TcArgs shared,
                           const TcTiles& tiles, TcGroupCache* cache) {
-  if (nprob < 1 || !cache) return cudaErrorInvalidValue;
+  if (nprob < 1 || !cache || shared.fmt < 0 || shared.fmt > 2) return cudaErrorInvalidValue;
   if (n % 128 != 0 || n <= 0 || (shared.pairs != 1 && shared.pairs != 2)) return cudaErrorInvalidValue;
   if (nprob == 1) {
     TcArgs a = probs[0].epi;
     a.nseg = shared.nseg;
     a.pairs = shared.pairs;
     a.sym = shared.sym;
-    a.bf16 = shared.bf16;
+    a.fmt = shared.fmt;
     a.split_acc = shared.split_acc;
     a.chunk_kb = shared.chunk_kb;
     a.err = shared.err;
@@ -1572,7 +1607,7 @@ cudaError_t gemm_tc_group(cudaStream_t s, int n, const TcProblem* probs, int npr
   // one of them changes)
   uint64_t key = 1469598103934665603ull;
   key = fnv_mix(key, (uint64_t)n * 1000003u + shared.nseg * 7 + shared.pairs * 31 + shared.sym * 131 +
-                         shared.bf16 * 521 + (uint64_t)bn * 7919);
+                         shared.fmt * 521 + (uint64_t)bn * 7919);
   key = fnv_mix(key, (uint64_t)(shared.sym ? (wide ? tiles.sym256 : tiles.sym128) : nullptr));
   key = fnv_mix(key, (uint64_t)shared.err + (uint64_t)shared.chunk_kb);
   for (int i = 0; i < nprob; ++i) {
@@ -1606,14 +1641,14 @@ cudaError_t gemm_tc_group(cudaStream_t s, int n, const TcProblem* probs, int npr
     for (int i = 0; i < nprob; ++i) {
       const TcProblem& q = probs[i];
       TcEntry& t = host[i];
-      const uint16_t* Alo = q.Alo ? q.Alo : q.Ahi;
-      const uint16_t* Blo = q.Blo ? q.Blo : q.Bhi;
-      if (!make_map(&t.map[0], q.Ahi, n, BM, shared.bf16) || !make_map(&t.map[1], Alo, n, BM, shared.bf16) ||
-          !make_map(&t.map[2], q.Bhi, n, bn, shared.bf16) || !make_map(&t.map[3], Blo, n, bn, shared.bf16))
+      const void* Alo = q.Alo ? q.Alo : q.Ahi;
+      const void* Blo = q.Blo ? q.Blo : q.Bhi;
+      if (!make_map(&t.map[0], q.Ahi, n, BM, shared.fmt) || !make_map(&t.map[1], Alo, n, BM, shared.fmt) ||
+          !make_map(&t.map[2], q.Bhi, n, bn, shared.fmt) || !make_map(&t.map[3], Blo, n, bn, shared.fmt))
         return cudaErrorInvalidValue;
       if (shared.pairs == 2) {
-        if (!make_map(&t.map[4], q.Bhi, n, BM, shared.bf16) || !make_map(&t.map[5], Blo, n, BM, shared.bf16) ||
-            !make_map(&t.map[6], q.Ahi, n, bn, shared.bf16) || !make_map(&t.map[7], Alo, n, bn, shared.bf16))
+        if (!make_map(&t.map[4], q.Bhi, n, BM, shared.fmt) || !make_map(&t.map[5], Blo, n, BM, shared.fmt) ||
+            !make_map(&t.map[6], q.Ahi, n, bn, shared.fmt) || !make_map(&t.map[7], Alo, n, bn, shared.fmt))
           return cudaErrorInvalidValue;
       } else {
         t.map[4] = t.map[0];
@@ -1629,7 +1664,7 @@ cudaError_t gemm_tc_group(cudaStream_t s, int n, const TcProblem* probs, int npr
       t.args.nseg = a.nseg;
       t.args.pairs = a.pairs;
       t.args.sym = a.sym;
-      t.args.bf16 = a.bf16;
+      t.args.fmt = a.fmt;
       t.args.split_acc = a.split_acc;
       t.args.chunk_kb = a.chunk_kb;
       t.args.bn = a.bn;
@@ -1650,23 +1685,10 @@ cudaError_t gemm_tc_group(cudaStream_t s, int n, const TcProblem* probs, int npr
   const int ntiles = nprob * tiles_per;
   const int grid = std::min(ntiles, sm_count());
   // the launch's own maps are unused (every problem's maps come from the table)
-  CUtensorMap dummy;
-  std::memset(&dummy, 0, sizeof(dummy));
-  if (wide) {
-    const int sb = smem_bytes_persistent<256>();
-    const cudaError_t attr = ensure_smem(0, gemm_tc_persistent_kernel<256>, sb);
-    if (attr != cudaSuccess) return attr;
-    gemm_tc_persistent_kernel<256><<<grid, 192, sb, s>>>(dummy, dummy, dummy, dummy, dummy, dummy, dummy, dummy, a,
-                                                           ntiles, table, tiles_per);
-  } else {
-    const int sb = smem_bytes_persistent<128>();
-    const cudaError_t attr = ensure_smem(1, gemm_tc_persistent_kernel<128>, sb);
-    if (attr != cudaSuccess) return attr;
-    gemm_tc_persistent_kernel<128><<<grid, 192, sb, s>>>(dummy, dummy, dummy, dummy, dummy, dummy, dummy, dummy, a,
-                                                           ntiles, table, tiles_per);
-  }
-  note_launch();
-  return cudaGetLastError();
+  CUtensorMap dummy[8];
+  std::memset(dummy, 0, sizeof(dummy));
+  return wide ? launch_persistent<256>(s, grid, dummy, a, ntiles, table, tiles_per)
+              : launch_persistent<128>(s, grid, dummy, a, ntiles, table, tiles_per);
 }
 
 // Tile list of symmetric two-SM products: the 256 x 256 tiles (tm, tn) with tn >= tm, in the

@@ -2,7 +2,7 @@
 //
 // The orchestration (capi.cu) is written once; an Engine runs the matrix
 // recursions in one arithmetic: plain FP64 products, or split-precision
-// tensor-core products (hi/lo 16-bit operands, FP32 accumulation).
+// tensor-core products (hi/lo FP16, BF16 or TF32 operands, FP32 accumulation).
 #pragma once
 #include <cstdio>
 #include <cstdlib>
@@ -15,15 +15,24 @@ namespace xl {
 
 constexpr int XLBOMD_FP16x3_ID = 1;
 constexpr int XLBOMD_BF16x3_ID = 2;
+constexpr int XLBOMD_TF32x3_ID = 3;
+
+inline bool is_split_prec(int prec) {
+  return prec == XLBOMD_FP16x3_ID || prec == XLBOMD_BF16x3_ID || prec == XLBOMD_TF32x3_ID;
+}
+// product operand format of a split precision (0 FP16, 1 BF16, 2 TF32) and its bytes per element
+inline int operand_fmt(int prec) { return prec == XLBOMD_TF32x3_ID ? 2 : prec == XLBOMD_BF16x3_ID ? 1 : 0; }
+inline int operand_bytes(int prec) { return prec == XLBOMD_TF32x3_ID ? 4 : 2; }
 
 // Matrices of one system in the working precision.  In the FP64 engine each
 // logical matrix is a double array; the split engines keep an FP32 value
-// array plus hi/lo 16-bit operand arrays with a power-of-two scale.
+// array plus hi/lo operand arrays (16-bit FP16/BF16, or TF32 in FP32 words)
+// with a power-of-two scale.
 struct SplitMat {
   float2* d = nullptr;       // double-float value hi + lo (matrices carried with an exact leading term)
   float* f = nullptr;        // FP32 value (np x np)
-  uint16_t* hi = nullptr;    // operand hi part of value * scale
-  uint16_t* lo = nullptr;    // operand lo part
+  void* hi = nullptr;        // operand hi part of value * scale
+  void* lo = nullptr;        // operand lo part
   float* scale = nullptr;    // device scalar
   unsigned* amax = nullptr;  // device scalar: float bits of max |value|
 };
@@ -168,7 +177,7 @@ cudaError_t alloc_matset_split(MatSet& m, cudaStream_t s);
 // response-chain slots of a split-precision system (grouped probes of one system)
 cudaError_t alloc_chain_slot(MatSet& slot, const MatSet& base, cudaStream_t s);
 void free_chain_slot(MatSet& slot);
-size_t chain_slot_bytes(int np);
+size_t chain_slot_bytes(int np, int prec);
 void free_matset_split(MatSet& m);
 
 // tensor-core product self-test (engine_split.cu)

@@ -20,7 +20,8 @@ struct TcArgs {
   int nseg = 3;                   // 1: hi only; 3: hi*hi + hi*lo + lo*hi
   int pairs = 1;                  // 2: C = A B^T + B A^T (the swapped pair as a second K range)
   int sym = 0;                    // symmetric output (upper tiles, mirrored)
-  int bf16 = 0;                   // operand type: 0 FP16, 1 BF16
+  int fmt = 0;                    // operand type: 0 FP16, 1 BF16 (kind::f16), 2 TF32 (kind::tf32,
+                                  // FP32 words; persistent kernel only)
   int tiles_n = 0;                // set by gemm_tc
   const int* tile_list = nullptr; // set by gemm_tc
   float alpha = 1.0f;             // C = alpha acc / (sa sb) + beta E^T + beta2 E2^T + beta64 E64(^T)
@@ -55,9 +56,9 @@ struct TcEntry {   // CUtensorMap's own alignment (64 bytes) aligns every entry
 };
 
 // One problem of a grouped product: operands and its epilogue arguments (n, K, nseg, pairs,
-// sym, bf16, chunk_kb and err come from the launch's shared arguments).
+// sym, fmt, chunk_kb and err come from the launch's shared arguments).
 struct TcProblem {
-  const uint16_t *Ahi = nullptr, *Alo = nullptr, *Bhi = nullptr, *Blo = nullptr;
+  const void *Ahi = nullptr, *Alo = nullptr, *Bhi = nullptr, *Blo = nullptr;   // operand arrays (n x n, row-major)
   TcArgs epi;
 };
 
@@ -75,8 +76,8 @@ struct TcTiles {
 
 // n x n product (n a multiple of 128); the symmetric tile lists come from tc_sym_tiles and
 // tc_sym_tiles_pair.
-cudaError_t gemm_tc(cudaStream_t s, int n, const uint16_t* Ahi, const uint16_t* Alo, const uint16_t* Bhi,
-                    const uint16_t* Blo, TcArgs args, const TcTiles& tiles);
+cudaError_t gemm_tc(cudaStream_t s, int n, const void* Ahi, const void* Alo, const void* Bhi, const void* Blo,
+                    TcArgs args, const TcTiles& tiles);
 // Grouped product: the problems' tiles in one persistent launch (one-SM kernel).  The device
 // table of each distinct problem list is built once and kept in `cache` (key: the table's
 // bytes), so repeated groups upload nothing.

@@ -57,6 +57,8 @@ def bytes_estimate(natoms: int, n_sq: int, prec: str = "fp16x3") -> int:
         per = 8 * ((n_sq + 1) + n_sq + 9 + 3)
     else:
         per = 12 * (n_sq + 1) + 8 * n_sq + 8 * 5 + 12 * 4 + 8 * 3
+        if prec == "tf32x3":   # TF32 operands: 4 bytes each, 2 more per hi and per lo word
+            per += 4 * ((n_sq + 1) + n_sq + 8)
     return int(per * e * 1.05) + (64 << 20)
 
 

@@ -70,6 +70,26 @@ def test_binding_struct_layout_matches_header(tmp_path):
             assert int(out[f"{cname}.{f}"]) == getattr(struct, f).offset, f
 
 
+def test_binding_precision_names_match_header_enum(tmp_path):
+    # the binding's precision names carry the header's xlbomd_prec values
+    import shutil
+    import subprocess
+    from paper_1705_10845_gb300 import binding
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    names = {"fp64": "XLBOMD_FP64", "fp16x3": "XLBOMD_FP16x3", "bf16x3": "XLBOMD_BF16x3", "tf32x3": "XLBOMD_TF32x3"}
+    assert set(binding.PREC) == set(names)
+    body = "".join(f'printf("{k} %d\\n", (int){v});' for k, v in names.items())
+    src = tmp_path / "prec.c"
+    src.write_text(f'#include <stdio.h>\n#include "xlbomd.h"\nint main(void) {{ {body} return 0; }}\n')
+    exe = tmp_path / "prec"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    assert {k: int(v) for k, v in out.items()} == binding.PREC
+
+
 def test_table_i_rows_of_the_library_match_the_printed_table(golden):
     # host-only call: the library's Table I (kappa, alpha, c_k) against the values printed in
     # the paper (tests/golden/table_i.txt)
@@ -87,7 +107,7 @@ def test_table_i_rows_of_the_library_match_the_printed_table(golden):
 BAD_PARAMS = [dict(mu_prec=2), dict(kernel_prec=-1), dict(graphs=2), dict(rank_m=9), dict(n_sq=0),
               dict(n_sq=41), dict(Te=0.0), dict(dt=0.0), dict(kernel_c=1.0), dict(mu_max_iter=0),
               dict(scf_mode=2), dict(kernel_mode=3), dict(kernel_every=-1), dict(rep_A=-1.0),
-              dict(rep_rho=0.0), dict(prec=5)]
+              dict(rep_rho=0.0), dict(prec=4), dict(prec=-1)]
 
 
 @pytest.mark.parametrize("bad", BAD_PARAMS, ids=lambda d: "-".join(f"{k}={v}" for k, v in d.items()))

@@ -51,7 +51,7 @@ def test_lockstep_batch_equals_solo_runs():
     for nat, seed in sizes:
         s = synth.make_system(nat, seed)
         systems.append(dict(natoms=s.natoms, L=s.L, R=s.R, V=s.V, Z=s.Z, mass=s.mass))
-    for prec in ("fp16x3", "fp64"):
+    for prec in ("fp16x3", "tf32x3", "fp64"):
         p = X.default_params(Te=1000.0, n_sq=10, rank_m=2, mix_alpha=0.06, kernel_c=1 - 1 / 0.06, prec=prec,
                              scf_mode=1, kernel_auto=1, scf_tol=1e-5 if prec != "fp64" else 1e-9,
                              mu_tol=1e-3 if prec != "fp64" else 1e-9, rep_A=40.0, rep_rho=0.3, kernel_prec=1,

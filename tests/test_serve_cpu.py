@@ -46,6 +46,15 @@ def test_memory_estimate_grows_with_size():
     assert serve.bytes_estimate(512, 10) > 10 * serve.bytes_estimate(64, 10)
 
 
+def test_memory_estimate_counts_operand_width():
+    # TF32 operands take 4 bytes against FP16's 2: 4 more bytes per element for each of the
+    # (n_sq + 1) + n_sq + 8 split matrices; FP64 keeps double arrays and no operands
+    e = 2048 * 2048
+    extra = serve.bytes_estimate(512, 10, "tf32x3") - serve.bytes_estimate(512, 10, "fp16x3")
+    assert extra == pytest.approx(4 * (11 + 10 + 8) * e * 1.05, rel=1e-6)
+    assert serve.bytes_estimate(512, 10, "bf16x3") == serve.bytes_estimate(512, 10, "fp16x3")
+
+
 def test_all_jobs_run_within_the_memory_budget():
     jobs = [serve.Job(arrival=0.0, jid=i, natoms=32 + 8 * (i % 5), Te=1000.0, steps=5, seed=i) for i in range(20)]
     budget = 3 * max(serve.bytes_estimate(j.natoms, serve.squarings_for(j.Te)) for j in jobs)
