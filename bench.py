@@ -6,7 +6,8 @@ carbon-like atoms (N = 16384 orbitals) in a 38.8 A periodic cube, Te = 1000 K,
 10 squarings of the recursive Fermi-operator expansion, rank-4 kernel,
 dt = 0.25 fs; split FP16x3 tensor-core products in the expansion (one 16-bit
 product in the probe and chemical-potential chains) with FP32 accumulation and
-FP64 traces, charges, forces and integration.  A step is one full XL-BOMD step
+FP64 traces, charges, forces and integration (--prec bf16x3, tf32x3 or fp64 selects
+another form).  A step is one full XL-BOMD step
 (H build, expansion with the chemical-potential loop, charges, forces, four
 response chains, kernel update, Verlet).  With --gpus N each rank runs its own
 replica trajectory (seed 1705 + rank): weak scaling, no collective on the data
@@ -61,10 +62,10 @@ def parse():
     ap.add_argument("--nsq", type=int, default=10)
     ap.add_argument("--rank", type=int, default=4)
     ap.add_argument("--kernel-prec", type=int, default=1, choices=[0, 1],
-                    help="1 (default): the kernel's probe chains take one 16-bit product instead of three; "
+                    help="1 (default): the kernel's probe chains take one hi*hi product instead of three; "
                          "0: three, as the expansion")
     ap.add_argument("--mu-prec", type=int, default=1, choices=[0, 1],
-                    help="1 (default): the chemical-potential chain (dD/dmu) takes one 16-bit product instead "
+                    help="1 (default): the chemical-potential chain (dD/dmu) takes one hi*hi product instead "
                          "of three; 0: three, as the expansion")
     ap.add_argument("--rep-A", type=float, default=40.0,
                     help="pair repulsion A exp(-r/0.3 A) (eV): the model's atoms collapse without it in long runs")
@@ -97,14 +98,22 @@ def parse():
     return ap.parse_args()
 
 
+def chain_products(a, single):
+    """Products per step of a response chain: one hi*hi product of the operand format, three (the
+    full split), or the plain FP64 product."""
+    if a.prec == "fp64":
+        return "one fp64 product"
+    return f"one {a.prec[:4]} product" if single else "three (full split)"
+
+
 def workload_config(a, parallel):
     return {
         "workload": f"XL-BOMD, {a.natoms} carbon-like atoms (N = {4 * a.natoms} orbitals), orthogonal SCC-TB, "
                     f"Te = {a.Te:g} K, {a.nsq} squarings, rank-{a.rank} kernel, dt = 0.25 fs",
         "natoms": a.natoms, "n_orb": 4 * a.natoms, "Te_K": a.Te, "n_squarings": a.nsq, "rank_m": a.rank,
         "pair_repulsion": f"{a.rep_A:g} exp(-r/0.3 A) eV" if a.rep_A else "off",
-        "kernel_probe_products": "one 16-bit product" if a.kernel_prec else "three (full split)",
-        "mu_chain_products": "one 16-bit product" if a.mu_prec else "three (full split)",
+        "kernel_probe_products": chain_products(a, a.kernel_prec),
+        "mu_chain_products": chain_products(a, a.mu_prec),
         "prec": a.prec, "parallelism": parallel,
         "l2": f"inputs larger than L2: about {expansion_bytes(a) / 1e9:.0f} GB of expansion matrices are "
               f"rewritten every step",
@@ -207,8 +216,8 @@ def single_product_chains(a):
 
 
 def dtype_label(a):
-    """The products' arithmetic: FP64, or the 16-bit split (three products per split product) with
-    the chains that take one 16-bit product named."""
+    """The products' arithmetic: FP64, or the split (three products of the operand format per split
+    product) with the chains that take one hi*hi product named."""
     if a.prec == "fp64":
         return "f64"
     base = a.prec[:4]
